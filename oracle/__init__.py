@@ -1,0 +1,442 @@
+"""FP64 CPU oracle for physics-grounded Gaussian volume rendering (test infrastructure).
+
+Only the test suite, the smoke check and the benchmark's CPU-baseline / reference leg may
+import this package. It shares no code with the CUDA library in ``paper_2603_09621_gb300``
+and never imports it; inputs reach both sides from ``paper_2603_09621_gb300.inputs``, which
+holds random draws and phantom geometry only.
+
+Each function cites the passage of the paper ("Physics-Driven 3D Gaussian Rendering for
+Zero-Shot MRI Super-Resolution") it follows. Where the paper is silent the reading is stated
+in the docstring.
+
+Parameter layout of one Gaussian (12 raw values, Sec. 3.1: position 3, covariance 7,
+amplitude 1, relaxation proxy 1): ``[mu_x, mu_y, mu_z, log_s_x, log_s_y, log_s_z,
+q_w, q_x, q_y, q_z, a, t]``.
+
+Volumes are ``[nz, ny, nx]`` arrays (x fastest); voxel (i, j, k) has centre
+``origin + (i + 1/2, j + 1/2, k + 1/2) * h``.
+
+Parity status: every function here is pinned by ``tests/test_oracle_*.py`` against closed
+forms, invariants, brute force or library routines, except ``ssim3d`` (a stated reading of
+the paper's evaluation metric whose window the paper does not give: parity unpinned beyond
+the identity and symmetry checks).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gs_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libgs_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle (FP64, OpenMP, no floating-point contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i64, f64, f32, i32 = ctypes.c_int64, ctypes.c_double, ctypes.c_float, ctypes.c_int
+        _lib.og_render.restype = i64
+        _lib.og_render.argtypes = [P, i64, P, P, P, P, f64, f64, i32, i32, i32, f64, i32,
+                                   P, P, P, P]
+        _lib.og_render_grad.restype = i64
+        _lib.og_render_grad.argtypes = [P, i64, P, P, P, P, f64, f64, i32, i32, i32, i32,
+                                        P, P, P]
+        _lib.og_bins_fp32.restype = None
+        _lib.og_bins_fp32.argtypes = [P, i64, P, P, P, P, f32, P]
+        _lib.og_signal_proxy.restype = None
+        _lib.og_signal_proxy.argtypes = [P, P, i64, f64, f64, P]
+        _lib.og_exp_cw_public.restype = f32
+        _lib.og_exp_cw_public.argtypes = [f32]
+        _lib.og_num_threads.restype = i32
+        _lib.og_set_num_threads.argtypes = [i32]
+    return _lib
+
+
+def num_threads() -> int:
+    return int(lib().og_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    lib().og_set_num_threads(int(n))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+@dataclass
+class Grid:
+    """Voxel grid: dims (nx, ny, nz), spacing h and origin (world units, mm)."""
+    nx: int
+    ny: int
+    nz: int
+    h: tuple = (1.0, 1.0, 1.0)
+    origin: tuple = (0.0, 0.0, 0.0)
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+
+@dataclass
+class Config:
+    """Rendering options. Defaults follow the readings stated in the module docstring."""
+    trunc_sigma: float = 3.0     # Sec. 3.3: 3-sigma Mahalanobis ellipsoids
+    eps: float = 1e-12           # W floor (the paper gives none)
+    signal_mode: int = 0         # 0: v = A, r = T ; 1: v = A T, r = 1
+    a_act: int = 0               # 0 identity, 1 sigmoid
+    t_act: int = 0               # 0 identity, 1 sigmoid
+    brick: tuple = (8, 8, 8)     # brick shape (x, y, z); the paper uses 8 x 8 x 4
+
+
+def _grid_arrays(grid: Grid):
+    dims = np.array([grid.nx, grid.ny, grid.nz], dtype=np.int32)
+    h = np.array(grid.h, dtype=np.float64)
+    o = np.array(grid.origin, dtype=np.float64)
+    return dims, h, o
+
+
+def _crop_array(grid: Grid, crop):
+    if crop is None:
+        return None, (grid.nz, grid.ny, grid.nx)
+    x0, x1, y0, y1, z0, z1 = [int(v) for v in crop]
+    assert 0 <= x0 <= x1 <= grid.nx and 0 <= y0 <= y1 <= grid.ny and 0 <= z0 <= z1 <= grid.nz
+    return np.array([x0, x1, y0, y1, z0, z1], dtype=np.int32), (z1 - z0, y1 - y0, x1 - x0)
+
+
+# --------------------------------------------------------------------------- Eq. 2
+
+def signal_proxy(T1, T2, TR: float, TE: float) -> np.ndarray:
+    """Eq. 2 (Sec. 3.1): relaxation proxy T = (1 - exp(-TR/T1)) exp(-TE/T2), FP64."""
+    T1 = np.ascontiguousarray(T1, dtype=np.float64).ravel()
+    T2 = np.ascontiguousarray(T2, dtype=np.float64).ravel()
+    out = np.empty_like(T1)
+    lib().og_signal_proxy(_ptr(T1), _ptr(T2), T1.size, float(TR), float(TE), _ptr(out))
+    return out
+
+
+# --------------------------------------------------------------------- Eq. 3-4
+
+def render(params, grid: Grid, cfg: Config = Config(), crop=None, amb_tol=None, prune=True):
+    """Eq. 3-4 with the Sec. 3.3 truncation, brute force in FP64.
+
+    Returns dict(I, W, S, amb, n_invalid), each volume crop-shaped ``[z, y, x]``. ``amb``
+    counts, per voxel, the pairs whose d^2 lies within ``amb_tol`` of sigma_t^2 (default
+    1e-4 sigma_t^2): their inclusion is decided by rounding, so parity tests compare only
+    voxels with ``amb == 0``.
+    """
+    p = np.ascontiguousarray(params, dtype=np.float64).reshape(-1, 12)
+    dims, h, o = _grid_arrays(grid)
+    carr, shape = _crop_array(grid, crop)
+    if amb_tol is None:
+        amb_tol = 1e-4 * cfg.trunc_sigma ** 2
+    I = np.zeros(shape, np.float64)
+    W = np.zeros(shape, np.float64)
+    S = np.zeros(shape, np.float64)
+    amb = np.zeros(shape, np.int32)
+    n_bad = lib().og_render(_ptr(p), p.shape[0], _ptr(dims), _ptr(h), _ptr(o),
+                            None if carr is None else _ptr(carr), cfg.trunc_sigma, cfg.eps,
+                            cfg.signal_mode, cfg.a_act, cfg.t_act, float(amb_tol),
+                            1 if prune else 0, _ptr(I), _ptr(W), _ptr(S), _ptr(amb))
+    if n_bad < 0:
+        raise MemoryError("oracle render: allocation failed")
+    return dict(I=I, W=W, S=S, amb=amb, n_invalid=int(n_bad))
+
+
+def render_grad(params, grid: Grid, dI, cfg: Config = Config(), crop=None, prune=True,
+                want_geo=False):
+    """Eq. 5-6 (Sec. 3.3) and the chain to the raw parameters, FP64.
+
+    ``dI`` is dL/dI on the crop (crop-shaped); voxels outside the crop have dL/dI = 0.
+    Returns dL/d(raw params) ``[N, 12]`` and, with ``want_geo``, dL/d(mu, c_xx, c_yy, c_zz,
+    c_xy, c_xz, c_yz, v, r) ``[N, 11]``.
+    """
+    p = np.ascontiguousarray(params, dtype=np.float64).reshape(-1, 12)
+    dims, h, o = _grid_arrays(grid)
+    carr, shape = _crop_array(grid, crop)
+    dI = np.ascontiguousarray(dI, dtype=np.float64)
+    assert dI.shape == shape, (dI.shape, shape)
+    out = np.zeros((p.shape[0], 12), np.float64)
+    geo = np.zeros((p.shape[0], 11), np.float64) if want_geo else None
+    n_bad = lib().og_render_grad(_ptr(p), p.shape[0], _ptr(dims), _ptr(h), _ptr(o),
+                                 None if carr is None else _ptr(carr), cfg.trunc_sigma,
+                                 cfg.eps, cfg.signal_mode, cfg.a_act, cfg.t_act,
+                                 1 if prune else 0, _ptr(dI), _ptr(out),
+                                 None if geo is None else _ptr(geo))
+    if n_bad < 0:
+        raise MemoryError("oracle render_grad: allocation failed")
+    return (out, geo) if want_geo else out
+
+
+# ------------------------------------------------------------ brick binning (FP32)
+
+def exp_cw(x: float) -> float:
+    """The FP32 exponential of the binning specification (Cody-Waite, see gs_oracle.c)."""
+    return float(lib().og_exp_cw_public(float(x)))
+
+
+def brick_ranges_fp32(params, grid: Grid, cfg: Config = Config()) -> np.ndarray:
+    """Per-Gaussian brick range ``[N, 7]`` (lo xyz, hi xyz, meets-grid flag), decided in FP32.
+
+    Sec. 3.3 bins each Gaussian by its 3-sigma extent; the axis-aligned bounding box of the
+    ellipsoid {d^2 <= sigma_t^2} has half-extent sigma_t sqrt(Sigma_kk). The decision is an
+    integer made by floating point, so it is taken in the kernel's precision (FP32) with the
+    operation order documented in gs_oracle.c.
+    """
+    p = np.ascontiguousarray(params, dtype=np.float32).reshape(-1, 12)
+    dims = np.array([grid.nx, grid.ny, grid.nz], dtype=np.int32)
+    h = np.array(grid.h, dtype=np.float32)
+    o = np.array(grid.origin, dtype=np.float32)
+    b = np.array(cfg.brick, dtype=np.int32)
+    out = np.zeros((p.shape[0], 7), np.int32)
+    lib().og_bins_fp32(_ptr(p), p.shape[0], _ptr(dims), _ptr(h), _ptr(o), _ptr(b),
+                       float(cfg.trunc_sigma), _ptr(out))
+    return out
+
+
+def brick_grid(grid: Grid, cfg: Config = Config()):
+    """Number of bricks along x, y, z (partial bricks at the far edges count)."""
+    bx, by, bz = cfg.brick
+    return (-(-grid.nx // bx), -(-grid.ny // by), -(-grid.nz // bz))
+
+
+def brick_lists(params, grid: Grid, cfg: Config = Config()):
+    """Per-brick Gaussian lists (Sec. 3.3: 'for each brick b we identify intersecting
+    Gaussians'), brick-major, ascending Gaussian id inside each brick.
+
+    Returns dict(brick_off [nb+1], pair_gid [P], gm_off [N+1], gm_brick [P]) where the
+    Gaussian-major list enumerates, for each Gaussian in ascending order, its bricks in
+    ascending linear brick index (x fastest).
+    """
+    rng = brick_ranges_fp32(params, grid, cfg)
+    nbx, nby, nbz = brick_grid(grid, cfg)
+    nb = nbx * nby * nbz
+    gm_brick = []
+    counts = np.zeros(rng.shape[0], np.int64)
+    for g in range(rng.shape[0]):
+        lo, hi, ok = rng[g, :3], rng[g, 3:6], rng[g, 6]
+        if not ok:
+            continue
+        zz, yy, xx = np.meshgrid(np.arange(lo[2], hi[2] + 1), np.arange(lo[1], hi[1] + 1),
+                                 np.arange(lo[0], hi[0] + 1), indexing="ij")
+        b = ((zz * nby + yy) * nbx + xx).ravel()
+        gm_brick.append(b)
+        counts[g] = b.size
+    gm_brick = np.concatenate(gm_brick) if gm_brick else np.zeros(0, np.int64)
+    gm_off = np.zeros(rng.shape[0] + 1, np.int64)
+    gm_off[1:] = np.cumsum(counts)
+    gm_gid = np.repeat(np.arange(rng.shape[0]), counts)
+    order = np.argsort(gm_brick, kind="stable")
+    pair_gid = gm_gid[order]
+    per_brick = np.bincount(gm_brick, minlength=nb) if gm_brick.size else np.zeros(nb, np.int64)
+    brick_off = np.zeros(nb + 1, np.int64)
+    brick_off[1:] = np.cumsum(per_brick)
+    return dict(brick_off=brick_off, pair_gid=pair_gid, gm_off=gm_off, gm_brick=gm_brick,
+                ranges=rng)
+
+
+# ------------------------------------------------------- slice-profile forward model
+
+def downsample(hr, s: int) -> np.ndarray:
+    """Box slice profile along z: LR[k] = (1/s) sum_{j<s} HR[s k + j], k < floor(nz/s).
+
+    The paper does not give its training forward model (it builds LR data by trilinear
+    downsampling, Sec. 4.1); the z box profile is the stated reading used for fitting.
+    """
+    hr = np.asarray(hr, dtype=np.float64)
+    nz = hr.shape[0]
+    nl = nz // s
+    out = np.zeros((nl,) + hr.shape[1:], np.float64)
+    for k in range(nl):
+        acc = np.zeros(hr.shape[1:], np.float64)
+        for j in range(s):
+            acc += hr[s * k + j]
+        out[k] = acc / s
+    return out
+
+
+def downsample_adjoint(dlr, nz: int, s: int) -> np.ndarray:
+    """Adjoint of ``downsample``: dHR[z] = dLR[z // s] / s for z < s floor(nz/s), else 0."""
+    dlr = np.asarray(dlr, dtype=np.float64)
+    out = np.zeros((nz,) + dlr.shape[1:], np.float64)
+    for z in range(s * (nz // s)):
+        out[z] = dlr[z // s] / s
+    return out
+
+
+def l1_loss(pred, target):
+    """Mean absolute error and its gradient sign(pred - target) / n (sign(0) = 0)."""
+    pred = np.asarray(pred, dtype=np.float64)
+    target = np.asarray(target, dtype=np.float64)
+    diff = pred - target
+    n = diff.size
+    return float(np.abs(diff).sum() / n), np.sign(diff) / n
+
+
+# ------------------------------------------------------------------------- Adam
+
+@dataclass
+class AdamConfig:
+    """Adam with per-group learning rates (the paper gives no optimiser; these follow the
+    fitting configuration: 1e-3 on means, 5e-3 on scales and tissue parameters)."""
+    lr_mu: float = 1e-3
+    lr_scale: float = 5e-3
+    lr_rot: float = 5e-3
+    lr_a: float = 5e-3
+    lr_t: float = 5e-3
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-8
+
+    def lr_vector(self):
+        return np.array([self.lr_mu] * 3 + [self.lr_scale] * 3 + [self.lr_rot] * 4
+                        + [self.lr_a, self.lr_t], dtype=np.float64)
+
+
+def adam_step(params, grad, m, v, step: int, acfg: AdamConfig = AdamConfig()):
+    """One Adam update (Kingma & Ba 2015, bias-corrected); ``step`` counts from 1."""
+    params = np.asarray(params, np.float64).copy()
+    g = np.asarray(grad, np.float64)
+    m = acfg.beta1 * np.asarray(m, np.float64) + (1 - acfg.beta1) * g
+    v = acfg.beta2 * np.asarray(v, np.float64) + (1 - acfg.beta2) * g * g
+    mhat = m / (1 - acfg.beta1 ** step)
+    vhat = v / (1 - acfg.beta2 ** step)
+    lr = acfg.lr_vector()[None, :]
+    params -= lr * mhat / (np.sqrt(vhat) + acfg.eps)
+    return params, m, v
+
+
+# ------------------------------------------------------------------ initialisation
+
+def lattice_dims(grid: Grid, n_target: int):
+    """Lattice of about n_target points over the volume with isotropic spacing
+    l = (V / n_target)^(1/3): n_a = max(1, round(L_a / l)) points along axis a."""
+    L = np.array([grid.nx * grid.h[0], grid.ny * grid.h[1], grid.nz * grid.h[2]])
+    ell = (L.prod() / n_target) ** (1.0 / 3.0)
+    n = [max(1, int(round(L[a] / ell))) for a in range(3)]
+    return n, L
+
+
+def trilinear(vol, grid_lr: Grid, pts) -> np.ndarray:
+    """Trilinear sample of ``vol`` ([z, y, x] on ``grid_lr``) at world points ``pts`` [M, 3],
+    with edge clamping (the continuous index is clamped to [0, n-1])."""
+    vol = np.asarray(vol, np.float64)
+    out = np.empty(pts.shape[0], np.float64)
+    n = (grid_lr.nx, grid_lr.ny, grid_lr.nz)
+    u = np.empty_like(pts, dtype=np.float64)
+    for a in range(3):
+        u[:, a] = (pts[:, a] - grid_lr.origin[a]) / grid_lr.h[a] - 0.5
+        u[:, a] = np.clip(u[:, a], 0.0, n[a] - 1)
+    i0 = np.floor(u).astype(np.int64)
+    i1 = np.minimum(i0 + 1, np.array(n) - 1)
+    f = u - i0
+    for m in range(pts.shape[0]):
+        acc = 0.0
+        for cz in (0, 1):
+            for cy in (0, 1):
+                for cx in (0, 1):
+                    wx = f[m, 0] if cx else 1.0 - f[m, 0]
+                    wy = f[m, 1] if cy else 1.0 - f[m, 1]
+                    wz = f[m, 2] if cz else 1.0 - f[m, 2]
+                    xi = i1[m, 0] if cx else i0[m, 0]
+                    yi = i1[m, 1] if cy else i0[m, 1]
+                    zi = i1[m, 2] if cz else i0[m, 2]
+                    acc += wx * wy * wz * vol[zi, yi, xi]
+        out[m] = acc
+    return out
+
+
+def init_lattice(lr_vol, grid_hr: Grid, s: int, n_target: int, t_act: int = 1,
+                 t_init: float = 0.5):
+    """Initial Gaussians from the LR volume ("3D Gaussians are initialized solely from the
+    coordinates of the low-resolution volume", Fig. 1 caption; details are not given).
+
+    Reading: an axis lattice (``lattice_dims``) with centres at the cell centres, amplitude
+    = trilinear sample of the LR volume at the centre, T = t_init, isotropic-per-axis scale
+    s_a = l_a / 2 (l_a = L_a / n_a), identity rotation. The LR grid has spacing (h_x, h_y,
+    s h_z) and the HR origin. Returns float32 ``[N, 12]`` raw parameters.
+    """
+    n, L = lattice_dims(grid_hr, n_target)
+    ell = [L[a] / n[a] for a in range(3)]
+    xs = [grid_hr.origin[a] + (np.arange(n[a]) + 0.5) * ell[a] for a in range(3)]
+    zz, yy, xx = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+    pts = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], axis=1)
+    grid_lr = Grid(grid_hr.nx, grid_hr.ny, grid_hr.nz // s,
+                   (grid_hr.h[0], grid_hr.h[1], grid_hr.h[2] * s), grid_hr.origin)
+    A = trilinear(lr_vol, grid_lr, pts)
+    N = pts.shape[0]
+    out = np.zeros((N, 12), np.float64)
+    out[:, 0:3] = pts
+    out[:, 3:6] = np.log(0.5 * np.array(ell))[None, :]
+    out[:, 6] = 1.0
+    out[:, 10] = A
+    out[:, 11] = math.log(t_init / (1.0 - t_init)) if t_act else t_init
+    return out.astype(np.float32)
+
+
+# ---------------------------------------------------------------- phantom (oracle side)
+
+def phantom_from_draws(ph: dict, TR: float, TE: float):
+    """HR phantom from the seeded draws of ``inputs.phantom_draws``: intensity of ellipsoid
+    e = PD_e T(T1_e, T2_e) (Eq. 2 signal), background 0, normalised to [0, 1] by the
+    largest tissue intensity (Sec. 4.1 normalises every volume to [0, 1])."""
+    tissue = ph["pd"] * signal_proxy(ph["t1"], ph["t2"], TR, TE)
+    table = np.concatenate([[0.0], tissue])
+    present = np.unique(ph["label"])
+    vmax = table[present].max()
+    return table[ph["label"]] / (vmax if vmax > 0 else 1.0)
+
+
+def rician(lr, n1, n2):
+    """Magnitude of the complex signal LR + n1 + i n2 (Rician noise on a magnitude image)."""
+    lr = np.asarray(lr, np.float64)
+    return np.sqrt((lr + n1) ** 2 + n2 ** 2)
+
+
+# --------------------------------------------------------------------- metrics
+
+def psnr(x, ref, data_range: float = 1.0) -> float:
+    """Peak signal-to-noise ratio over the whole volume (data range 1, Sec. 4.1)."""
+    mse = float(np.mean((np.asarray(x, np.float64) - np.asarray(ref, np.float64)) ** 2))
+    return float("inf") if mse == 0 else 10.0 * math.log10(data_range ** 2 / mse)
+
+
+def ssim3d(x, ref, data_range: float = 1.0, sigma: float = 1.5) -> float:
+    """Mean SSIM (Wang et al. 2004, cited in Sec. 4.2) in 3D with a Gaussian window of
+    std ``sigma`` voxels, K1 = 0.01, K2 = 0.03 (window and constants are readings)."""
+    from scipy.ndimage import gaussian_filter
+    x = np.asarray(x, np.float64)
+    y = np.asarray(ref, np.float64)
+    c1 = (0.01 * data_range) ** 2
+    c2 = (0.03 * data_range) ** 2
+    f = lambda a: gaussian_filter(a, sigma, mode="reflect", truncate=3.5)
+    mx, my = f(x), f(y)
+    sxx = f(x * x) - mx * mx
+    syy = f(y * y) - my * my
+    sxy = f(x * y) - mx * my
+    num = (2 * mx * my + c1) * (2 * sxy + c2)
+    den = (mx * mx + my * my + c1) * (sxx + syy + c2)
+    return float(np.mean(num / den))
