@@ -1,0 +1,419 @@
+#!/usr/bin/env python
+"""Benchmark of the Gaussian volume rasteriser's hot path on GB300.
+
+One step = one zero-shot fitting iteration through the C ABI (gs_fit_step): brick binning,
+forward render (Eq. 3-4), z box slice profile + L1 + adjoint profile, adjoint render
+(Eq. 5-6), gradient reduction and parameter chain, Adam. Workload (default): 256 x 256 x 128
+HR grid at 1 mm, 500k Gaussians initialised on a lattice from the LR scan, LR = 4-slice z box
+average of a seeded 12-ellipsoid tissue phantom with Rician noise (sigma 0.02), L1 loss,
+deterministic reduction.
+
+Metric: effective Gaussian-voxel pair evaluations per second, where an effective pair is a
+(Gaussian, voxel) pair inside the 3-sigma ellipsoid (d^2 <= 9), taken once through the
+forward and once through the adjoint render of a step. Also reported: ms per step, fit
+seconds per scan (2,000 iterations at this size), voxels per second.
+
+Timing: W warm-up steps, then K steps timed with CUDA events recorded by the library on the
+launching stream at the step's phase boundaries; L2 is flushed (256 MB write) between timed
+steps; barrier + synchronize on both sides; max over ranks. `--gpus N` under torchrun runs
+N independent replicas (one scan per GPU; the path does not shard).
+
+`--impl reference` times the FP64 CPU oracle (the only reference: the paper ships no code)
+on a bounded sample of the same workload, in the same unit.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+SHAPE = (128, 256, 256)       # (nz, ny, nx)
+S_FACTOR = 4
+N_GAUSS = 500_000
+FIT_ITERS = 2000
+L2_FLUSH_BYTES = 256 << 20
+SM_COUNT_NOMINAL = 152
+EX2_PER_CLK_SM = 16           # MUFU ex2 results per clock per SM
+FALLBACK_SM_MHZ = 2070.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--fast", action="store_true", help="non-deterministic (atomic) reduction")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------- helpers
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"sm_max_mhz": FALLBACK_SM_MHZ, "hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.gpu_id:
+                cmd += ["-i", self.gpu_id]
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, reasons, n = [], [], set(), 0
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                n += 1
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": n}
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        t = json.load(f)
+    ent = t.get(kernel)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_2603_09621_gb300", "csrc", ent["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return ent["bytes_per_launch"] if h == ent["source_sha"] else None
+
+
+# ------------------------------------------------------------------------- oracle sample
+def oracle_workload():
+    """Oracle-side copy of the fitting workload (built from the same draws by the oracle)."""
+    import numpy as np
+    import oracle
+    from paper_2603_09621_gb300 import inputs
+    nz, ny, nx = SHAPE
+    ph = inputs.phantom_draws(0, SHAPE, n_ell=12, s=S_FACTOR)
+    hr = oracle.phantom_from_draws(ph, inputs.TR_MS, inputs.TE_MS)
+    lr = oracle.rician(oracle.downsample(hr, S_FACTOR), ph["n1"], ph["n2"]).astype(np.float32)
+    grid = oracle.Grid(nx, ny, nz)
+    params = oracle.init_lattice(lr, grid, S_FACTOR, N_GAUSS, t_act=1)
+    return grid, params
+
+
+def oracle_sample(grid, params, nslices: int, z0: int):
+    """FP64 oracle forward + adjoint on a z-slab of `nslices` full x-y slices (all Gaussians).
+    Returns (seconds, effective pairs)."""
+    import numpy as np
+    import oracle
+    cfg = oracle.Config(t_act=1)
+    crop = (0, grid.nx, 0, grid.ny, z0, z0 + nslices)
+    p64 = params.astype(np.float64)
+    t0 = time.perf_counter()
+    r = oracle.render(p64, grid, cfg, crop=crop)
+    dI = np.ones(r["I"].shape)
+    oracle.render_grad(p64, grid, dI, cfg, crop=crop)
+    dt = time.perf_counter() - t0
+    return dt, int(r["npair"].sum())
+
+
+def cpu_baseline(target_s: float):
+    import oracle
+    oracle.build()
+    grid, params = oracle_workload()
+    z0 = SHAPE[0] // 2
+    t1, _ = oracle_sample(grid, params, 1, z0)
+    k = max(1, min(SHAPE[0] - z0, int(target_s / max(t1, 1e-3))))
+    dt, pairs = oracle_sample(grid, params, k, z0 - k // 2)
+    # render_grad re-renders the slab, so each effective pair is evaluated in a forward and
+    # an adjoint pass, as in the GPU step; the metric counts it once.
+    return {"value": pairs / dt, "unit": "pair-evals/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"FP64 oracle forward+adjoint on a {grid.nx}x{grid.ny}x{k} z-slab of the "
+                      f"{grid.nx}x{grid.ny}x{grid.nz} fit workload with all {N_GAUSS} Gaussians "
+                      f"({pairs} effective pairs, {dt:.1f} s)"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    grid, params = oracle_workload()
+    z0 = SHAPE[0] // 2
+    t1, _ = oracle_sample(grid, params, 1, z0)
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    k = max(1, min(16, int(budget / max(t1, 1e-3))))
+    for _ in range(args.warmup):
+        oracle_sample(grid, params, k, z0)
+    tot_t, tot_p = 0.0, 0
+    for _ in range(args.steps):
+        dt, pairs = oracle_sample(grid, params, k, z0)
+        tot_t += dt
+        tot_p += pairs
+    value = tot_p / tot_t
+    sample = (f"FP64 oracle forward+adjoint per step on a {grid.nx}x{grid.ny}x{k} z-slab of "
+              f"the {grid.nx}x{grid.ny}x{grid.nz} fit workload with all {N_GAUSS} Gaussians")
+    line = {"metric": "gaussian_voxel_pair_evals_per_s", "value": value,
+            "unit": "pair-evals/s", "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * tot_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args),
+            "cpu_baseline": {"value": value, "unit": "pair-evals/s", "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "pair-evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(args):
+    nz, ny, nx = SHAPE
+    return {"workload": f"zero-shot fit step {nx}x{ny}x{nz} HR, {N_GAUSS} Gaussians, "
+                        f"z box x{S_FACTOR}, L1, Adam",
+            "grid": [nx, ny, nz], "n_gauss": N_GAUSS, "slice_factor": S_FACTOR,
+            "brick": [8, 8, 8], "deterministic": 0 if args.fast else 1,
+            "l2": "flushed between timed steps (256 MB write)"}
+
+
+# ------------------------------------------------------------------------- our path
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2603_09621_gb300 import build as gbuild
+    gbuild.build()
+    from paper_2603_09621_gb300 import gs, workloads
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    cfg = gs.Config(t_act=1, deterministic=0 if args.fast else 1)
+    w = workloads.phantom_fit(shape=SHAPE, s=S_FACTOR, n_gauss=N_GAUSS, seed=rank)
+    g = w["grid"]
+    st = gs.FitState(w["params0"], w["lr"], g, S_FACTOR, cfg)
+    stream = torch.cuda.current_stream()
+    events = [torch.cuda.Event(enable_timing=True) for _ in range(gs.GS_FIT_PHASES)]
+    for e in events:
+        e.record(stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(args.warmup):
+        st.step()
+    torch.cuda.synchronize()
+    rc, bits = st.check()
+    if rc != 0:
+        raise RuntimeError(f"fit step status {gs.STATUS.get(rc, rc)} bits {bits}")
+
+    # effective / evaluated pairs of the current cloud (outside the timed region)
+    stats = torch.zeros(2, dtype=torch.int64, device=dev)
+    gs.gs_bin_bricks(st.params, g, cfg, st.bins, st.ws)
+    I_tmp, W_tmp = gs.gs_render_fwd(st.bins, g, cfg, stats=stats)
+    torch.cuda.synchronize()
+    n_eff, n_eval = [int(x) for x in stats.cpu()]
+    n_pairs = st.bins.npairs()
+    del I_tmp, W_tmp
+
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(gpu_id)
+    st.set_phase_events(events)
+    phase_ms = [0.0] * (gs.GS_FIT_PHASES - 1)
+    step_ms = []
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = gs.gs_launch_count()
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1.0)                      # evict L2 between timed steps
+        st.step()
+        events[-1].synchronize()
+        for i in range(gs.GS_FIT_PHASES - 1):
+            phase_ms[i] += events[i].elapsed_time(events[i + 1])
+        step_ms.append(events[0].elapsed_time(events[-1]))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    launches = gs.gs_launch_count() - launches0
+    barrier(world)
+    clk = clocks.stop()
+    st.set_phase_events(None)
+    rc, bits = st.check()
+    if rc != 0:
+        raise RuntimeError(f"fit step status {gs.STATUS.get(rc, rc)} bits {bits}")
+
+    t_dev = sum(step_ms) / 1000.0
+    t_max = allreduce_max(t_dev, world)
+    units = allreduce_sum(float(n_eff) * args.steps, world)
+    value = units / t_max
+    ms_step = 1000.0 * t_max / args.steps
+
+    # roofline of the dominant render kernel (effective pairs per launch / mean duration)
+    names = ["binning", "forward_render", "profile_l1", "adjoint_render", "reduce_chain", "adam"]
+    per_phase = {n: phase_ms[i] / args.steps for i, n in enumerate(names)}
+    kern = "k_render_bwd" if per_phase["adjoint_render"] >= per_phase["forward_render"] else "k_render_fwd"
+    t_k = (per_phase["adjoint_render"] if kern == "k_render_bwd" else per_phase["forward_render"]) / 1e3
+    peaks, peak_src = measured_peaks()
+    f_mhz = float(peaks.get("sm_max_mhz", FALLBACK_SM_MHZ))
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_gpairs = n_sm * EX2_PER_CLK_SM * f_mhz * 1e6 / 1e9
+    achieved = n_eff / t_k / 1e9
+    roofline = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak_gpairs,
+                "unit": "Gpair/s", "frac": achieved / peak_gpairs,
+                "traffic": traffic_for(kern),
+                "peak_basis": f"{n_sm} SMs x {EX2_PER_CLK_SM} ex2/clk x {f_mhz:.0f} MHz "
+                              f"(SM max clock, {peak_src}); one ex2 per effective pair"}
+
+    # end to end through the public API with host buffers
+    h_params = w["params0"].cpu().pin_memory()
+    h_lr = w["lr"].cpu().pin_memory()
+    h_loss = torch.empty((), dtype=torch.float32).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_ms = []
+    for i in range(args.e2e_steps + 1):
+        flush.fill_(1.0)
+        e0.record(stream)
+        st.params.copy_(h_params, non_blocking=True)
+        st.lr_target.copy_(h_lr, non_blocking=True)
+        st.step()
+        h_loss.copy_(st.d_loss, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if i > 0:
+            e2e_ms.append(e0.elapsed_time(e1))
+    t_e2e = allreduce_max(sum(e2e_ms) / 1000.0, world)
+    e2e = {"value": allreduce_sum(float(n_eff) * len(e2e_ms), world) / t_e2e,
+           "unit": "pair-evals/s",
+           "h2d_bytes_per_step": h_params.numel() * 4 + h_lr.numel() * 4,
+           "d2h_bytes_per_step": 4, "ms_per_step": 1000.0 * t_e2e / len(e2e_ms)}
+
+    if rank != 0:
+        return
+    nz, ny, nx = SHAPE
+    line = {"metric": "gaussian_voxel_pair_evals_per_s", "value": value,
+            "unit": "pair-evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded ellipsoid tissue phantom standing in for MSD/FeTA)",
+            "config": config_dict(args),
+            "fit_s_per_scan": FIT_ITERS * ms_step / 1000.0,
+            "voxels_per_s": world * nx * ny * nz * args.steps / t_max,
+            "pairs": {"effective": n_eff, "evaluated": n_eval, "brick_pairs": n_pairs,
+                      "culling": n_eff / max(n_eval, 1)},
+            "phase_ms": per_phase, "wall_s": wall,
+            "roofline": roofline, "clocks": clk, "e2e": e2e, "gpu_launches": launches}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,254 @@
+/*
+ * gs_api.h -- C ABI of the GB300 (sm_103a) Gaussian volume rasteriser for zero-shot MRI
+ * super-resolution ("Physics-Driven 3D Gaussian Rendering for Zero-Shot MRI
+ * Super-Resolution", Sec. 3).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers marked "device" are CUDA device memory owned by the caller; "host" pointers
+ *     are ordinary host memory. The library allocates no memory: scratch comes from a
+ *     caller-provided workspace whose size gs_workspace_bytes() reports.
+ *   - Every compute call is asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *     default stream) unless its comment says "synchronous". Argument errors are detected on
+ *     the host before any launch and returned at once; CUDA launch errors map to
+ *     GS_ERR_CUDA. Conditions found on the device (pair capacity exceeded, invalid Gaussians)
+ *     are written to the device status word of the bins (see gs_status_read).
+ *   - Raw Gaussian parameters are float32 [N, 12] row-major (48 bytes per Gaussian), Sec. 3.1
+ *     (position 3, covariance 7 = log-scale 3 + quaternion 4, amplitude 1, relaxation 1):
+ *        [mu_x, mu_y, mu_z, log_s_x, log_s_y, log_s_z, q_w, q_x, q_y, q_z, a, t]
+ *     Sigma = R(q/|q|) diag(exp(2 log_s)) R^T; A = act_a(a); T = act_t(t) (identity or
+ *     sigmoid). Signal mode 0 renders v = A with relaxation factor r = T (Eq. 3-4); mode 1
+ *     renders v = A T with r = 1. Gaussians with a non-finite value, a zero quaternion or a
+ *     log-scale outside [-30, 30] are invalid: they contribute nothing and raise
+ *     GS_STATUS_NONFINITE in the device status word.
+ *   - Volumes are float32 [nz, ny, nx] (x fastest). Voxel (i, j, k) has centre
+ *     origin + (i + 1/2, j + 1/2, k + 1/2) * h (world units, mm).
+ *   - The forward render is I(p) = sum_i v_i w_i(p) / max(sum_i w_i(p), eps) with
+ *     w_i(p) = r_i exp(-d^2/2), d^2 = (p - mu_i)^T Sigma_i^{-1} (p - mu_i), and a pair
+ *     contributes only when d^2 <= trunc_sigma^2 (Eq. 3-4; the 3-sigma truncation of
+ *     Sec. 3.3). Per voxel the sum runs over Gaussians in ascending id order, so results are
+ *     deterministic and independent of the brick shape.
+ */
+#ifndef GS_API_H
+#define GS_API_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (the CUDA runtime's stream handle type). */
+typedef struct CUstream_st* gs_stream;
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = -1, /* a null pointer, a bad size or an unsupported option */
+    GS_ERR_CAPACITY = -2,    /* the pair list needs more than the bins' capacity */
+    GS_ERR_WORKSPACE = -3,   /* workspace smaller than gs_workspace_bytes() */
+    GS_ERR_CUDA = -4,        /* a CUDA runtime call or kernel launch failed */
+    GS_ERR_TIMEOUT = -5,     /* a bounded device wait gave up */
+    GS_ERR_NONFINITE = -6    /* invalid Gaussians (NaN/Inf, zero quaternion, |log_s| > 30) */
+} gs_status;
+
+/* Bits of the device status word written by the kernels. */
+#define GS_STATUS_CAPACITY 1
+#define GS_STATUS_NONFINITE 2
+
+/* Voxel grid: nx, ny, nz voxels; spacing h (x, y, z) and origin in world units. */
+typedef struct {
+    int32_t nx, ny, nz;
+    float h[3];
+    float origin[3];
+} gs_grid;
+
+/* Rendering options.
+ *   brick: brick shape in voxels (x, y, z); each component a multiple of 4, product <= 1024.
+ *          Sec. 3.3 uses 8 x 8 x 4; the default is 8 x 8 x 8. Output does not depend on it.
+ *   trunc_sigma: Mahalanobis truncation radius (3.0: the 3-sigma ellipsoids of Sec. 3.3).
+ *   eps: floor of the weight sum in the normalisation of Eq. 3 (the paper gives none).
+ *   deterministic: 1 = the backward pass reduces per-Gaussian gradients in a fixed order
+ *                  (bit-reproducible, no floating-point atomics); 0 = one float atomic
+ *                  per (brick, Gaussian, value).
+ *   signal_mode: 0 (v = A, r = T) or 1 (v = A T, r = 1).
+ *   a_act, t_act: 0 = identity, 1 = sigmoid for A and T. */
+typedef struct {
+    int32_t brick[3];
+    float trunc_sigma;
+    float eps;
+    int32_t deterministic;
+    int32_t signal_mode;
+    int32_t a_act;
+    int32_t t_act;
+} gs_config;
+
+/* Brick bins of one Gaussian cloud on one grid (Sec. 3.3: "for each brick b we identify
+ * intersecting Gaussians G_b"). All arrays are device memory carved from one caller-owned
+ * arena by gs_bins_bind(). Brick b = (bx, by, bz) has linear index (bz * nby + by) * nbx + bx.
+ *   brick_off [n_bricks + 1]: pairs of brick b are [brick_off[b], brick_off[b+1]).
+ *   pair_gid  [capacity]: Gaussian id of each pair, brick-major, ascending inside a brick.
+ *   pair_gmj  [capacity]: position of each brick-major pair in the Gaussian-major order.
+ *   gm_off    [n_gauss + 1]: Gaussian-major pair offsets (bricks of one Gaussian ascend).
+ *   rec       [n_gauss, 16] float: per-Gaussian render record (internal layout).
+ *   brange    [n_gauss, 8] int32: brick range lo (x, y, z), hi (x, y, z), pair count, valid.
+ *   d_npairs  device int64: pairs needed by the last gs_bin_bricks call.
+ *   d_status  device int32: GS_STATUS_* bits of the last gs_bin_bricks call. */
+typedef struct {
+    int64_t n_gauss;
+    int64_t capacity;
+    int32_t n_bricks;
+    int32_t nbx, nby, nbz;
+    int32_t* brick_off;
+    int32_t* pair_gid;
+    int32_t* pair_gmj;
+    int32_t* gm_off;
+    float* rec;
+    int32_t* brange;
+    int64_t* d_npairs;
+    int32_t* d_status;
+} gs_bins;
+
+/* Adam hyper-parameters (bias-corrected Adam, Kingma & Ba 2015; the paper names no
+ * optimiser). Learning rates per parameter group: means, log-scales, quaternion, a, t. */
+typedef struct {
+    float lr_mu, lr_scale, lr_rot, lr_a, lr_t;
+    float beta1, beta2, eps;
+} gs_adam;
+
+/* Size in bytes of the device arena that gs_bins_bind() carves; 0 on invalid arguments.
+ * capacity is the maximum number of (brick, Gaussian) pairs, at most 2^31 - 4096. */
+size_t gs_bins_bytes(int64_t n_gauss, int64_t capacity, const gs_grid* grid,
+                     const gs_config* cfg);
+
+/* Fill `out` with pointers into `arena` (device, at least gs_bins_bytes() bytes, 256-byte
+ * aligned). Host-only; nothing is launched. */
+gs_status gs_bins_bind(void* arena, size_t arena_bytes, int64_t n_gauss, int64_t capacity,
+                       const gs_grid* grid, const gs_config* cfg, gs_bins* out);
+
+/* Scratch bytes needed by gs_bin_bricks, gs_render_bwd, gs_l1_loss and gs_fit_step for this
+ * problem size (one workspace serves all of them; calls sharing it must not overlap). */
+size_t gs_workspace_bytes(int64_t n_gauss, int64_t capacity, const gs_grid* grid,
+                          const gs_config* cfg);
+
+/* Sec. 3.1 / Eq. 2: T = (1 - exp(-TR/T1)) exp(-TE/T2) elementwise.
+ * T1, T2, T_out: device float [n]. TR, TE in the same unit as T1, T2. */
+gs_status gs_signal_proxy(const float* T1, const float* T2, int64_t n, float TR, float TE,
+                          float* T_out, gs_stream stream);
+
+/* Sec. 3.3 brick intersection and binning: activate every Gaussian, bound its truncated
+ * ellipsoid by its axis-aligned box (half-extent trunc_sigma sqrt(Sigma_kk), padded by
+ * 2^-13 relative and 2^-8 voxel), and list it in every brick the box meets (count, exclusive
+ * scan, stable radix scatter: deterministic, bit-exact). The brick-range arithmetic is a
+ * fixed FP32 operation sequence (documented in the oracle's binning specification).
+ * params: device float [n_gauss, 12]. bins: bound to this n_gauss, grid and cfg.
+ * ws: device workspace of ws_bytes >= gs_workspace_bytes().
+ * If the pairs exceed bins->capacity, *d_npairs holds the count needed, the status word
+ * gets GS_STATUS_CAPACITY, and the brick lists are left empty (no later kernel reads past
+ * the capacity). */
+gs_status gs_bin_bricks(const float* params, const gs_grid* grid, const gs_config* cfg,
+                        gs_bins* bins, void* ws, size_t ws_bytes, gs_stream stream);
+
+/* Eq. 3-4 forward render (Sec. 3.3: one CTA per brick, the brick's Gaussians staged through
+ * shared memory). Writes I = S / max(W, eps) and W = sum_i w_i for every voxel.
+ * I, W: device float [nz, ny, nx]. d_stats: device uint64 [2] or NULL; when given, adds the
+ * number of pairs with d^2 <= trunc_sigma^2 (stats[0]) and of pairs evaluated (stats[1]). */
+gs_status gs_render_fwd(const gs_bins* bins, const gs_grid* grid, const gs_config* cfg,
+                        float* I, float* W, unsigned long long* d_stats, gs_stream stream);
+
+/* Eq. 5-6 adjoint of the forward render and the chain to the raw parameters.
+ * params: device float [n_gauss, 12] (the ones binned); I, W: the forward outputs;
+ * dI: device float [nz, ny, nx], dL/dI; dparams: device float [n_gauss, 12], overwritten
+ * with dL/d(raw params). ws: workspace (>= gs_workspace_bytes()). */
+gs_status gs_render_bwd(const float* params, const gs_bins* bins, const gs_grid* grid,
+                        const gs_config* cfg, const float* I, const float* W, const float* dI,
+                        float* dparams, void* ws, size_t ws_bytes, gs_stream stream);
+
+/* Slice-profile forward model (not in the paper; the fitting workload's reading): box
+ * average of s consecutive slices along z. hr: device [nz, ny, nx]; lr: device
+ * [nz / s, ny, nx] (integer division; trailing slices are dropped). */
+gs_status gs_downsample_fwd(const float* hr, int32_t nz, int32_t ny, int32_t nx, int32_t s,
+                            float* lr, gs_stream stream);
+
+/* Adjoint of gs_downsample_fwd: dhr[z] = dlr[z / s] / s for z < s (nz / s), else 0.
+ * dlr: device [nz / s, ny, nx]; dhr: device [nz, ny, nx]. */
+gs_status gs_downsample_bwd(const float* dlr, int32_t nz, int32_t ny, int32_t nx, int32_t s,
+                            float* dhr, gs_stream stream);
+
+/* Mean absolute error over n values, reduced in a fixed order (deterministic).
+ * pred, target: device float [n]; d_loss: device float scalar; dpred: device float [n] or
+ * NULL, receives sign(pred - target) / n (sign(0) = 0). ws: workspace. */
+gs_status gs_l1_loss(const float* pred, const float* target, int64_t n, float* d_loss,
+                     float* dpred, void* ws, size_t ws_bytes, gs_stream stream);
+
+/* One bias-corrected Adam update of params [n_gauss, 12] from grad, with moments m, v
+ * (device float [n_gauss, 12], zero before the first step). d_step: device int32, the
+ * number of steps taken so far; incremented on the device (graph-capturable). */
+gs_status gs_adam_step(float* params, const float* grad, float* m, float* v, int64_t n_gauss,
+                       const gs_adam* hp, int32_t* d_step, gs_stream stream);
+
+/* Initial cloud from the LR volume (Fig. 1 caption: Gaussians are initialised from the
+ * coordinates of the LR volume; details are this library's reading): an axis lattice of
+ * nl = (nlx, nly, nlz) points with centres origin + (i + 1/2) L / nl, amplitude = trilinear
+ * sample of lr (edge-clamped) at the centre, T = t_init (through t_act), log-scale =
+ * log(L_a / (2 nl_a)), identity rotation. lr: device [hr_nz / s, ny, nx] on the grid with
+ * spacing (h_x, h_y, s h_z); params: device float [nlx nly nlz, 12] (x fastest). */
+gs_status gs_init_lattice(const float* lr, const gs_grid* hr_grid, int32_t s, int32_t nlx,
+                          int32_t nly, int32_t nlz, int32_t t_act, float t_init, float* params,
+                          gs_stream stream);
+
+/* One zero-shot fitting iteration (all device work, no host synchronisation; the step can
+ * be captured in a CUDA graph): bin, forward render, z box slice profile, L1 loss against
+ * lr_target, its adjoint, adjoint render, Adam. Every pointer is device memory:
+ *   params, grad, m, v [n_gauss, 12]; I, W, dI [nz, ny, nx]; lr_pred [nz / s, ny, nx]
+ *   (after the step it holds dL/dLR); lr_target [nz / s, ny, nx]; d_loss float scalar (the
+ *   loss of this step's forward pass); d_step int32 (Adam step counter); bins bound for
+ *   n_gauss; ws workspace. On return grad holds dL/d(params) of this step.
+ * phase_events: NULL, or GS_FIT_PHASES cudaEvent_t handles (host) recorded on `stream` at
+ *   the start and after each phase: [0] start, [1] binning, [2] forward render, [3] slice
+ *   profile + L1 + adjoint profile, [4] adjoint render kernel, [5] gradient reduction and
+ *   parameter chain, [6] Adam. n_phase_events is 0 or GS_FIT_PHASES. */
+#define GS_FIT_PHASES 7
+typedef struct {
+    gs_grid grid;
+    gs_config cfg;
+    gs_adam adam;
+    int64_t n_gauss;
+    int32_t s;
+    float* params;
+    float* grad;
+    float* m;
+    float* v;
+    int32_t* d_step;
+    gs_bins bins;
+    float* I;
+    float* W;
+    float* dI;
+    float* lr_pred;
+    const float* lr_target;
+    float* d_loss;
+    void* ws;
+    size_t ws_bytes;
+    void* const* phase_events;
+    int32_t n_phase_events;
+} gs_fit_state;
+
+gs_status gs_fit_step(gs_fit_state* st, gs_stream stream);
+
+/* Synchronous: waits for `stream`, then copies the device status word to *h_status and
+ * returns GS_ERR_CAPACITY or GS_ERR_NONFINITE if the matching bit is set, else GS_OK. */
+gs_status gs_status_read(const int32_t* d_status, int32_t* h_status, gs_stream stream);
+
+/* Static string naming a status code. */
+const char* gs_status_string(gs_status s);
+
+/* Number of kernels this library has launched in the calling process (host counter). */
+unsigned long long gs_launch_count(void);
+
+/* Library version string. */
+const char* gs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_API_H */

@@ -60,7 +60,7 @@ def lib():
         i64, f64, f32, i32 = ctypes.c_int64, ctypes.c_double, ctypes.c_float, ctypes.c_int
         _lib.og_render.restype = i64
         _lib.og_render.argtypes = [P, i64, P, P, P, P, f64, f64, i32, i32, i32, f64, i32,
-                                   P, P, P, P]
+                                   P, P, P, P, P]
         _lib.og_render_grad.restype = i64
         _lib.og_render_grad.argtypes = [P, i64, P, P, P, P, f64, f64, i32, i32, i32, i32,
                                         P, P, P]
@@ -143,10 +143,10 @@ def signal_proxy(T1, T2, TR: float, TE: float) -> np.ndarray:
 def render(params, grid: Grid, cfg: Config = Config(), crop=None, amb_tol=None, prune=True):
     """Eq. 3-4 with the Sec. 3.3 truncation, brute force in FP64.
 
-    Returns dict(I, W, S, amb, n_invalid), each volume crop-shaped ``[z, y, x]``. ``amb``
-    counts, per voxel, the pairs whose d^2 lies within ``amb_tol`` of sigma_t^2 (default
-    1e-4 sigma_t^2): their inclusion is decided by rounding, so parity tests compare only
-    voxels with ``amb == 0``.
+    Returns dict(I, W, S, amb, npair, n_invalid), each volume crop-shaped ``[z, y, x]``.
+    ``amb`` counts, per voxel, the pairs whose d^2 lies within ``amb_tol`` of sigma_t^2
+    (default 1e-4 sigma_t^2): their inclusion is decided by rounding, so parity tests compare
+    only voxels with ``amb == 0``. ``npair`` counts the contributing pairs per voxel.
     """
     p = np.ascontiguousarray(params, dtype=np.float64).reshape(-1, 12)
     dims, h, o = _grid_arrays(grid)
@@ -157,13 +157,15 @@ def render(params, grid: Grid, cfg: Config = Config(), crop=None, amb_tol=None, 
     W = np.zeros(shape, np.float64)
     S = np.zeros(shape, np.float64)
     amb = np.zeros(shape, np.int32)
+    npair = np.zeros(shape, np.int32)
     n_bad = lib().og_render(_ptr(p), p.shape[0], _ptr(dims), _ptr(h), _ptr(o),
                             None if carr is None else _ptr(carr), cfg.trunc_sigma, cfg.eps,
                             cfg.signal_mode, cfg.a_act, cfg.t_act, float(amb_tol),
-                            1 if prune else 0, _ptr(I), _ptr(W), _ptr(S), _ptr(amb))
+                            1 if prune else 0, _ptr(I), _ptr(W), _ptr(S), _ptr(amb),
+                            _ptr(npair))
     if n_bad < 0:
         raise MemoryError("oracle render: allocation failed")
-    return dict(I=I, W=W, S=S, amb=amb, n_invalid=int(n_bad))
+    return dict(I=I, W=W, S=S, amb=amb, npair=npair, n_invalid=int(n_bad))
 
 
 def render_grad(params, grid: Grid, dI, cfg: Config = Config(), crop=None, prune=True,
@@ -234,21 +236,21 @@ def brick_lists(params, grid: Grid, cfg: Config = Config()):
     rng = brick_ranges_fp32(params, grid, cfg)
     nbx, nby, nbz = brick_grid(grid, cfg)
     nb = nbx * nby * nbz
-    gm_brick = []
-    counts = np.zeros(rng.shape[0], np.int64)
-    for g in range(rng.shape[0]):
-        lo, hi, ok = rng[g, :3], rng[g, 3:6], rng[g, 6]
-        if not ok:
-            continue
-        zz, yy, xx = np.meshgrid(np.arange(lo[2], hi[2] + 1), np.arange(lo[1], hi[1] + 1),
-                                 np.arange(lo[0], hi[0] + 1), indexing="ij")
-        b = ((zz * nby + yy) * nbx + xx).ravel()
-        gm_brick.append(b)
-        counts[g] = b.size
-    gm_brick = np.concatenate(gm_brick) if gm_brick else np.zeros(0, np.int64)
+    lo = rng[:, :3].astype(np.int64)
+    ok = rng[:, 6] == 1
+    ext = np.where(ok[:, None], rng[:, 3:6].astype(np.int64) - lo + 1, 0)
+    counts = ext.prod(axis=1)
     gm_off = np.zeros(rng.shape[0] + 1, np.int64)
     gm_off[1:] = np.cumsum(counts)
     gm_gid = np.repeat(np.arange(rng.shape[0]), counts)
+    # Local index t of each pair inside its Gaussian's brick box, x fastest, so that the
+    # bricks of one Gaussian come in ascending linear brick index.
+    t = np.arange(gm_off[-1], dtype=np.int64) - gm_off[gm_gid]
+    ex, ey = ext[gm_gid, 0], ext[gm_gid, 1]
+    bx = lo[gm_gid, 0] + t % ex
+    by = lo[gm_gid, 1] + (t // ex) % ey
+    bz = lo[gm_gid, 2] + t // (ex * ey)
+    gm_brick = (bz * nby + by) * nbx + bx
     order = np.argsort(gm_brick, kind="stable")
     pair_gid = gm_gid[order]
     per_brick = np.bincount(gm_brick, minlength=nb) if gm_brick.size else np.zeros(nb, np.int64)
@@ -353,19 +355,17 @@ def trilinear(vol, grid_lr: Grid, pts) -> np.ndarray:
     i0 = np.floor(u).astype(np.int64)
     i1 = np.minimum(i0 + 1, np.array(n) - 1)
     f = u - i0
-    for m in range(pts.shape[0]):
-        acc = 0.0
-        for cz in (0, 1):
-            for cy in (0, 1):
-                for cx in (0, 1):
-                    wx = f[m, 0] if cx else 1.0 - f[m, 0]
-                    wy = f[m, 1] if cy else 1.0 - f[m, 1]
-                    wz = f[m, 2] if cz else 1.0 - f[m, 2]
-                    xi = i1[m, 0] if cx else i0[m, 0]
-                    yi = i1[m, 1] if cy else i0[m, 1]
-                    zi = i1[m, 2] if cz else i0[m, 2]
-                    acc += wx * wy * wz * vol[zi, yi, xi]
-        out[m] = acc
+    out[:] = 0.0
+    for cz in (0, 1):
+        for cy in (0, 1):
+            for cx in (0, 1):
+                wx = f[:, 0] if cx else 1.0 - f[:, 0]
+                wy = f[:, 1] if cy else 1.0 - f[:, 1]
+                wz = f[:, 2] if cz else 1.0 - f[:, 2]
+                xi = i1[:, 0] if cx else i0[:, 0]
+                yi = i1[:, 1] if cy else i0[:, 1]
+                zi = i1[:, 2] if cz else i0[:, 2]
+                out += wx * wy * wz * vol[zi, yi, xi]
     return out
 
 
@@ -440,3 +440,21 @@ def ssim3d(x, ref, data_range: float = 1.0, sigma: float = 1.5) -> float:
     num = (2 * mx * my + c1) * (2 * sxy + c2)
     den = (mx * mx + my * my + c1) * (sxx + syy + c2)
     return float(np.mean(num / den))
+
+
+# ------------------------------------------------------------------- fitting step
+
+def fit_step(params, lr_target, grid: Grid, s: int, cfg: Config, m, v, step: int,
+             acfg: AdamConfig = AdamConfig()):
+    """One zero-shot fitting iteration, composed of the pinned pieces above: render
+    (Eq. 3-4), z box slice profile, L1 against the LR scan, adjoint slice profile, adjoint
+    render (Eq. 5-6 and the chain), Adam. Returns dict(loss, grad, params, m, v, I, lr_pred)."""
+    p = np.asarray(params, np.float64)
+    r = render(p, grid, cfg)
+    lr_pred = downsample(r["I"], s)
+    loss, dlr = l1_loss(lr_pred, lr_target)
+    dI = downsample_adjoint(dlr, grid.nz, s)
+    grad = render_grad(p, grid, dI, cfg)
+    p2, m2, v2 = adam_step(p, grad, m, v, step, acfg)
+    return dict(loss=loss, grad=grad, params=p2, m=m2, v=v2, I=r["I"], lr_pred=lr_pred,
+                amb=r["amb"])

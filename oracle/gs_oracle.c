@@ -181,13 +181,14 @@ static double og_d2(const og_gauss* g, const double d[3]) {
  * Outputs are crop-shaped, z-major, x fastest:
  *   S = sum_i v_i w_i, W = sum_i w_i, I = S / max(W, eps),
  *   amb = number of pairs with |d^2 - sigma_t^2| <= amb_tol (their inclusion depends on
- *         rounding at the truncation boundary; tests compare only voxels with amb == 0).
+ *         rounding at the truncation boundary; tests compare only voxels with amb == 0),
+ *   npair (optional) = number of contributing pairs (d^2 <= sigma_t^2) per voxel.
  * Returns the number of invalid Gaussians.
  */
 int64_t og_render(const double* params, int64_t N, const int32_t dims[3], const double h[3],
                   const double origin[3], const int32_t* crop, double sigma_t, double eps,
                   int signal_mode, int a_act, int t_act, double amb_tol, int prune, double* I,
-                  double* W, double* S, int32_t* amb) {
+                  double* W, double* S, int32_t* amb, int32_t* npair) {
     int32_t c[6] = {0, dims[0], 0, dims[1], 0, dims[2]};
     if (crop) memcpy(c, crop, sizeof(c));
     const int64_t cx = c[1] - c[0], cy = c[3] - c[2], cz = c[5] - c[4];
@@ -206,10 +207,12 @@ int64_t og_render(const double* params, int64_t N, const int32_t dims[3], const 
         double* Sz = S + zz * cy * cx;
         double* Wz = W + zz * cy * cx;
         int32_t* Az = amb + zz * cy * cx;
+        int32_t* Nz = npair ? npair + zz * cy * cx : NULL;
         for (int64_t k = 0; k < cy * cx; ++k) {
             Sz[k] = 0.0;
             Wz[k] = 0.0;
             Az[k] = 0;
+            if (Nz) Nz[k] = 0;
         }
         const double pz = origin[2] + (z + 0.5) * h[2];
         for (int64_t i = 0; i < N; ++i) {
@@ -231,6 +234,7 @@ int64_t og_render(const double* params, int64_t N, const int32_t dims[3], const 
                         double w = exp(-0.5 * d2) * g->r;
                         Sz[idx] += g->v * w;
                         Wz[idx] += w;
+                        if (Nz) Nz[idx] += 1;
                     }
                 }
             }
@@ -266,7 +270,7 @@ int64_t og_render_grad(const double* params, int64_t N, const int32_t dims[3], c
     int32_t* amb = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nv > 0 ? nv : 1));
     if (!I || !W || !S || !amb) return -1;
     int64_t n_invalid = og_render(params, N, dims, h, origin, crop, sigma_t, eps, signal_mode,
-                                  a_act, t_act, 0.0, prune, I, W, S, amb);
+                                  a_act, t_act, 0.0, prune, I, W, S, amb, NULL);
     og_gauss* G = og_activate_all(params, N, dims, h, origin, sigma_t, 0.0, signal_mode, a_act,
                                   t_act, prune);
     const double s2 = sigma_t * sigma_t;

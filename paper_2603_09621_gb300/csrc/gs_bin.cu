@@ -1,0 +1,649 @@
+// gs_bin.cu -- Sec. 3.3 brick intersection and binning: per-Gaussian activation and bounds,
+// per-brick Gaussian lists built by count / exclusive scan / stable radix scatter.
+//
+// Pipeline of gs_bin_bricks (all asynchronous on one stream):
+//   k_preprocess   one thread per Gaussian: validity, FP32 brick range (fixed operation order,
+//                  bit-exact against the oracle's binning specification), render record.
+//   scan           exclusive scan of per-Gaussian pair counts -> gm_off, total -> d_npairs.
+//   k_capacity     flags GS_STATUS_CAPACITY when the total exceeds the bins' capacity.
+//   k_emit         Gaussian-major pair emission (brick key, owner) + per-brick counts.
+//   scan           exclusive scan of per-brick counts -> brick_off.
+//   radix passes   stable LSD radix sort of the brick keys, 8 bits per pass: per-tile digit
+//                  histograms, a digit-major scan, and a stable scatter whose in-tile ranks
+//                  come from warp match masks. Stability keeps ascending Gaussian ids inside
+//                  each brick, so the lists are deterministic.
+//   k_finalize     pair_gmj (Gaussian-major position) and pair_gid (owner) per brick-major pair.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "gs_common.cuh"
+
+namespace gs {
+
+// ============================================================================ validation
+
+gs_status validate_grid_cfg(const gs_grid* g, const gs_config* c) {
+    if (!g || !c) return GS_ERR_INVALID_ARG;
+    if (g->nx <= 0 || g->ny <= 0 || g->nz <= 0) return GS_ERR_INVALID_ARG;
+    if (int64_t(g->nx) * g->ny * g->nz > (int64_t(1) << 31) - 1) return GS_ERR_INVALID_ARG;
+    for (int k = 0; k < 3; ++k) {
+        if (!(g->h[k] > 0.0f) || !isfinite(g->h[k]) || !isfinite(g->origin[k]))
+            return GS_ERR_INVALID_ARG;
+        if (c->brick[k] <= 0 || c->brick[k] % 4 != 0) return GS_ERR_INVALID_ARG;
+    }
+    if (c->brick[0] * c->brick[1] * c->brick[2] > 1024) return GS_ERR_INVALID_ARG;
+    if (!(c->trunc_sigma > 0.0f) || !isfinite(c->trunc_sigma)) return GS_ERR_INVALID_ARG;
+    if (!(c->eps > 0.0f)) return GS_ERR_INVALID_ARG;
+    if (c->signal_mode != 0 && c->signal_mode != 1) return GS_ERR_INVALID_ARG;
+    if ((c->a_act != 0 && c->a_act != 1) || (c->t_act != 0 && c->t_act != 1))
+        return GS_ERR_INVALID_ARG;
+    BrickGeom b = brick_geom(g, c);
+    if (int64_t(b.nbx) * b.nby * b.nbz > (int64_t(1) << 30)) return GS_ERR_INVALID_ARG;
+    return GS_OK;
+}
+
+// ============================================================================ scan
+
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_scan(T x, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the exclusive prefix and the
+// block total. smem must hold 32 values. Ends with a barrier (smem reusable afterwards).
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T* smem, T* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    T inc = warp_inclusive_scan(v, lane);
+    if (lane == 31) smem[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        T s = lane < nwarps ? smem[lane] : T(0);
+        s = warp_inclusive_scan(s, lane);
+        smem[lane] = s;
+    }
+    __syncthreads();
+    T prefix = (warp > 0 ? smem[warp - 1] : T(0)) + inc - v;
+    *total = smem[nwarps - 1];
+    __syncthreads();
+    return prefix;
+}
+
+// Per-block sums (64-bit) of kScanTile consecutive values.
+template <typename Tin>
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const Tin* __restrict__ in, int64_t n,
+                                                              long long* __restrict__ sums) {
+    __shared__ long long sm[32];
+    const int64_t base = int64_t(blockIdx.x) * kScanTile + int64_t(threadIdx.x) * kScanItems;
+    long long s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i)
+        if (base + i < n) s += static_cast<long long>(in[base + i]);
+    long long tot;
+    block_exclusive_scan(s, sm, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// Exclusive scan of each block, offset by the scanned block sums (nullptr: single block).
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const Tin* __restrict__ in, Tout* out,
+                                                            int64_t n, const long long* __restrict__ offs,
+                                                            long long* total) {
+    __shared__ long long sm[32];
+    const int64_t base = int64_t(blockIdx.x) * kScanTile + int64_t(threadIdx.x) * kScanItems;
+    long long vals[kScanItems];
+    long long s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        vals[i] = (base + i < n) ? static_cast<long long>(in[base + i]) : 0;
+        s += vals[i];
+    }
+    long long tot;
+    long long run = block_exclusive_scan(s, sm, &tot);
+    if (offs) run += offs[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < n) out[base + i] = static_cast<Tout>(run);
+        run += vals[i];
+    }
+    if (total && blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) *total = run;
+}
+
+template <typename Tin, typename Tout>
+static gs_status scan_rec(const Tin* in, Tout* out, int64_t n, long long* total, long long* tmp,
+                          int64_t tmp_len, cudaStream_t st) {
+    if (n <= 0) return GS_OK;
+    if (n <= kScanTile) {
+        k_scan_down<Tin, Tout><<<1, kScanThreads, 0, st>>>(in, out, n, nullptr, total);
+        return last_launch_status();
+    }
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb + 1 > tmp_len) return GS_ERR_WORKSPACE;
+    long long* sums = tmp;
+    k_scan_reduce<Tin><<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, n, sums);
+    gs_status s = last_launch_status();
+    if (s != GS_OK) return s;
+    // Scan the block sums in place (64-bit), recursively.
+    s = scan_rec<long long, long long>(sums, sums, nb, nullptr, tmp + nb + 1, tmp_len - nb - 1, st);
+    if (s != GS_OK) return s;
+    k_scan_down<Tin, Tout><<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, out, n, sums, total);
+    return last_launch_status();
+}
+
+gs_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, long long* total,
+                             long long* tmp, int64_t tmp_len, cudaStream_t stream) {
+    return scan_rec<int32_t, int32_t>(in, out, n, total, tmp, tmp_len, stream);
+}
+
+// ============================================================================ preprocess
+
+struct GridF {
+    int n[3];
+    float h[3];
+    float o[3];
+    double hd[3];
+    double od[3];
+    int b[3];
+    int nb[3];
+};
+
+__global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ params, int64_t N, GridF G,
+                                                    float trunc_sigma, int signal_mode, int a_act,
+                                                    int t_act, float* __restrict__ rec,
+                                                    int32_t* __restrict__ brange,
+                                                    int32_t* __restrict__ gm_cnt,
+                                                    int32_t* __restrict__ status) {
+    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= N) return;
+    const float4* p4 = reinterpret_cast<const float4*>(params + g * 12);
+    float4 a0 = p4[0], a1 = p4[1], a2 = p4[2];
+    float p[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
+    int32_t* br = brange + g * 8;
+    float4* r4 = reinterpret_cast<float4*>(rec + g * REC_FLOATS);
+
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) ok = ok && isfinite(p[k]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ok = ok && (fabsf(p[3 + k]) <= 30.0f);
+    float nn = __fmul_rn(p[6], p[6]);
+    nn = __fadd_rn(nn, __fmul_rn(p[7], p[7]));
+    nn = __fadd_rn(nn, __fmul_rn(p[8], p[8]));
+    nn = __fadd_rn(nn, __fmul_rn(p[9], p[9]));
+    ok = ok && (nn > 0.0f);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!ok) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) br[k] = 0;
+        gm_cnt[g] = 0;
+        r4[0] = z4; r4[1] = z4; r4[2] = z4; r4[3] = z4;
+        atomicOr(status, GS_STATUS_NONFINITE);
+        return;
+    }
+
+    // ---- binning specification (FP32, explicit rounding, fixed order) ----
+    float s[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) s[k] = exp_cw(p[3 + k]);
+    const float n = __fsqrt_rn(nn);
+    const float w = __fdiv_rn(p[6], n), x = __fdiv_rn(p[7], n);
+    const float y = __fdiv_rn(p[8], n), z = __fdiv_rn(p[9], n);
+    const float xx = __fmul_rn(x, x), yy = __fmul_rn(y, y), zz = __fmul_rn(z, z);
+    const float xy = __fmul_rn(x, y), xz = __fmul_rn(x, z), yz = __fmul_rn(y, z);
+    const float wx = __fmul_rn(w, x), wy = __fmul_rn(w, y), wz = __fmul_rn(w, z);
+    float R[3][3];
+    R[0][0] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(yy, zz)));
+    R[0][1] = __fmul_rn(2.0f, __fsub_rn(xy, wz));
+    R[0][2] = __fmul_rn(2.0f, __fadd_rn(xz, wy));
+    R[1][0] = __fmul_rn(2.0f, __fadd_rn(xy, wz));
+    R[1][1] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(xx, zz)));
+    R[1][2] = __fmul_rn(2.0f, __fsub_rn(yz, wx));
+    R[2][0] = __fmul_rn(2.0f, __fsub_rn(xz, wy));
+    R[2][1] = __fmul_rn(2.0f, __fadd_rn(yz, wx));
+    R[2][2] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(xx, yy)));
+    const float ksig = __fmul_rn(trunc_sigma, 1.0001220703125f);
+    int lo[3], hi[3];
+    bool inside = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float m0 = __fmul_rn(R[k][0], s[0]), m1 = __fmul_rn(R[k][1], s[1]);
+        float m2 = __fmul_rn(R[k][2], s[2]);
+        float sig = __fmul_rn(m0, m0);
+        sig = __fadd_rn(sig, __fmul_rn(m1, m1));
+        sig = __fadd_rn(sig, __fmul_rn(m2, m2));
+        float e = __fmul_rn(ksig, __fsqrt_rn(sig));
+        float lo_f = __fsub_rn(__fsub_rn(__fdiv_rn(__fsub_rn(__fsub_rn(p[k], e), G.o[k]), G.h[k]), 0.5f),
+                               0.00390625f);
+        float hi_f = __fadd_rn(__fsub_rn(__fdiv_rn(__fsub_rn(__fadd_rn(p[k], e), G.o[k]), G.h[k]), 0.5f),
+                               0.00390625f);
+        float nmax = static_cast<float>(G.n[k] - 1);
+        if (!(hi_f >= 0.0f) || !(lo_f <= nmax)) {
+            inside = false;
+        } else {
+            float lc = ceilf(lo_f), hc = floorf(hi_f);
+            lc = fmaxf(lc, 0.0f);
+            hc = fminf(hc, nmax);
+            if (lc > hc) inside = false;
+            lo[k] = static_cast<int>(lc);
+            hi[k] = static_cast<int>(hc);
+        }
+    }
+    int cnt = 0;
+    if (inside) {
+        int b0[3], b1[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            b0[k] = lo[k] / G.b[k];
+            b1[k] = hi[k] / G.b[k];
+            br[k] = b0[k];
+            br[3 + k] = b1[k];
+        }
+        cnt = (b1[0] - b0[0] + 1) * (b1[1] - b0[1] + 1) * (b1[2] - b0[2] + 1);
+        br[B_CNT] = cnt;
+        br[B_VALID] = 1;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) br[k] = 0;
+        br[B_VALID] = 1;
+    }
+    gm_cnt[g] = cnt;
+
+    // ---- render record (accuracy only; contraction allowed) ----
+    float inv_s2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) inv_s2[k] = 1.0f / (s[k] * s[k]);
+    float C[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            C[a][b] = R[a][0] * R[b][0] * inv_s2[0] + R[a][1] * R[b][1] * inv_s2[1] +
+                      R[a][2] * R[b][2] * inv_s2[2];
+    const float kq = -kHalfLog2e;
+    float Qxx = kq * G.h[0] * G.h[0] * C[0][0];
+    float Qyy = kq * G.h[1] * G.h[1] * C[1][1];
+    float Qzz = kq * G.h[2] * G.h[2] * C[2][2];
+    float Q2xy = 2.0f * kq * G.h[0] * G.h[1] * C[0][1];
+    float Q2xz = 2.0f * kq * G.h[0] * G.h[2] * C[0][2];
+    float Q2yz = 2.0f * kq * G.h[1] * G.h[2] * C[1][2];
+    float mh[3], ml[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double m = (static_cast<double>(p[k]) - G.od[k]) / G.hd[k] - 0.5;
+        mh[k] = static_cast<float>(m);
+        ml[k] = static_cast<float>(m - static_cast<double>(mh[k]));
+    }
+    float A = a_act ? sigmoidf_(p[10]) : p[10];
+    float T = t_act ? sigmoidf_(p[11]) : p[11];
+    float v, r;
+    if (signal_mode == 0) {
+        v = A;
+        r = T;
+    } else {
+        v = A * T;
+        r = 1.0f;
+    }
+    r4[0] = make_float4(mh[0], mh[1], mh[2], ml[0]);
+    r4[1] = make_float4(ml[1], ml[2], Qxx, Qyy);
+    r4[2] = make_float4(Qzz, Q2xy, Q2xz, Q2yz);
+    r4[3] = make_float4(v * r, r, v, 0.0f);
+}
+
+// ============================================================================ capacity / emit
+
+__global__ void k_capacity(const long long* __restrict__ total, int64_t capacity,
+                           int64_t* __restrict__ npairs, int32_t* __restrict__ status) {
+    long long t = *total;
+    *npairs = t;
+    if (t > capacity) atomicOr(status, GS_STATUS_CAPACITY);
+}
+
+__device__ __forceinline__ int64_t valid_pairs(const int64_t* npairs, int64_t capacity) {
+    int64_t P = *npairs;
+    return (P > capacity || P < 0) ? 0 : P;
+}
+
+__global__ void __launch_bounds__(256) k_emit(const int32_t* __restrict__ brange,
+                                              const int32_t* __restrict__ gm_off, int64_t N, int nbx,
+                                              int nby, const int64_t* __restrict__ npairs,
+                                              int64_t capacity, int32_t* __restrict__ keys,
+                                              int32_t* __restrict__ gm_gid,
+                                              int32_t* __restrict__ brick_cnt) {
+    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= N) return;
+    if (valid_pairs(npairs, capacity) == 0) return;
+    const int32_t* br = brange + g * 8;
+    if (br[B_CNT] == 0) return;
+    int j = gm_off[g];
+    for (int bz = br[B_LOZ]; bz <= br[B_HIZ]; ++bz)
+        for (int by = br[B_LOY]; by <= br[B_HIY]; ++by)
+            for (int bx = br[B_LOX]; bx <= br[B_HIX]; ++bx) {
+                int b = (bz * nby + by) * nbx + bx;
+                keys[j] = b;
+                gm_gid[j] = static_cast<int32_t>(g);
+                atomicAdd(&brick_cnt[b], 1);
+                ++j;
+            }
+}
+
+// ============================================================================ radix sort
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const int32_t* __restrict__ keys,
+                                                            const int64_t* __restrict__ npairs,
+                                                            int64_t capacity, int shift, int n_tiles,
+                                                            int32_t* __restrict__ hist) {
+    __shared__ int cnt[kRadix];
+    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    const int64_t P = valid_pairs(npairs, capacity);
+    const int64_t base = int64_t(blockIdx.x) * kSortTile;
+    for (int i = threadIdx.x; i < kSortTile; i += blockDim.x) {
+        int64_t idx = base + i;
+        if (idx < P) atomicAdd(&cnt[(keys[idx] >> shift) & (kRadix - 1)], 1);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
+        hist[int64_t(d) * n_tiles + blockIdx.x] = cnt[d];
+}
+
+// Stable scatter of one tile. Items are visited in kSortItems rounds of kSortThreads
+// consecutive keys; the rank of an item among equal digits is (items of that digit in
+// earlier rounds) + (in earlier warps of this round) + (in lower lanes of its warp).
+template <bool kFirst>
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+    const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in,
+    int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out,
+    const int32_t* __restrict__ hist_off, const int64_t* __restrict__ npairs, int64_t capacity,
+    int shift, int n_tiles) {
+    constexpr int kWarps = kSortThreads / 32;
+    __shared__ int base[kRadix];
+    __shared__ int wcnt[kWarps][kRadix];
+    __shared__ int tot[kRadix];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int d = tid; d < kRadix; d += kSortThreads) {
+        base[d] = hist_off[int64_t(d) * n_tiles + blockIdx.x];
+        for (int w = 0; w < kWarps; ++w) wcnt[w][d] = 0;
+    }
+    __syncthreads();
+    const int64_t P = valid_pairs(npairs, capacity);
+    const int64_t tile0 = int64_t(blockIdx.x) * kSortTile;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int r = 0; r < kSortItems; ++r) {
+        const int64_t idx = tile0 + int64_t(r) * kSortThreads + tid;
+        const bool valid = idx < P;
+        int key = 0, val = 0, d = 0;
+        if (valid) {
+            key = keys_in[idx];
+            val = kFirst ? static_cast<int>(idx) : vals_in[idx];
+            d = (key >> shift) & (kRadix - 1);
+        }
+        // Invalid lanes get a unique tag outside the digit range so they match nobody.
+        const unsigned tag = valid ? static_cast<unsigned>(d) : static_cast<unsigned>(kRadix + lane);
+        const unsigned peers = __match_any_sync(0xffffffffu, tag);
+        const int rank = __popc(peers & lt_mask);
+        const int leader = __ffs(peers) - 1;
+        if (valid && lane == leader) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        for (int dd = tid; dd < kRadix; dd += kSortThreads) {
+            int run = 0;
+            for (int w = 0; w < kWarps; ++w) {
+                int c = wcnt[w][dd];
+                wcnt[w][dd] = run;
+                run += c;
+            }
+            tot[dd] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            const int pos = base[d] + wcnt[warp][d] + rank;
+            keys_out[pos] = key;
+            vals_out[pos] = val;
+        }
+        __syncthreads();
+        for (int dd = tid; dd < kRadix; dd += kSortThreads) {
+            base[dd] += tot[dd];
+            for (int w = 0; w < kWarps; ++w) wcnt[w][dd] = 0;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_finalize(const int32_t* __restrict__ vals,
+                                                  const int32_t* __restrict__ gm_gid,
+                                                  const int64_t* __restrict__ npairs, int64_t capacity,
+                                                  int32_t* __restrict__ pair_gmj,
+                                                  int32_t* __restrict__ pair_gid) {
+    const int64_t P = valid_pairs(npairs, capacity);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        int j = vals[i];
+        pair_gmj[i] = j;
+        pair_gid[i] = gm_gid[j];
+    }
+}
+
+}  // namespace gs
+
+// ============================================================================ C ABI
+
+using namespace gs;
+
+namespace {
+
+struct BinsLayout {
+    size_t off_brick_off, off_pair_gid, off_pair_gmj, off_gm_off, off_rec, off_brange, off_npairs,
+        off_status, bytes;
+};
+
+bool bins_layout(int64_t n_gauss, int64_t capacity, int32_t n_bricks, BinsLayout* L) {
+    if (n_gauss < 0 || capacity < 0 || capacity > kMaxCapacity || n_bricks <= 0) return false;
+    if (n_gauss > (int64_t(1) << 31) - 2) return false;
+    const int64_t cap = capacity > 0 ? capacity : 1;
+    const int64_t n = n_gauss > 0 ? n_gauss : 1;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    L->off_brick_off = take(sizeof(int32_t) * (int64_t(n_bricks) + 1));
+    L->off_pair_gid = take(sizeof(int32_t) * cap);
+    L->off_pair_gmj = take(sizeof(int32_t) * cap);
+    L->off_gm_off = take(sizeof(int32_t) * (n + 1));
+    L->off_rec = take(sizeof(float) * REC_FLOATS * n);
+    L->off_brange = take(sizeof(int32_t) * 8 * n);
+    L->off_npairs = take(sizeof(int64_t));
+    L->off_status = take(sizeof(int32_t));
+    L->bytes = off;
+    return true;
+}
+
+int32_t n_bricks_of(const gs_grid* g, const gs_config* c) {
+    BrickGeom b = brick_geom(g, c);
+    return b.nbx * b.nby * b.nbz;
+}
+
+}  // namespace
+
+extern "C" size_t gs_bins_bytes(int64_t n_gauss, int64_t capacity, const gs_grid* grid,
+                                const gs_config* cfg) {
+    if (validate_grid_cfg(grid, cfg) != GS_OK) return 0;
+    BinsLayout L;
+    if (!bins_layout(n_gauss, capacity, n_bricks_of(grid, cfg), &L)) return 0;
+    return L.bytes;
+}
+
+extern "C" gs_status gs_bins_bind(void* arena, size_t arena_bytes, int64_t n_gauss,
+                                  int64_t capacity, const gs_grid* grid, const gs_config* cfg,
+                                  gs_bins* out) {
+    if (!arena || !out) return GS_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(arena) % 256 != 0) return GS_ERR_INVALID_ARG;
+    gs_status s = validate_grid_cfg(grid, cfg);
+    if (s != GS_OK) return s;
+    BinsLayout L;
+    const int32_t nb = n_bricks_of(grid, cfg);
+    if (!bins_layout(n_gauss, capacity, nb, &L)) return GS_ERR_INVALID_ARG;
+    if (arena_bytes < L.bytes) return GS_ERR_WORKSPACE;
+    char* a = static_cast<char*>(arena);
+    BrickGeom b = brick_geom(grid, cfg);
+    out->n_gauss = n_gauss;
+    out->capacity = capacity;
+    out->n_bricks = nb;
+    out->nbx = b.nbx;
+    out->nby = b.nby;
+    out->nbz = b.nbz;
+    out->brick_off = reinterpret_cast<int32_t*>(a + L.off_brick_off);
+    out->pair_gid = reinterpret_cast<int32_t*>(a + L.off_pair_gid);
+    out->pair_gmj = reinterpret_cast<int32_t*>(a + L.off_pair_gmj);
+    out->gm_off = reinterpret_cast<int32_t*>(a + L.off_gm_off);
+    out->rec = reinterpret_cast<float*>(a + L.off_rec);
+    out->brange = reinterpret_cast<int32_t*>(a + L.off_brange);
+    out->d_npairs = reinterpret_cast<int64_t*>(a + L.off_npairs);
+    out->d_status = reinterpret_cast<int32_t*>(a + L.off_status);
+    return GS_OK;
+}
+
+extern "C" size_t gs_workspace_bytes(int64_t n_gauss, int64_t capacity, const gs_grid* grid,
+                                     const gs_config* cfg) {
+    if (validate_grid_cfg(grid, cfg) != GS_OK) return 0;
+    if (n_gauss < 0 || capacity < 0 || capacity > kMaxCapacity) return 0;
+    Workspace ws;
+    carve_workspace(nullptr, n_gauss, capacity, n_bricks_of(grid, cfg), cfg->deterministic != 0,
+                    &ws);
+    return ws.bytes;
+}
+
+namespace gs {
+// Shared by the other translation units: bind the workspace for a problem size.
+gs_status bind_workspace(void* base, size_t bytes, int64_t n_gauss, int64_t capacity,
+                         const gs_grid* grid, const gs_config* cfg, Workspace* ws) {
+    if (!base) return GS_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(base) % 256 != 0) return GS_ERR_INVALID_ARG;
+    carve_workspace(nullptr, n_gauss, capacity, n_bricks_of(grid, cfg), cfg->deterministic != 0, ws);
+    if (bytes < ws->bytes) return GS_ERR_WORKSPACE;
+    carve_workspace(base, n_gauss, capacity, n_bricks_of(grid, cfg), cfg->deterministic != 0, ws);
+    return GS_OK;
+}
+
+bool bins_match(const gs_bins* b, const gs_grid* grid, const gs_config* cfg) {
+    if (!b || !b->brick_off || !b->pair_gid || !b->pair_gmj || !b->gm_off || !b->rec ||
+        !b->brange || !b->d_npairs || !b->d_status)
+        return false;
+    BrickGeom g = brick_geom(grid, cfg);
+    return b->nbx == g.nbx && b->nby == g.nby && b->nbz == g.nbz &&
+           b->n_bricks == g.nbx * g.nby * g.nbz && b->capacity >= 0 &&
+           b->capacity <= kMaxCapacity && b->n_gauss >= 0;
+}
+
+static int radix_passes(int32_t n_bricks) {
+    int bits = 0;
+    while ((int64_t(1) << bits) < n_bricks) ++bits;
+    int passes = (bits + kRadixBits - 1) / kRadixBits;
+    return passes < 1 ? 1 : passes;
+}
+
+gs_status bin_bricks_impl(const float* params, const gs_grid* grid, const gs_config* cfg,
+                          gs_bins* bins, const Workspace& ws, cudaStream_t st) {
+    const int64_t N = bins->n_gauss;
+    const int64_t cap = bins->capacity;
+    BrickGeom b = brick_geom(grid, cfg);
+    GridF G;
+    G.n[0] = grid->nx; G.n[1] = grid->ny; G.n[2] = grid->nz;
+    for (int k = 0; k < 3; ++k) {
+        G.h[k] = grid->h[k];
+        G.o[k] = grid->origin[k];
+        G.hd[k] = grid->h[k];
+        G.od[k] = grid->origin[k];
+    }
+    G.b[0] = b.bx; G.b[1] = b.by; G.b[2] = b.bz;
+    G.nb[0] = b.nbx; G.nb[1] = b.nby; G.nb[2] = b.nbz;
+
+    if (cudaMemsetAsync(bins->d_status, 0, sizeof(int32_t), st) != cudaSuccess) return GS_ERR_CUDA;
+    if (cudaMemsetAsync(ws.brick_cnt, 0, sizeof(int32_t) * (int64_t(bins->n_bricks) + 1), st) !=
+        cudaSuccess)
+        return GS_ERR_CUDA;
+    long long* total = ws.scan_tmp + ws.scan_tmp_len - 1;
+    if (N > 0) {
+        const unsigned gb = static_cast<unsigned>((N + 255) / 256);
+        k_preprocess<<<gb, 256, 0, st>>>(params, N, G, cfg->trunc_sigma, cfg->signal_mode,
+                                         cfg->a_act, cfg->t_act, bins->rec, bins->brange, ws.gm_cnt,
+                                         bins->d_status);
+        gs_status s = last_launch_status();
+        if (s != GS_OK) return s;
+        // gm_off = exclusive scan of counts (N + 1 entries; gm_cnt[N] = 0 sentinel).
+        if (cudaMemsetAsync(ws.gm_cnt + N, 0, sizeof(int32_t), st) != cudaSuccess) return GS_ERR_CUDA;
+        s = exclusive_scan_i32(ws.gm_cnt, bins->gm_off, N + 1, total, ws.scan_tmp,
+                               ws.scan_tmp_len - 1, st);
+        if (s != GS_OK) return s;
+    } else {
+        if (cudaMemsetAsync(total, 0, sizeof(long long), st) != cudaSuccess) return GS_ERR_CUDA;
+        if (cudaMemsetAsync(bins->gm_off, 0, sizeof(int32_t), st) != cudaSuccess) return GS_ERR_CUDA;
+    }
+    k_capacity<<<1, 1, 0, st>>>(total, cap, bins->d_npairs, bins->d_status);
+    gs_status s = last_launch_status();
+    if (s != GS_OK) return s;
+    if (N > 0) {
+        k_emit<<<static_cast<unsigned>((N + 255) / 256), 256, 0, st>>>(
+            bins->brange, bins->gm_off, N, b.nbx, b.nby, bins->d_npairs, cap, ws.keys0, ws.gm_gid,
+            ws.brick_cnt);
+        s = last_launch_status();
+        if (s != GS_OK) return s;
+    }
+    s = exclusive_scan_i32(ws.brick_cnt, bins->brick_off, int64_t(bins->n_bricks) + 1, nullptr,
+                           ws.scan_tmp, ws.scan_tmp_len - 1, st);
+    if (s != GS_OK) return s;
+    if (cap == 0) return GS_OK;
+
+    // Stable LSD radix sort of brick keys; values are Gaussian-major positions.
+    const int passes = radix_passes(bins->n_bricks);
+    int32_t* kin = ws.keys0;
+    int32_t* vin = ws.vals0;
+    int32_t* kout = ws.keys1;
+    int32_t* vout = ws.vals1;
+    const int nt = ws.n_tiles;
+    const int64_t hist_len = int64_t(kRadix) * nt;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = pass * kRadixBits;
+        k_radix_hist<<<nt, kSortThreads, 0, st>>>(kin, bins->d_npairs, cap, shift, nt, ws.hist);
+        s = last_launch_status();
+        if (s != GS_OK) return s;
+        s = exclusive_scan_i32(ws.hist, ws.hist, hist_len, nullptr, ws.scan_tmp, ws.scan_tmp_len - 1, st);
+        if (s != GS_OK) return s;
+        if (pass == 0)
+            k_radix_scatter<true><<<nt, kSortThreads, 0, st>>>(kin, vin, kout, vout, ws.hist,
+                                                              bins->d_npairs, cap, shift, nt);
+        else
+            k_radix_scatter<false><<<nt, kSortThreads, 0, st>>>(kin, vin, kout, vout, ws.hist,
+                                                               bins->d_npairs, cap, shift, nt);
+        s = last_launch_status();
+        if (s != GS_OK) return s;
+        int32_t* t = kin; kin = kout; kout = t;
+        t = vin; vin = vout; vout = t;
+    }
+    k_finalize<<<1184, 256, 0, st>>>(vin, ws.gm_gid, bins->d_npairs, cap, bins->pair_gmj,
+                                     bins->pair_gid);
+    return last_launch_status();
+}
+
+}  // namespace gs
+
+extern "C" gs_status gs_bin_bricks(const float* params, const gs_grid* grid, const gs_config* cfg,
+                                   gs_bins* bins, void* ws, size_t ws_bytes, gs_stream stream) {
+    gs_status s = validate_grid_cfg(grid, cfg);
+    if (s != GS_OK) return s;
+    if (!bins_match(bins, grid, cfg)) return GS_ERR_INVALID_ARG;
+    if (bins->n_gauss > 0 && !params) return GS_ERR_INVALID_ARG;
+    if (params && reinterpret_cast<uintptr_t>(params) % 16 != 0) return GS_ERR_INVALID_ARG;
+    Workspace w;
+    s = bind_workspace(ws, ws_bytes, bins->n_gauss, bins->capacity, grid, cfg, &w);
+    if (s != GS_OK) return s;
+    return bin_bricks_impl(params, grid, cfg, bins, w, reinterpret_cast<cudaStream_t>(stream));
+}

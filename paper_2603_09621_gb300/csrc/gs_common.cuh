@@ -1,0 +1,213 @@
+// gs_common.cuh -- internal definitions shared by the CUDA translation units of libgsmri.
+// Not part of the public ABI (include/gs_api.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gs_api.h"
+
+namespace gs {
+
+// ------------------------------------------------------------------ render record
+// Per-Gaussian record (16 floats = 64 bytes, 16-byte aligned) written by the preprocess
+// kernel and staged into shared memory by the render kernels. Coordinates are in voxel
+// index space: the voxel (i, j, k) sits at (i, j, k). mu' = (mu - o) / h - 1/2 is stored as a
+// float head plus a float tail computed in FP64, so that d = (i - head) - tail is accurate to
+// one rounding of d itself even at large coordinates. Q = -(log2 e / 2) H Sigma^{-1} H with
+// H = diag(h), so the log2 of the Gaussian kernel is e = d^T Q d (off-diagonals stored
+// doubled): e = Qxx dx^2 + Qyy dy^2 + Qzz dz^2 + Q2xy dx dy + Q2xz dx dz + Q2yz dy dz.
+enum RecField : int {
+    R_MUX = 0, R_MUY = 1, R_MUZ = 2,       // mu' head
+    R_LOX = 3, R_LOY = 4, R_LOZ = 5,       // mu' tail
+    R_QXX = 6, R_QYY = 7, R_QZZ = 8,
+    R_Q2XY = 9, R_Q2XZ = 10, R_Q2YZ = 11,
+    R_VR = 12,                              // v * r (signal times relaxation factor)
+    R_R = 13,                               // r
+    R_V = 14,                               // v
+    R_PAD = 15,
+    REC_FLOATS = 16
+};
+
+// Render-space gradient accumulated per Gaussian by the adjoint kernel (12 floats):
+// m1 = sum G d (3), m2 = sum G d d^T (xx, yy, zz, xy, xz, yz), dv, dr, pad, where
+// G = dL/dw * w for every contributing pair (see gs_render.cu).
+enum GradField : int {
+    G_M1X = 0, G_M1Y = 1, G_M1Z = 2,
+    G_M2XX = 3, G_M2YY = 4, G_M2ZZ = 5, G_M2XY = 6, G_M2XZ = 7, G_M2YZ = 8,
+    G_DV = 9, G_DR = 10, G_PAD = 11,
+    GRAD_FLOATS = 12
+};
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+constexpr float kHalfLog2e = 0.7213475204444817f;  // (1/2) log2(e)
+
+// Brick-range brange layout [N, 8].
+enum BrangeField : int { B_LOX = 0, B_LOY, B_LOZ, B_HIX, B_HIY, B_HIZ, B_CNT, B_VALID };
+
+// ------------------------------------------------------------------ sort constants
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per tile
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;  // 1024 values per block
+
+constexpr int kL1Blocks = 1024;  // fixed block count of the L1 reduction (deterministic)
+
+constexpr int64_t kMaxCapacity = (int64_t(1) << 31) - 4096;
+
+// ------------------------------------------------------------------ workspace layout
+struct Workspace {
+    int32_t* keys0;
+    int32_t* vals0;
+    int32_t* keys1;
+    int32_t* vals1;
+    int32_t* gm_gid;
+    int32_t* gm_cnt;
+    int32_t* brick_cnt;
+    int32_t* hist;
+    long long* scan_tmp;     // block sums of the multi-level scan
+    float* part;             // [capacity, 12] per-pair partial gradients (deterministic mode)
+    float* gacc;             // [n_gauss, 12] render-space gradient per Gaussian
+    float* l1_part;          // [kL1Blocks]
+    int64_t scan_tmp_len;
+    int32_t n_tiles;
+    size_t bytes;
+};
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+inline int64_t scan_tmp_len_for(int64_t n) {
+    // Space for every level of the recursive block-sum scan of n values.
+    int64_t total = 0;
+    while (n > kScanTile) {
+        n = (n + kScanTile - 1) / kScanTile;
+        total += n + 1;
+    }
+    return total + 8;
+}
+
+// Carve (or size, if base == nullptr) the workspace. Returns false on overflow.
+inline bool carve_workspace(void* base, int64_t n_gauss, int64_t capacity, int32_t n_bricks,
+                            bool deterministic, Workspace* ws) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return base ? static_cast<char*>(base) + o : nullptr;
+    };
+    const int64_t cap = capacity > 0 ? capacity : 1;
+    const int64_t n = n_gauss > 0 ? n_gauss : 1;
+    ws->n_tiles = static_cast<int32_t>((cap + kSortTile - 1) / kSortTile);
+    int64_t hist_len = int64_t(kRadix) * ws->n_tiles;
+    int64_t max_scan = hist_len;
+    if (n + 1 > max_scan) max_scan = n + 1;
+    if (int64_t(n_bricks) + 1 > max_scan) max_scan = int64_t(n_bricks) + 1;
+    ws->scan_tmp_len = scan_tmp_len_for(max_scan);
+    ws->keys0 = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * cap));
+    ws->vals0 = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * cap));
+    ws->keys1 = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * cap));
+    ws->vals1 = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * cap));
+    ws->gm_gid = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * cap));
+    ws->gm_cnt = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * (n + 1)));
+    ws->brick_cnt = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * (int64_t(n_bricks) + 1)));
+    ws->hist = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * (hist_len + 1)));
+    ws->scan_tmp = reinterpret_cast<long long*>(take(sizeof(long long) * ws->scan_tmp_len));
+    ws->part = reinterpret_cast<float*>(
+        take(deterministic ? sizeof(float) * GRAD_FLOATS * cap : 256));
+    ws->gacc = reinterpret_cast<float*>(take(sizeof(float) * GRAD_FLOATS * n));
+    ws->l1_part = reinterpret_cast<float*>(take(sizeof(float) * kL1Blocks));
+    ws->bytes = off;
+    return true;
+}
+
+// ------------------------------------------------------------------ helpers
+struct BrickGeom {
+    int nbx, nby, nbz;
+    int bx, by, bz;
+};
+
+inline BrickGeom brick_geom(const gs_grid* g, const gs_config* c) {
+    BrickGeom b;
+    b.bx = c->brick[0];
+    b.by = c->brick[1];
+    b.bz = c->brick[2];
+    b.nbx = (g->nx + b.bx - 1) / b.bx;
+    b.nby = (g->ny + b.by - 1) / b.by;
+    b.nbz = (g->nz + b.bz - 1) / b.bz;
+    return b;
+}
+
+// Validation shared by the entry points. Returns GS_OK or GS_ERR_INVALID_ARG.
+gs_status validate_grid_cfg(const gs_grid* g, const gs_config* c);
+
+// Launch counter (every kernel launch site is followed by last_launch_status()).
+void note_launch();
+
+// Launch error check -> gs_status; counts the launch it follows.
+inline gs_status last_launch_status() {
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+// Device-wide exclusive scan of int32 values (n <= kMaxCapacity + 1); 64-bit accumulation.
+// out may alias in. If total != nullptr, the grand total is written there (device int64).
+gs_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, long long* total,
+                             long long* tmp, int64_t tmp_len, cudaStream_t stream);
+
+// Parameter chain + render-space gradient -> raw-parameter gradient (gs_param.cu).
+gs_status launch_param_bwd(const float* params, const float* gacc, int64_t n,
+                           const gs_grid* grid, const gs_config* cfg, float* dparams,
+                           cudaStream_t stream);
+
+// L1 loss with optional sign gradient into dpred (gs_volume.cu).
+gs_status launch_l1(const float* pred, const float* target, int64_t n, float* d_loss,
+                    float* dpred, float* partials, cudaStream_t stream);
+
+}  // namespace gs
+
+// ------------------------------------------------------------------ device math
+#ifdef __CUDACC__
+namespace gs {
+
+// FP32 exponential of the binning specification: Cody-Waite argument reduction with a
+// 15-bit head of ln 2 and a degree-7 Taylor polynomial in Horner form (W. J. Cody and
+// W. Waite, "Software Manual for the Elementary Functions", 1980). Every operation is one
+// explicitly rounded IEEE operation in a fixed order (no contraction), so the result is the
+// same on any IEEE-754 implementation that follows the same sequence. |x| <= 30.
+__device__ __forceinline__ float exp_cw(float x) {
+    const float L2E = 1.44269502f;
+    const float LN2_HI = 0.693145751953125f;
+    const float LN2_LO = 1.42860677e-6f;
+    float kf = floorf(__fadd_rn(__fmul_rn(x, L2E), 0.5f));
+    float r = __fsub_rn(__fsub_rn(x, __fmul_rn(kf, LN2_HI)), __fmul_rn(kf, LN2_LO));
+    float p = 1.0f / 5040.0f;
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f / 720.0f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f / 120.0f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f / 24.0f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f / 6.0f);
+    p = __fadd_rn(__fmul_rn(p, r), 0.5f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f);
+    int k = static_cast<int>(kf);
+    float two_k = __int_as_float((k + 127) << 23);
+    return __fmul_rn(p, two_k);
+}
+
+// 2^x on the special-function unit (ex2.approx, flush-to-zero).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+}  // namespace gs
+#endif

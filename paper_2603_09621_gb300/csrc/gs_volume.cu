@@ -1,0 +1,228 @@
+// gs_volume.cu -- slice-profile forward model (box average of s slices along z), its
+// adjoint, the deterministic L1 loss, the fused fitting step and the small host utilities of
+// the C ABI.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <functional>
+
+#include "gs_common.cuh"
+
+namespace gs {
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+__global__ void __launch_bounds__(256) k_downsample_fwd(const float* __restrict__ hr, int ny, int nx,
+                                                        int nzl, int s, float inv_s,
+                                                        float* __restrict__ lr) {
+    const int64_t plane = int64_t(ny) * nx;
+    const int64_t n = plane * nzl;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t k = i / plane, r = i - k * plane;
+        const float* src = hr + (k * s) * plane + r;
+        float acc = 0.f;
+        for (int j = 0; j < s; ++j) acc += src[j * plane];
+        lr[i] = acc * inv_s;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_downsample_bwd(const float* __restrict__ dlr, int nz, int ny,
+                                                        int nx, int s, float inv_s,
+                                                        float* __restrict__ dhr) {
+    const int64_t plane = int64_t(ny) * nx;
+    const int64_t n = plane * nz;
+    const int zmax = s * (nz / s);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t z = i / plane, r = i - z * plane;
+        dhr[i] = (z < zmax) ? dlr[(z / s) * plane + r] * inv_s : 0.0f;
+    }
+}
+
+// Stage 1: fixed grid of kL1Blocks blocks; each thread sums |pred - target| over a fixed
+// stride, then a fixed-shape block tree. Optionally writes sign(pred - target) / n.
+__global__ void __launch_bounds__(256) k_l1_partial(const float* __restrict__ pred,
+                                                    const float* __restrict__ target, int64_t n,
+                                                    float inv_n, float* __restrict__ dpred,
+                                                    float* __restrict__ partials) {
+    __shared__ float sm[256];
+    float acc = 0.f;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const float d = pred[i] - target[i];
+        acc += fabsf(d);
+        if (dpred) dpred[i] = (d > 0.f) ? inv_n : ((d < 0.f) ? -inv_n : 0.f);
+    }
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = sm[0];
+}
+
+__global__ void __launch_bounds__(1024) k_l1_final(const float* __restrict__ partials, float inv_n,
+                                                   float* __restrict__ loss) {
+    __shared__ float sm[kL1Blocks];
+    sm[threadIdx.x] = partials[threadIdx.x];
+    __syncthreads();
+    for (int o = kL1Blocks / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = sm[0] * inv_n;
+}
+
+static unsigned grid_for(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    if (b < 1) b = 1;
+    return static_cast<unsigned>(b < 65536 ? b : 65536);
+}
+
+gs_status launch_l1(const float* pred, const float* target, int64_t n, float* d_loss, float* dpred,
+                    float* partials, cudaStream_t st) {
+    const float inv_n = n > 0 ? 1.0f / float(n) : 0.0f;
+    k_l1_partial<<<kL1Blocks, 256, 0, st>>>(pred, target, n, inv_n, dpred, partials);
+    gs_status s = last_launch_status();
+    if (s != GS_OK) return s;
+    k_l1_final<<<1, kL1Blocks, 0, st>>>(partials, inv_n, d_loss);
+    return last_launch_status();
+}
+
+gs_status downsample_fwd_impl(const float* hr, int nz, int ny, int nx, int s, float* lr,
+                              cudaStream_t st) {
+    const int nzl = nz / s;
+    const int64_t n = int64_t(nzl) * ny * nx;
+    if (n == 0) return GS_OK;
+    k_downsample_fwd<<<grid_for(n), 256, 0, st>>>(hr, ny, nx, nzl, s, 1.0f / float(s), lr);
+    return last_launch_status();
+}
+
+gs_status downsample_bwd_impl(const float* dlr, int nz, int ny, int nx, int s, float* dhr,
+                              cudaStream_t st) {
+    const int64_t n = int64_t(nz) * ny * nx;
+    k_downsample_bwd<<<grid_for(n), 256, 0, st>>>(dlr, nz, ny, nx, s, 1.0f / float(s), dhr);
+    return last_launch_status();
+}
+
+// Provided by the other translation units.
+gs_status bind_workspace(void* base, size_t bytes, int64_t n_gauss, int64_t capacity,
+                         const gs_grid* grid, const gs_config* cfg, Workspace* ws);
+bool bins_match(const gs_bins* b, const gs_grid* grid, const gs_config* cfg);
+gs_status bin_bricks_impl(const float* params, const gs_grid* grid, const gs_config* cfg,
+                          gs_bins* bins, const Workspace& ws, cudaStream_t st);
+gs_status render_fwd_impl(const gs_bins* bins, const gs_grid* grid, const gs_config* cfg, float* I,
+                          float* W, unsigned long long* stats, cudaStream_t st);
+gs_status render_bwd_geo(const gs_bins* bins, const gs_grid* grid, const gs_config* cfg,
+                         const float* I, const float* W, const float* dI, const Workspace& ws,
+                         cudaStream_t st, const std::function<bool()>& after_kernel);
+
+}  // namespace gs
+
+using namespace gs;
+
+static bool vol_args_ok(const void* a, const void* b, int32_t nz, int32_t ny, int32_t nx, int32_t s) {
+    return a && b && nz > 0 && ny > 0 && nx > 0 && s > 0 &&
+           int64_t(nz) * ny * nx <= (int64_t(1) << 31) - 1;
+}
+
+extern "C" gs_status gs_downsample_fwd(const float* hr, int32_t nz, int32_t ny, int32_t nx,
+                                       int32_t s, float* lr, gs_stream stream) {
+    if (!vol_args_ok(hr, lr, nz, ny, nx, s)) return GS_ERR_INVALID_ARG;
+    return downsample_fwd_impl(hr, nz, ny, nx, s, lr, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" gs_status gs_downsample_bwd(const float* dlr, int32_t nz, int32_t ny, int32_t nx,
+                                       int32_t s, float* dhr, gs_stream stream) {
+    if (!vol_args_ok(dlr, dhr, nz, ny, nx, s)) return GS_ERR_INVALID_ARG;
+    return downsample_bwd_impl(dlr, nz, ny, nx, s, dhr, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" gs_status gs_l1_loss(const float* pred, const float* target, int64_t n, float* d_loss,
+                                float* dpred, void* ws, size_t ws_bytes, gs_stream stream) {
+    if (!pred || !target || !d_loss || !ws || n <= 0) return GS_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return GS_ERR_INVALID_ARG;
+    if (ws_bytes < sizeof(float) * kL1Blocks) return GS_ERR_WORKSPACE;
+    return launch_l1(pred, target, n, d_loss, dpred, static_cast<float*>(ws),
+                     reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" gs_status gs_fit_step(gs_fit_state* st, gs_stream stream) {
+    if (!st) return GS_ERR_INVALID_ARG;
+    gs_status s = validate_grid_cfg(&st->grid, &st->cfg);
+    if (s != GS_OK) return s;
+    if (st->n_gauss <= 0 || st->s <= 0 || st->grid.nz / st->s <= 0) return GS_ERR_INVALID_ARG;
+    if (!st->params || !st->grad || !st->m || !st->v || !st->d_step || !st->I || !st->W ||
+        !st->dI || !st->lr_pred || !st->lr_target || !st->d_loss)
+        return GS_ERR_INVALID_ARG;
+    if (!bins_match(&st->bins, &st->grid, &st->cfg) || st->bins.n_gauss != st->n_gauss)
+        return GS_ERR_INVALID_ARG;
+    Workspace w;
+    s = bind_workspace(st->ws, st->ws_bytes, st->n_gauss, st->bins.capacity, &st->grid, &st->cfg, &w);
+    if (s != GS_OK) return s;
+    if (st->n_phase_events != 0 && (st->n_phase_events != GS_FIT_PHASES || !st->phase_events))
+        return GS_ERR_INVALID_ARG;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    auto mark = [&](int phase) -> bool {
+        if (!st->n_phase_events) return true;
+        return cudaEventRecord(static_cast<cudaEvent_t>(st->phase_events[phase]), cs) == cudaSuccess;
+    };
+    const gs_grid& g = st->grid;
+    if (!mark(0)) return GS_ERR_CUDA;
+    s = bin_bricks_impl(st->params, &g, &st->cfg, &st->bins, w, cs);
+    if (s != GS_OK) return s;
+    if (!mark(1)) return GS_ERR_CUDA;
+    s = render_fwd_impl(&st->bins, &g, &st->cfg, st->I, st->W, nullptr, cs);
+    if (s != GS_OK) return s;
+    if (!mark(2)) return GS_ERR_CUDA;
+    s = downsample_fwd_impl(st->I, g.nz, g.ny, g.nx, st->s, st->lr_pred, cs);
+    if (s != GS_OK) return s;
+    const int64_t n_lr = int64_t(g.nz / st->s) * g.ny * g.nx;
+    // L1 loss; its gradient overwrites lr_pred in place.
+    s = launch_l1(st->lr_pred, st->lr_target, n_lr, st->d_loss, st->lr_pred, w.l1_part, cs);
+    if (s != GS_OK) return s;
+    s = downsample_bwd_impl(st->lr_pred, g.nz, g.ny, g.nx, st->s, st->dI, cs);
+    if (s != GS_OK) return s;
+    if (!mark(3)) return GS_ERR_CUDA;
+    s = render_bwd_geo(&st->bins, &g, &st->cfg, st->I, st->W, st->dI, w, cs, [&]() { return mark(4); });
+    if (s != GS_OK) return s;
+    s = launch_param_bwd(st->params, w.gacc, st->n_gauss, &g, &st->cfg, st->grad, cs);
+    if (s != GS_OK) return s;
+    if (!mark(5)) return GS_ERR_CUDA;
+    s = gs_adam_step(st->params, st->grad, st->m, st->v, st->n_gauss, &st->adam, st->d_step, stream);
+    if (s != GS_OK) return s;
+    if (!mark(6)) return GS_ERR_CUDA;
+    return GS_OK;
+}
+
+extern "C" gs_status gs_status_read(const int32_t* d_status, int32_t* h_status, gs_stream stream) {
+    if (!d_status || !h_status) return GS_ERR_INVALID_ARG;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(h_status, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+        return GS_ERR_CUDA;
+    if (cudaStreamSynchronize(cs) != cudaSuccess) return GS_ERR_CUDA;
+    if (*h_status & GS_STATUS_CAPACITY) return GS_ERR_CAPACITY;
+    if (*h_status & GS_STATUS_NONFINITE) return GS_ERR_NONFINITE;
+    return GS_OK;
+}
+
+extern "C" const char* gs_status_string(gs_status s) {
+    switch (s) {
+        case GS_OK: return "ok";
+        case GS_ERR_INVALID_ARG: return "invalid argument";
+        case GS_ERR_CAPACITY: return "pair capacity exceeded";
+        case GS_ERR_WORKSPACE: return "workspace too small";
+        case GS_ERR_CUDA: return "CUDA error";
+        case GS_ERR_TIMEOUT: return "device wait timed out";
+        case GS_ERR_NONFINITE: return "invalid Gaussian parameters";
+    }
+    return "unknown status";
+}
+
+extern "C" unsigned long long gs_launch_count(void) { return g_launches.load(); }
+
+extern "C" const char* gs_version(void) { return "gsmri 0.1.0 (sm_103a)"; }

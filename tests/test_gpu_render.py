@@ -1,0 +1,154 @@
+"""Forward render on the GPU (Eq. 3-4, Sec. 3.3) against the FP64 oracle.
+
+Acceptance: max relative error of I <= 1e-5 over voxels with W > 1e-6, excluding voxels
+where some pair sits within 1e-4 sigma^2 of the truncation boundary (there the inclusion is
+decided by rounding, so both results are valid)."""
+import numpy as np
+import pytest
+
+from helpers import c1, cloud_params, phantom_fit, to_dev
+from paper_2603_09621_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def _gs():
+    from paper_2603_09621_gb300 import gs
+    return gs
+
+
+def _grid(og):
+    return _gs().Grid(og.nx, og.ny, og.nz, tuple(og.h), tuple(og.origin))
+
+
+def gpu_render(params_np, og, brick=(8, 8, 8), signal_mode=0, a_act=0, t_act=0, stats=False):
+    import torch
+    gs = _gs()
+    cfg = gs.Config(brick=brick, signal_mode=signal_mode, a_act=a_act, t_act=t_act)
+    st = torch.zeros(2, dtype=torch.int64, device="cuda") if stats else None
+    I, W, bins, _ = gs.render(to_dev(params_np.astype(np.float32)), _grid(og), cfg, stats=st)
+    torch.cuda.synchronize()
+    out = dict(I=I.cpu().numpy(), W=W.cpu().numpy(), status=bins.status(), npairs=bins.npairs())
+    if stats:
+        out["stats"] = st.cpu().numpy()
+    return out
+
+
+def check_forward(I, W, ref, tol=TOL):
+    mask = (ref["W"] > 1e-6) & (ref["amb"] == 0)
+    assert mask.sum() > 0
+    excluded = ((ref["W"] > 1e-6) & (ref["amb"] > 0)).sum()
+    assert excluded <= 0.01 * (ref["W"] > 1e-6).sum() + 2
+    Io, Wo = ref["I"][mask], ref["W"][mask]
+    relI = np.abs(I[mask] - Io) / np.maximum(np.abs(Io), 1e-30)
+    relW = np.abs(W[mask] - Wo) / Wo
+    assert relI.max() <= tol, (relI.max(), np.argmax(relI))
+    assert relW.max() <= tol, relW.max()
+    # voxels nobody reaches render exactly zero
+    none = ref["W"] == 0
+    assert np.all(W[none] == 0) and np.all(I[none] == 0)
+    return relI.max()
+
+
+def test_forward_workload_vs_oracle():
+    """32^3 grid, 4,096 Gaussians (the forward-only workload), full volume."""
+    import oracle
+    params, og = c1()
+    ref = oracle.render(params.astype(np.float64), og)
+    out = gpu_render(params, og, stats=True)
+    check_forward(out["I"], out["W"], ref)
+    # effective pairs counted by the kernel = pairs with d^2 <= 9 (up to boundary ties)
+    n_eff_ref = None
+    assert out["stats"][0] > 0 and out["stats"][1] >= out["stats"][0]
+
+
+@pytest.mark.parametrize("brick", [(8, 8, 4), (4, 4, 4), (16, 8, 4)])
+def test_forward_brick_shape_invariance(brick):
+    """Output does not depend on the brick shape: bit-identical to the 8^3 default."""
+    params, og = c1()
+    a = gpu_render(params, og)
+    b = gpu_render(params, og, brick=brick)
+    assert np.array_equal(a["I"], b["I"]) and np.array_equal(a["W"], b["W"])
+
+
+def test_forward_deterministic():
+    params, og = c1()
+    a = gpu_render(params, og)
+    b = gpu_render(params, og)
+    assert np.array_equal(a["I"], b["I"]) and np.array_equal(a["W"], b["W"])
+
+
+def test_forward_ragged_anisotropic_grid():
+    """Partial edge bricks, non-unit spacing (arbitrary-scale sampling, Sec. 4.2), offset
+    origin, Gaussians partly outside the grid."""
+    import oracle
+    og = oracle.Grid(37, 29, 21, (0.9, 1.2, 1.5), (-3.0, 2.5, 1.0))
+    d = inputs.gaussian_cloud(5, 3000, (21, 29, 37), h=og.h)
+    d["mu"] = d["mu"] + np.array(og.origin, np.float32)
+    d["mu"][:50] = d["mu"][:50] * 1.6 - 10.0
+    params = cloud_params(d)
+    ref = oracle.render(params.astype(np.float64), og)
+    out = gpu_render(params, og)
+    check_forward(out["I"], out["W"], ref)
+
+
+@pytest.mark.parametrize("mode,a_act,t_act", [(1, 0, 0), (0, 1, 1), (1, 1, 1)])
+def test_forward_signal_modes_and_activations(mode, a_act, t_act):
+    import oracle
+    params, og = c1()
+    p = params.copy()
+    rng = np.random.default_rng(0)
+    if a_act:
+        p[:, 10] = rng.normal(0, 1.5, p.shape[0])
+    if t_act:
+        p[:, 11] = rng.normal(-0.5, 1.5, p.shape[0])
+    cfg = oracle.Config(signal_mode=mode, a_act=a_act, t_act=t_act)
+    ref = oracle.render(p.astype(np.float64), og, cfg)
+    out = gpu_render(p, og, signal_mode=mode, a_act=a_act, t_act=t_act)
+    check_forward(out["I"], out["W"], ref)
+
+
+def test_forward_edge_cases():
+    """Empty cloud; a Gaussian wholly outside the grid; a tiny Gaussian between voxel
+    centres that reaches none; one huge Gaussian covering the whole grid."""
+    import oracle
+    og = oracle.Grid(20, 18, 12)
+    out = gpu_render(np.zeros((0, 12), np.float32), og)
+    assert np.all(out["I"] == 0) and np.all(out["W"] == 0)
+    p = np.array([[-50.0, 5.0, 5.0, 0, 0, 0, 1, 0, 0, 0, 0.7, 0.5],
+                  [10.0, 9.0, 6.0, np.log(0.05), np.log(0.05), np.log(0.05), 1, 0, 0, 0, 0.3, 0.5],
+                  [10.0, 9.0, 6.0, np.log(40.0), np.log(30.0), np.log(20.0), 0.3, 0.2, 0.1, 0.9,
+                   0.6, 0.8]], np.float32)
+    ref = oracle.render(p.astype(np.float64), og)
+    out = gpu_render(p, og)
+    check_forward(out["I"], out["W"], ref)
+    assert np.all(out["W"] > 0)
+
+
+def test_forward_fit_workload_crops():
+    """256 x 256 x 128, 500k Gaussians (the fitting workload), rendered whole on the GPU and
+    compared with the oracle on three 24^3 crops (centre, corner, far edge) that the oracle
+    renders from all 500k Gaussians."""
+    import oracle
+    w = phantom_fit()
+    og = w["grid"]
+    out = gpu_render(w["params0"], og)
+    assert out["status"] == 0
+    for (x0, y0, z0) in ((116, 116, 52), (0, 0, 0), (232, 100, 104)):
+        crop = (x0, x0 + 24, y0, y0 + 24, z0, z0 + 24)
+        ref = oracle.render(w["params0"].astype(np.float64), og, crop=crop)
+        sl = (slice(z0, z0 + 24), slice(y0, y0 + 24), slice(x0, x0 + 24))
+        check_forward(out["I"][sl], out["W"][sl], ref)
+
+
+def test_forward_clustered_anisotropic():
+    """Clustered, strongly anisotropic cloud (one axis up to 8 voxels) with heavy brick
+    overlap, on a 64^3 grid."""
+    import oracle
+    og = oracle.Grid(64, 64, 64)
+    d = inputs.gmm_cloud(3, 20000, (64, 64, 64), n_blobs=4, blob_std=8.0)
+    params = cloud_params(d)
+    ref = oracle.render(params.astype(np.float64), og)
+    out = gpu_render(params, og)
+    check_forward(out["I"], out["W"], ref)
