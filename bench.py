@@ -366,7 +366,7 @@ def run_ours(args, world, rank, local):
     h_loss = torch.empty((), dtype=torch.float32).pin_memory()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_ms = []
-    for i in range(args.e2e_steps + 1):
+    for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         flush.fill_(1.0)
         e0.record(stream)
         st.params.copy_(h_params, non_blocking=True)
@@ -377,11 +377,13 @@ def run_ours(args, world, rank, local):
         e1.synchronize()
         if i > 0:
             e2e_ms.append(e0.elapsed_time(e1))
-    t_e2e = allreduce_max(sum(e2e_ms) / 1000.0, world)
-    e2e = {"value": allreduce_sum(float(n_eff) * len(e2e_ms), world) / t_e2e,
-           "unit": "pair-evals/s",
-           "h2d_bytes_per_step": h_params.numel() * 4 + h_lr.numel() * 4,
-           "d2h_bytes_per_step": 4, "ms_per_step": 1000.0 * t_e2e / len(e2e_ms)}
+    e2e = None
+    if e2e_ms:
+        t_e2e = allreduce_max(sum(e2e_ms) / 1000.0, world)
+        e2e = {"value": allreduce_sum(float(n_eff) * len(e2e_ms), world) / t_e2e,
+               "unit": "pair-evals/s",
+               "h2d_bytes_per_step": h_params.numel() * 4 + h_lr.numel() * 4,
+               "d2h_bytes_per_step": 4, "ms_per_step": 1000.0 * t_e2e / len(e2e_ms)}
 
     if rank != 0:
         return

@@ -112,7 +112,7 @@ typedef struct {
  * optimiser). Learning rates per parameter group: means, log-scales, quaternion, a, t. */
 typedef struct {
     float lr_mu, lr_scale, lr_rot, lr_a, lr_t;
-    float beta1, beta2, eps;
+    double beta1, beta2, eps; /* double, so 1 - beta is exact for decimal inputs like 0.999 */
 } gs_adam;
 
 /* Size in bytes of the device arena that gs_bins_bind() carves; 0 on invalid arguments.

@@ -144,15 +144,17 @@ def render(params, grid: Grid, cfg: Config = Config(), crop=None, amb_tol=None, 
     """Eq. 3-4 with the Sec. 3.3 truncation, brute force in FP64.
 
     Returns dict(I, W, S, amb, npair, n_invalid), each volume crop-shaped ``[z, y, x]``.
-    ``amb`` counts, per voxel, the pairs whose d^2 lies within ``amb_tol`` of sigma_t^2
-    (default 1e-4 sigma_t^2): their inclusion is decided by rounding, so parity tests compare
-    only voxels with ``amb == 0``. ``npair`` counts the contributing pairs per voxel.
+    ``amb`` counts, per voxel, the pairs with |d^2 - sigma_t^2| <= amb_tol sum_ab
+    |C_ab d_a d_b| (default amb_tol 2e-5, about 170 FP32 units in the last place of the
+    form's absolute terms): a rounded FP32 evaluation of d^2 may put them on either side of
+    the truncation boundary, so parity tests compare only voxels with ``amb == 0``.
+    ``npair`` counts the contributing pairs per voxel.
     """
     p = np.ascontiguousarray(params, dtype=np.float64).reshape(-1, 12)
     dims, h, o = _grid_arrays(grid)
     carr, shape = _crop_array(grid, crop)
     if amb_tol is None:
-        amb_tol = 1e-4 * cfg.trunc_sigma ** 2
+        amb_tol = 2e-5
     I = np.zeros(shape, np.float64)
     W = np.zeros(shape, np.float64)
     S = np.zeros(shape, np.float64)

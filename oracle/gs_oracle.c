@@ -128,12 +128,14 @@ static void og_activate(const double* p, const int32_t dims[3], const double h[3
         g->v = g->A * g->T;
         g->r = 1.0;
     }
-    /* Exact bounding box: d^2 >= |p-mu|^2 / s_max^2. Pad the radius so that every pair in the
-     * ambiguity band |d^2 - sigma_t^2| <= amb_tol is visited as well, then add one voxel. */
+    /* Exact bounding box: d^2 >= |p-mu|^2 / s_max^2. The radius is padded by 1 % in d^2 so
+     * that pairs in the ambiguity band just outside the ellipsoid are visited as well, then
+     * one voxel is added. */
     double smax = g->s[0];
     if (g->s[1] > smax) smax = g->s[1];
     if (g->s[2] > smax) smax = g->s[2];
-    double rad = sqrt(sigma_t * sigma_t + 2.0 * amb_tol) * smax * (1.0 + 1e-6) + 1e-9;
+    double rad = sqrt(sigma_t * sigma_t * (1.0 + (amb_tol > 0.0 ? 0.01 : 0.0))) * smax *
+                     (1.0 + 1e-6) + 1e-9;
     for (int k = 0; k < 3; ++k) {
         if (!prune) {
             g->lo[k] = 0;
@@ -174,14 +176,23 @@ static double og_d2(const og_gauss* g, const double d[3]) {
     return acc;
 }
 
+/* Sum of the absolute terms of the quadratic form: the scale of its rounding error. */
+static double og_d2_abs(const og_gauss* g, const double d[3]) {
+    double acc = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) acc += fabs(d[a] * g->C[a][b] * d[b]);
+    return acc;
+}
+
 /* ------------------------------------------------------------- Eq. 3-4 */
 
 /*
  * Forward render of the voxels in crop = [x0,x1) x [y0,y1) x [z0,z1) (NULL: whole grid).
  * Outputs are crop-shaped, z-major, x fastest:
  *   S = sum_i v_i w_i, W = sum_i w_i, I = S / max(W, eps),
- *   amb = number of pairs with |d^2 - sigma_t^2| <= amb_tol (their inclusion depends on
- *         rounding at the truncation boundary; tests compare only voxels with amb == 0),
+ *   amb = number of pairs with |d^2 - sigma_t^2| <= amb_tol * sum_ab |C_ab d_a d_b| (a
+ *         rounded evaluation of d^2 may fall on either side of the truncation boundary;
+ *         tests compare only voxels with amb == 0),
  *   npair (optional) = number of contributing pairs (d^2 <= sigma_t^2) per voxel.
  * Returns the number of invalid Gaussians.
  */
@@ -229,7 +240,7 @@ int64_t og_render(const double* params, int64_t N, const int32_t dims[3], const 
                     double d[3] = {px - g->mu[0], py - g->mu[1], pz - g->mu[2]};
                     double d2 = og_d2(g, d);
                     int64_t idx = (int64_t)(y - c[2]) * cx + (x - c[0]);
-                    if (fabs(d2 - s2) <= amb_tol) Az[idx] += 1;
+                    if (amb_tol > 0.0 && fabs(d2 - s2) <= amb_tol * og_d2_abs(g, d)) Az[idx] += 1;
                     if (d2 <= s2) {
                         double w = exp(-0.5 * d2) * g->r;
                         Sz[idx] += g->v * w;

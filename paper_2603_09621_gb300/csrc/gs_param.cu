@@ -154,7 +154,10 @@ gs_status launch_param_bwd(const float* params, const float* gacc, int64_t n, co
 // ------------------------------------------------------------------------ Adam
 struct AdamLr {
     float lr[5];
-    float beta1, beta2, eps;
+    float beta1, beta2;          // decay rates
+    float omb1, omb2;            // 1 - beta, formed in double on the host
+    float log_b1, log_b2;        // log(beta), formed in double on the host
+    float eps;
 };
 
 __device__ __forceinline__ int lr_group(int col) {
@@ -165,14 +168,15 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ params, const 
                                               float* __restrict__ m, float* __restrict__ v, int64_t n,
                                               AdamLr hp, const int32_t* __restrict__ d_step) {
     const int t = *d_step + 1;
-    const float bc1 = 1.0f - powf(hp.beta1, float(t));
-    const float bc2 = 1.0f - powf(hp.beta2, float(t));
-    const float rs_bc2 = rsqrtf(bc2);
+    // bias corrections 1 - beta^t = -expm1(t log beta), accurate for small t (1 - beta ~ 1e-3)
+    const float bc1 = -expm1f(float(t) * hp.log_b1);
+    const float bc2 = -expm1f(float(t) * hp.log_b2);
+    const float rs_bc2 = 1.0f / sqrtf(bc2);
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += int64_t(gridDim.x) * blockDim.x) {
         const float gr = grad[i];
-        const float mi = hp.beta1 * m[i] + (1.0f - hp.beta1) * gr;
-        const float vi = hp.beta2 * v[i] + (1.0f - hp.beta2) * gr * gr;
+        const float mi = hp.beta1 * m[i] + hp.omb1 * gr;
+        const float vi = hp.beta2 * v[i] + hp.omb2 * gr * gr;
         m[i] = mi;
         v[i] = vi;
         const float lr = hp.lr[lr_group(static_cast<int>(i % 12))];
@@ -186,8 +190,8 @@ __global__ void k_step_inc(int32_t* d_step) { *d_step += 1; }
 // ------------------------------------------------------------------------ init
 struct InitGeo {
     int nx, ny, nzl;         // LR volume dims
-    float o[3], hl[3];       // origin, LR spacing
-    float ext[3];            // HR extent L = n h
+    double o[3], hl[3];      // origin, LR spacing
+    double ext[3];           // HR extent L = n h
     int nl[3];               // lattice counts
     float log_s[3];
     float t_raw;
@@ -203,16 +207,18 @@ __global__ void __launch_bounds__(256) k_init_lattice(const float* __restrict__ 
     const int k = static_cast<int>(g / (int64_t(G.nl[0]) * G.nl[1]));
     const int idx[3] = {i, j, k};
     const int dims[3] = {G.nx, G.ny, G.nzl};
+    // Lattice centres and LR continuous indices in FP64 (a handful of operations per point).
     float c[3], f[3];
     int i0[3], i1[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        c[a] = G.o[a] + (float(idx[a]) + 0.5f) * (G.ext[a] / float(G.nl[a]));
-        float u = (c[a] - G.o[a]) / G.hl[a] - 0.5f;
-        u = fminf(fmaxf(u, 0.0f), float(dims[a] - 1));
-        i0[a] = static_cast<int>(floorf(u));
+        const double cd = G.o[a] + (double(idx[a]) + 0.5) * (G.ext[a] / double(G.nl[a]));
+        double u = (cd - G.o[a]) / G.hl[a] - 0.5;
+        u = fmin(fmax(u, 0.0), double(dims[a] - 1));
+        i0[a] = static_cast<int>(floor(u));
         i1[a] = min(i0[a] + 1, dims[a] - 1);
-        f[a] = u - float(i0[a]);
+        f[a] = static_cast<float>(u - double(i0[a]));
+        c[a] = static_cast<float>(cd);
     }
     float acc = 0.f;
 #pragma unroll
@@ -260,9 +266,16 @@ extern "C" gs_status gs_adam_step(float* params, const float* grad, float* m, fl
         a.lr[2] = hp->lr_rot;
         a.lr[3] = hp->lr_a;
         a.lr[4] = hp->lr_t;
-        a.beta1 = hp->beta1;
-        a.beta2 = hp->beta2;
-        a.eps = hp->eps;
+        if (!(hp->beta1 >= 0.0 && hp->beta1 < 1.0 && hp->beta2 >= 0.0 && hp->beta2 < 1.0 &&
+              hp->eps > 0.0))
+            return GS_ERR_INVALID_ARG;
+        a.beta1 = static_cast<float>(hp->beta1);
+        a.beta2 = static_cast<float>(hp->beta2);
+        a.omb1 = static_cast<float>(1.0 - hp->beta1);
+        a.omb2 = static_cast<float>(1.0 - hp->beta2);
+        a.log_b1 = static_cast<float>(log(hp->beta1 > 0.0 ? hp->beta1 : 1e-300));
+        a.log_b2 = static_cast<float>(log(hp->beta2 > 0.0 ? hp->beta2 : 1e-300));
+        a.eps = static_cast<float>(hp->eps);
         const int64_t n = n_gauss * 12;
         const int64_t blocks64 = (n + 255) / 256;
         const unsigned blocks = static_cast<unsigned>(blocks64 < 65536 ? blocks64 : 65536);
@@ -288,12 +301,12 @@ extern "C" gs_status gs_init_lattice(const float* lr, const gs_grid* g, int32_t 
     const int nl[3] = {nlx, nly, nlz};
     for (int a = 0; a < 3; ++a) {
         G.o[a] = g->origin[a];
-        G.hl[a] = g->h[a] * (a == 2 ? float(s) : 1.0f);
-        G.ext[a] = float(n[a]) * g->h[a];
+        G.hl[a] = double(g->h[a]) * (a == 2 ? double(s) : 1.0);
+        G.ext[a] = double(n[a]) * double(g->h[a]);
         G.nl[a] = nl[a];
-        G.log_s[a] = logf(0.5f * G.ext[a] / float(nl[a]));
+        G.log_s[a] = static_cast<float>(log(0.5 * G.ext[a] / double(nl[a])));
     }
-    G.t_raw = t_act ? logf(t_init / (1.0f - t_init)) : t_init;
+    G.t_raw = t_act ? static_cast<float>(log(double(t_init) / (1.0 - double(t_init)))) : t_init;
     const int64_t N = int64_t(nlx) * nly * nlz;
     k_init_lattice<<<static_cast<unsigned>((N + 255) / 256), 256, 0,
                      reinterpret_cast<cudaStream_t>(stream)>>>(lr, G, params);

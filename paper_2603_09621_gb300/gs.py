@@ -47,7 +47,7 @@ class gs_bins(ctypes.Structure):
 class gs_adam(ctypes.Structure):
     _fields_ = [("lr_mu", ctypes.c_float), ("lr_scale", ctypes.c_float),
                 ("lr_rot", ctypes.c_float), ("lr_a", ctypes.c_float), ("lr_t", ctypes.c_float),
-                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float)]
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double)]
 
 
 class gs_fit_state(ctypes.Structure):

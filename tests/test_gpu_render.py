@@ -1,8 +1,8 @@
 """Forward render on the GPU (Eq. 3-4, Sec. 3.3) against the FP64 oracle.
 
 Acceptance: max relative error of I <= 1e-5 over voxels with W > 1e-6, excluding voxels
-where some pair sits within 1e-4 sigma^2 of the truncation boundary (there the inclusion is
-decided by rounding, so both results are valid)."""
+where some pair's d^2 lies within 2e-5 of the form's absolute terms of the truncation
+boundary (there an FP32 evaluation may fall either side, so both results are valid)."""
 import numpy as np
 import pytest
 
@@ -39,7 +39,7 @@ def check_forward(I, W, ref, tol=TOL):
     mask = (ref["W"] > 1e-6) & (ref["amb"] == 0)
     assert mask.sum() > 0
     excluded = ((ref["W"] > 1e-6) & (ref["amb"] > 0)).sum()
-    assert excluded <= 0.01 * (ref["W"] > 1e-6).sum() + 2
+    assert excluded <= 0.02 * (ref["W"] > 1e-6).sum() + 2
     Io, Wo = ref["I"][mask], ref["W"][mask]
     relI = np.abs(I[mask] - Io) / np.maximum(np.abs(Io), 1e-30)
     relW = np.abs(W[mask] - Wo) / Wo
@@ -58,9 +58,10 @@ def test_forward_workload_vs_oracle():
     ref = oracle.render(params.astype(np.float64), og)
     out = gpu_render(params, og, stats=True)
     check_forward(out["I"], out["W"], ref)
-    # effective pairs counted by the kernel = pairs with d^2 <= 9 (up to boundary ties)
-    n_eff_ref = None
-    assert out["stats"][0] > 0 and out["stats"][1] >= out["stats"][0]
+    # effective pairs counted by the kernel = pairs with d^2 <= 9, up to boundary ties
+    n_eff, n_eval = out["stats"]
+    assert abs(int(n_eff) - int(ref["npair"].sum())) <= int(ref["amb"].sum())
+    assert n_eval >= n_eff
 
 
 @pytest.mark.parametrize("brick", [(8, 8, 4), (4, 4, 4), (16, 8, 4)])
@@ -133,11 +134,12 @@ def test_forward_fit_workload_crops():
     import oracle
     w = phantom_fit()
     og = w["grid"]
-    out = gpu_render(w["params0"], og)
+    out = gpu_render(w["params0"], og, t_act=1)
     assert out["status"] == 0
     for (x0, y0, z0) in ((116, 116, 52), (0, 0, 0), (232, 100, 104)):
         crop = (x0, x0 + 24, y0, y0 + 24, z0, z0 + 24)
-        ref = oracle.render(w["params0"].astype(np.float64), og, crop=crop)
+        ref = oracle.render(w["params0"].astype(np.float64), og, oracle.Config(t_act=1),
+                            crop=crop)
         sl = (slice(z0, z0 + 24), slice(y0, y0 + 24), slice(x0, x0 + 24))
         check_forward(out["I"][sl], out["W"][sl], ref)
 

@@ -103,6 +103,6 @@ def test_init_lattice_matches_oracle():
     torch.cuda.synchronize()
     got = got.cpu().numpy()
     assert got.shape == ref.shape
-    np.testing.assert_allclose(got[:, :10], ref[:, :10], rtol=1e-6, atol=1e-5)
+    np.testing.assert_allclose(got[:, :10], ref[:, :10], rtol=1e-6, atol=1e-6)
     np.testing.assert_allclose(got[:, 10], ref[:, 10], rtol=1e-5, atol=1e-6)
     np.testing.assert_allclose(got[:, 11], ref[:, 11], atol=1e-7)

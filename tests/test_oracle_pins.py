@@ -112,6 +112,7 @@ def test_single_gaussian_reproduces_its_signal(oracle_mod):
         assert sup.sum() > 0
         np.testing.assert_allclose(out["I"][sup], p[0, 10], rtol=1e-14)
         assert np.all(out["I"][~sup] == 0.0)
+        assert np.array_equal(out["npair"], sup.astype(np.int32))
 
 
 def test_two_symmetric_gaussians_average(oracle_mod):
@@ -290,7 +291,7 @@ def test_gradient_fd_at_three_sigma_away_from_boundary(oracle_mod):
         d = inputs.gaussian_cloud(seed, 6, (10, 10, 10), scale_range=(0.9, 1.8))
         p = inputs.assemble_params(d["mu"], d["log_s"], d["q"], d["pd"],
                                    d["pd"] * 0.5 + 0.2).astype(np.float64)
-        if o.render(p, g, cfg, amb_tol=1e-3)["amb"].sum() == 0:
+        if o.render(p, g, cfg, amb_tol=1e-3)["amb"].sum() == 0:  # band 1e-3 |terms|
             break
     else:
         pytest.fail("no boundary-free configuration found")
