@@ -35,11 +35,11 @@ def gpu_render(params_np, og, brick=(8, 8, 8), signal_mode=0, a_act=0, t_act=0, 
     return out
 
 
-def check_forward(I, W, ref, tol=TOL):
+def check_forward(I, W, ref, tol=TOL, max_tie_frac=0.02):
     mask = (ref["W"] > 1e-6) & (ref["amb"] == 0)
     assert mask.sum() > 0
     excluded = ((ref["W"] > 1e-6) & (ref["amb"] > 0)).sum()
-    assert excluded <= 0.02 * (ref["W"] > 1e-6).sum() + 2
+    assert excluded <= max_tie_frac * (ref["W"] > 1e-6).sum() + 2
     Io, Wo = ref["I"][mask], ref["W"][mask]
     relI = np.abs(I[mask] - Io) / np.maximum(np.abs(Io), 1e-30)
     relW = np.abs(W[mask] - Wo) / Wo
@@ -153,4 +153,5 @@ def test_forward_clustered_anisotropic():
     params = cloud_params(d)
     ref = oracle.render(params.astype(np.float64), og)
     out = gpu_render(params, og)
-    check_forward(out["I"], out["W"], ref)
+    # Hundreds of pairs per voxel in the blob cores: more voxels hold a boundary tie.
+    check_forward(out["I"], out["W"], ref, max_tie_frac=0.10)
