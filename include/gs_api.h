@@ -180,6 +180,26 @@ gs_status gs_downsample_bwd(const float* dlr, int32_t nz, int32_t ny, int32_t nx
 gs_status gs_l1_loss(const float* pred, const float* target, int64_t n, float* d_loss,
                      float* dpred, void* ws, size_t ws_bytes, gs_stream stream);
 
+/* Largest n accepted by gs_l1_loss_static (4096 partial sums of 8192 values each). */
+#define GS_L1_STATIC_MAX_N 33554432LL
+
+/* Mean absolute error like gs_l1_loss, for callers that cannot allocate device memory (the
+ * paper has no counterpart; it is a property of this library's interface). A process that
+ * reserved its whole device budget at start-up, or a host program that embeds this library
+ * without a GPU allocator, cannot provide gs_l1_loss's workspace; this entry point keeps the
+ * per-block partial sums in a 16 KB array compiled into the library instead (every GPU that
+ * loads the library holds it until the process exits) and calls no allocation routine.
+ * pred, target: device float [n]; d_loss: device float scalar; dpred: device float [n] or
+ * NULL (sign(pred - target) / n). n must be in [1, GS_L1_STATIC_MAX_N]; larger n returns
+ * GS_ERR_INVALID_ARG before any launch. The first call on a device looks up the array's
+ * device address (with that device current); make that first call before any stream
+ * capture. All calls share the one array and it keeps the last call's partial sums; every
+ * call overwrites the entries it reads, so nothing needs clearing, but calls that overlap on
+ * the GPU (concurrent streams, or other processes' threads on the same device) race on it:
+ * issue them in order on one stream. */
+gs_status gs_l1_loss_static(const float* pred, const float* target, int64_t n, float* d_loss,
+                            float* dpred, gs_stream stream);
+
 /* One bias-corrected Adam update of params [n_gauss, 12] from grad, with moments m, v
  * (device float [n_gauss, 12], zero before the first step). d_step: device int32, the
  * number of steps taken so far; incremented on the device (graph-capturable). */

@@ -84,6 +84,7 @@ SIGNATURES = {
     "gs_downsample_fwd": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _P, _P]),
     "gs_downsample_bwd": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _P, _P]),
     "gs_l1_loss": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _SZ, _P]),
+    "gs_l1_loss_static": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P]),
     "gs_adam_step": (ctypes.c_int, [_P, _P, _P, _P, _I64, _P, _P, _P]),
     "gs_init_lattice": (ctypes.c_int, [_P, _P, _I32, _I32, _I32, _I32, _I32, _F, _P, _P]),
     "gs_fit_step": (ctypes.c_int, [_P, _P]),
@@ -317,6 +318,17 @@ def gs_l1_loss(pred, target, ws: Workspace, d_loss=None, dpred=None, stream=None
     d_loss = torch.empty((), dtype=torch.float32, device=pred.device) if d_loss is None else d_loss
     _check(load().gs_l1_loss(_ptr(pred), _ptr(target), pred.numel(), _ptr(d_loss), _ptr(dpred),
                              _ptr(ws.buf), ws.nbytes, _stream(stream)), "gs_l1_loss")
+    return d_loss
+
+
+GS_L1_STATIC_MAX_N = 33554432
+
+
+def gs_l1_loss_static(pred, target, d_loss=None, dpred=None, stream=None):
+    """L1 loss without a workspace (for callers that cannot allocate device memory)."""
+    d_loss = torch.empty((), dtype=torch.float32, device=pred.device) if d_loss is None else d_loss
+    _check(load().gs_l1_loss_static(_ptr(pred), _ptr(target), pred.numel(), _ptr(d_loss),
+                                    _ptr(dpred), _stream(stream)), "gs_l1_loss_static")
     return d_loss
 
 
