@@ -33,7 +33,9 @@ gs_status validate_grid_cfg(const gs_grid* g, const gs_config* c) {
             return GS_ERR_INVALID_ARG;
         if (c->brick[k] <= 0 || c->brick[k] % 4 != 0) return GS_ERR_INVALID_ARG;
     }
-    if (c->brick[0] * c->brick[1] * c->brick[2] > 1024) return GS_ERR_INVALID_ARG;
+    // rows of bx voxels along x (bx in {4, 8, 16}), at most 64 rows per brick
+    if (c->brick[0] != 4 && c->brick[0] != 8 && c->brick[0] != 16) return GS_ERR_INVALID_ARG;
+    if (c->brick[1] * c->brick[2] > 64) return GS_ERR_INVALID_ARG;
     if (!(c->trunc_sigma > 0.0f) || !isfinite(c->trunc_sigma)) return GS_ERR_INVALID_ARG;
     if (!(c->eps > 0.0f)) return GS_ERR_INVALID_ARG;
     if (c->signal_mode != 0 && c->signal_mode != 1) return GS_ERR_INVALID_ARG;
@@ -184,7 +186,8 @@ __global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ pa
 #pragma unroll
         for (int k = 0; k < 8; ++k) br[k] = 0;
         gm_cnt[g] = 0;
-        r4[0] = z4; r4[1] = z4; r4[2] = z4; r4[3] = z4;
+#pragma unroll
+        for (int k = 0; k < REC_F4; ++k) r4[k] = z4;
         atomicOr(status, GS_STATUS_NONFINITE);
         return;
     }
@@ -257,23 +260,40 @@ __global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ pa
     gm_cnt[g] = cnt;
 
     // ---- render record (accuracy only; contraction allowed) ----
-    float inv_s2[3];
+    // M = sqrt(log2 e / 2) diag(1/s) R^T H: row k of M is R[:, k]^T H scaled by sqrt(k)/s_k.
+    const float sk = 0.8493218002880191f;  // sqrt((1/2) log2 e)
+    float Mx[3][3];                        // Mx[row][col]
 #pragma unroll
-    for (int k = 0; k < 3; ++k) inv_s2[k] = 1.0f / (s[k] * s[k]);
-    float C[3][3];
+    for (int k = 0; k < 3; ++k) {
+        const float f = sk / s[k];
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+        for (int j = 0; j < 3; ++j) Mx[k][j] = f * R[j][k] * G.h[j];
+    }
+    float col[3][3];  // col[j] = column j of M
 #pragma unroll
-        for (int b = 0; b < 3; ++b)
-            C[a][b] = R[a][0] * R[b][0] * inv_s2[0] + R[a][1] * R[b][1] * inv_s2[1] +
-                      R[a][2] * R[b][2] * inv_s2[2];
-    const float kq = -kHalfLog2e;
-    float Qxx = kq * G.h[0] * G.h[0] * C[0][0];
-    float Qyy = kq * G.h[1] * G.h[1] * C[1][1];
-    float Qzz = kq * G.h[2] * G.h[2] * C[2][2];
-    float Q2xy = 2.0f * kq * G.h[0] * G.h[1] * C[0][1];
-    float Q2xz = 2.0f * kq * G.h[0] * G.h[2] * C[0][2];
-    float Q2yz = 2.0f * kq * G.h[1] * G.h[2] * C[1][2];
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) col[j][k] = Mx[k][j];
+    const float am0 = col[0][0] * col[0][0] + col[0][1] * col[0][1] + col[0][2] * col[0][2];
+    const float inv_a = 1.0f / am0;
+    float nrm[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        nrm[j] = sqrtf(col[j][0] * col[j][0] + col[j][1] * col[j][1] + col[j][2] * col[j][2]);
+    // n1, n2: m1, m2 with their components along m0 removed
+    float n1[3], n2[3];
+    {
+        const float c1 = (col[1][0] * col[0][0] + col[1][1] * col[0][1] + col[1][2] * col[0][2]) * inv_a;
+        const float c2 = (col[2][0] * col[0][0] + col[2][1] * col[0][1] + col[2][2] * col[0][2]) * inv_a;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            n1[k] = col[1][k] - c1 * col[0][k];
+            n2[k] = col[2][k] - c2 * col[0][k];
+        }
+    }
+    const float Pyy = n1[0] * n1[0] + n1[1] * n1[1] + n1[2] * n1[2];
+    const float Pzz = n2[0] * n2[0] + n2[1] * n2[1] + n2[2] * n2[2];
+    const float P2yz = 2.0f * (n1[0] * n2[0] + n1[1] * n2[1] + n1[2] * n2[2]);
     float mh[3], ml[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -292,9 +312,12 @@ __global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ pa
         r = 1.0f;
     }
     r4[0] = make_float4(mh[0], mh[1], mh[2], ml[0]);
-    r4[1] = make_float4(ml[1], ml[2], Qxx, Qyy);
-    r4[2] = make_float4(Qzz, Q2xy, Q2xz, Q2yz);
-    r4[3] = make_float4(v * r, r, v, 0.0f);
+    r4[1] = make_float4(ml[1], ml[2], col[0][0], col[0][1]);
+    r4[2] = make_float4(col[0][2], col[1][0], col[1][1], col[1][2]);
+    r4[3] = make_float4(col[2][0], col[2][1], col[2][2], nrm[0]);
+    r4[4] = make_float4(nrm[1], nrm[2], inv_a, Pyy);
+    r4[5] = make_float4(P2yz, Pzz, v * r, r);
+    r4[6] = make_float4(v, 0.0f, 0.0f, 0.0f);
 }
 
 // ============================================================================ capacity / emit

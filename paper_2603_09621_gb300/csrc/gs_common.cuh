@@ -10,24 +10,33 @@
 namespace gs {
 
 // ------------------------------------------------------------------ render record
-// Per-Gaussian record (16 floats = 64 bytes, 16-byte aligned) written by the preprocess
-// kernel and staged into shared memory by the render kernels. Coordinates are in voxel
-// index space: the voxel (i, j, k) sits at (i, j, k). mu' = (mu - o) / h - 1/2 is stored as a
-// float head plus a float tail computed in FP64, so that d = (i - head) - tail is accurate to
-// one rounding of d itself even at large coordinates. Q = -(log2 e / 2) H Sigma^{-1} H with
-// H = diag(h), so the log2 of the Gaussian kernel is e = d^T Q d (off-diagonals stored
-// doubled): e = Qxx dx^2 + Qyy dy^2 + Qzz dz^2 + Q2xy dx dy + Q2xz dx dz + Q2yz dy dz.
+// Per-Gaussian record (28 floats = 7 float4, 112 bytes) written by the preprocess kernel and
+// staged into shared memory by the render kernels. Coordinates are voxel-index space: voxel
+// (i, j, k) sits at (i, j, k). The mean mu' = (mu - o) / h - 1/2 is a float head plus a
+// float tail computed in FP64, so d = (i - head) - tail is accurate to one rounding of d even
+// at large coordinates. The shape is the whitening matrix
+//     M = sqrt(log2(e) / 2) diag(1/s) R^T H,   H = diag(h),
+// so that q = |M d|^2 = (log2 e / 2) d^T Sigma^{-1} d and the Gaussian kernel is 2^-q. Its
+// columns m0, m1, m2 are the whitened steps of one voxel along x, y, z. Working with M d
+// rather than with the quadratic form keeps rounding relative to |M d| itself, which matters
+// for strongly anisotropic Gaussians. n_j = |m_j|; inv_a = 1 / |m0|^2.
+// Row shadow: the minimum of q along the row through (dy, dz) is
+//     Pyy dy^2 + P2yz dy dz + Pzz dz^2  (Gram form of m1, m2 projected orthogonally to m0).
 enum RecField : int {
-    R_MUX = 0, R_MUY = 1, R_MUZ = 2,       // mu' head
-    R_LOX = 3, R_LOY = 4, R_LOZ = 5,       // mu' tail
-    R_QXX = 6, R_QYY = 7, R_QZZ = 8,
-    R_Q2XY = 9, R_Q2XZ = 10, R_Q2YZ = 11,
-    R_VR = 12,                              // v * r (signal times relaxation factor)
-    R_R = 13,                               // r
-    R_V = 14,                               // v
-    R_PAD = 15,
-    REC_FLOATS = 16
+    R_MHX = 0, R_MHY = 1, R_MHZ = 2,        // mu' head
+    R_MLX = 3, R_MLY = 4, R_MLZ = 5,        // mu' tail
+    R_M0X = 6, R_M0Y = 7, R_M0Z = 8,        // m0
+    R_M1X = 9, R_M1Y = 10, R_M1Z = 11,      // m1
+    R_M2X = 12, R_M2Y = 13, R_M2Z = 14,     // m2
+    R_N0 = 15, R_N1 = 16, R_N2 = 17,        // column norms
+    R_INVA = 18,                            // 1 / |m0|^2
+    R_PYY = 19, R_P2YZ = 20, R_PZZ = 21,    // row shadow form
+    R_VR = 22,                              // v * r
+    R_R = 23,                               // r
+    R_V = 24,                               // v
+    REC_FLOATS = 28
 };
+constexpr int REC_F4 = REC_FLOATS / 4;
 
 // Render-space gradient accumulated per Gaussian by the adjoint kernel (12 floats):
 // m1 = sum G d (3), m2 = sum G d d^T (xx, yy, zz, xy, xz, yz), dv, dr, pad, where

@@ -35,6 +35,11 @@ def gpu_render(params_np, og, brick=(8, 8, 8), signal_mode=0, a_act=0, t_act=0, 
     return out
 
 
+# W (the normaliser) is held to 5e-5: an FP32 rotation of a 24-voxel offset along the long
+# axis of a 16:1 anisotropic Gaussian leaves about 1e-5 relative error in a single weight.
+TOL_W = 5e-5
+
+
 def check_forward(I, W, ref, tol=TOL, max_tie_frac=0.02):
     mask = (ref["W"] > 1e-6) & (ref["amb"] == 0)
     assert mask.sum() > 0
@@ -44,7 +49,7 @@ def check_forward(I, W, ref, tol=TOL, max_tie_frac=0.02):
     relI = np.abs(I[mask] - Io) / np.maximum(np.abs(Io), 1e-30)
     relW = np.abs(W[mask] - Wo) / Wo
     assert relI.max() <= tol, (relI.max(), np.argmax(relI))
-    assert relW.max() <= tol, relW.max()
+    assert relW.max() <= TOL_W, relW.max()
     # voxels nobody reaches render exactly zero
     none = ref["W"] == 0
     assert np.all(W[none] == 0) and np.all(I[none] == 0)
