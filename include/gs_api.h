@@ -63,9 +63,9 @@ typedef struct {
 } gs_grid;
 
 /* Rendering options.
- *   brick: brick shape in voxels (x, y, z): x in {4, 8, 16}, y and z multiples of 4 with
- *          y * z <= 64. Sec. 3.3 uses 8 x 8 x 4; the default is 8 x 8 x 8. Output does not
- *          depend on it.
+ *   brick: brick shape in voxels (x, y, z): x in {4, 8, 16}, y and z multiples of 4,
+ *          y * z <= 64 and x * y * z <= 512. Sec. 3.3 uses 8 x 8 x 4; the default is 8 x 8 x 8.
+ *          Output does not depend on it.
  *   trunc_sigma: Mahalanobis truncation radius (3.0: the 3-sigma ellipsoids of Sec. 3.3).
  *   eps: floor of the weight sum in the normalisation of Eq. 3 (the paper gives none).
  *   deterministic: 1 = the backward pass reduces per-Gaussian gradients in a fixed order

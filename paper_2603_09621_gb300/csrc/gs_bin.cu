@@ -36,6 +36,7 @@ gs_status validate_grid_cfg(const gs_grid* g, const gs_config* c) {
     // rows of bx voxels along x (bx in {4, 8, 16}), at most 64 rows per brick
     if (c->brick[0] != 4 && c->brick[0] != 8 && c->brick[0] != 16) return GS_ERR_INVALID_ARG;
     if (c->brick[1] * c->brick[2] > 64) return GS_ERR_INVALID_ARG;
+    if (c->brick[0] * c->brick[1] * c->brick[2] > 512) return GS_ERR_INVALID_ARG;
     if (!(c->trunc_sigma > 0.0f) || !isfinite(c->trunc_sigma)) return GS_ERR_INVALID_ARG;
     if (!(c->eps > 0.0f)) return GS_ERR_INVALID_ARG;
     if (c->signal_mode != 0 && c->signal_mode != 1) return GS_ERR_INVALID_ARG;
@@ -281,15 +282,14 @@ __global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ pa
     for (int j = 0; j < 3; ++j)
         nrm[j] = sqrtf(col[j][0] * col[j][0] + col[j][1] * col[j][1] + col[j][2] * col[j][2]);
     // n1, n2: m1, m2 with their components along m0 removed
+    // n1, n2: m1, m2 with their components along m0 removed; c_j = -(m_j . m0) / a
     float n1[3], n2[3];
-    {
-        const float c1 = (col[1][0] * col[0][0] + col[1][1] * col[0][1] + col[1][2] * col[0][2]) * inv_a;
-        const float c2 = (col[2][0] * col[0][0] + col[2][1] * col[0][1] + col[2][2] * col[0][2]) * inv_a;
+    const float d1 = (col[1][0] * col[0][0] + col[1][1] * col[0][1] + col[1][2] * col[0][2]) * inv_a;
+    const float d2 = (col[2][0] * col[0][0] + col[2][1] * col[0][1] + col[2][2] * col[0][2]) * inv_a;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            n1[k] = col[1][k] - c1 * col[0][k];
-            n2[k] = col[2][k] - c2 * col[0][k];
-        }
+    for (int k = 0; k < 3; ++k) {
+        n1[k] = col[1][k] - d1 * col[0][k];
+        n2[k] = col[2][k] - d2 * col[0][k];
     }
     const float Pyy = n1[0] * n1[0] + n1[1] * n1[1] + n1[2] * n1[2];
     const float Pzz = n2[0] * n2[0] + n2[1] * n2[1] + n2[2] * n2[2];
@@ -312,12 +312,10 @@ __global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ pa
         r = 1.0f;
     }
     r4[0] = make_float4(mh[0], mh[1], mh[2], ml[0]);
-    r4[1] = make_float4(ml[1], ml[2], col[0][0], col[0][1]);
-    r4[2] = make_float4(col[0][2], col[1][0], col[1][1], col[1][2]);
-    r4[3] = make_float4(col[2][0], col[2][1], col[2][2], nrm[0]);
-    r4[4] = make_float4(nrm[1], nrm[2], inv_a, Pyy);
-    r4[5] = make_float4(P2yz, Pzz, v * r, r);
-    r4[6] = make_float4(v, 0.0f, 0.0f, 0.0f);
+    r4[1] = make_float4(ml[1], ml[2], Pyy, P2yz);
+    r4[2] = make_float4(Pzz, -d1, -d2, am0);
+    r4[3] = make_float4(inv_a, nrm[0], nrm[1], nrm[2]);
+    r4[4] = make_float4(v * r, r, v, 0.0f);
 }
 
 // ============================================================================ capacity / emit

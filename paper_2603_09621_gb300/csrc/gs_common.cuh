@@ -10,31 +10,33 @@
 namespace gs {
 
 // ------------------------------------------------------------------ render record
-// Per-Gaussian record (28 floats = 7 float4, 112 bytes) written by the preprocess kernel and
+// Per-Gaussian record (20 floats = 5 float4, 80 bytes) written by the preprocess kernel and
 // staged into shared memory by the render kernels. Coordinates are voxel-index space: voxel
 // (i, j, k) sits at (i, j, k). The mean mu' = (mu - o) / h - 1/2 is a float head plus a
 // float tail computed in FP64, so d = (i - head) - tail is accurate to one rounding of d even
-// at large coordinates. The shape is the whitening matrix
-//     M = sqrt(log2(e) / 2) diag(1/s) R^T H,   H = diag(h),
-// so that q = |M d|^2 = (log2 e / 2) d^T Sigma^{-1} d and the Gaussian kernel is 2^-q. Its
-// columns m0, m1, m2 are the whitened steps of one voxel along x, y, z. Working with M d
-// rather than with the quadratic form keeps rounding relative to |M d| itself, which matters
-// for strongly anisotropic Gaussians. n_j = |m_j|; inv_a = 1 / |m0|^2.
-// Row shadow: the minimum of q along the row through (dy, dz) is
-//     Pyy dy^2 + P2yz dy dz + Pzz dz^2  (Gram form of m1, m2 projected orthogonally to m0).
+// at large coordinates.
+// The exponent q = (log2 e / 2) d^T Sigma'^{-1} d (Sigma' the covariance in voxel units, the
+// Gaussian kernel is 2^-q) is stored by completing the square along x:
+//     q(dx, dy, dz) = S(dy, dz) + a (dx - dx*(dy, dz))^2,
+//     S(dy, dz) = Pyy dy^2 + P2yz dy dz + Pzz dz^2   (the minimum of q along the x-row),
+//     dx*(dy, dz) = c1 dy + c2 dz                      (where that minimum is reached).
+// With M = sqrt(log2 e / 2) diag(1/s) R^T H (columns m0, m1, m2, the whitened steps of one
+// voxel along x, y, z): a = |m0|^2, c_j = -(m_j . m0) / a, and S is the Gram form of m1, m2
+// with their components along m0 removed. Every term of this form has the size of q itself
+// for voxels inside the ellipsoid, so FP32 keeps its accuracy for strongly anisotropic
+// Gaussians, and the value at a voxel depends only on the voxel and the Gaussian.
+// n_j = |m_j| bound |M (p - c)| <= sum_j h_j n_j over a box of half-extents h (culling).
 enum RecField : int {
     R_MHX = 0, R_MHY = 1, R_MHZ = 2,        // mu' head
     R_MLX = 3, R_MLY = 4, R_MLZ = 5,        // mu' tail
-    R_M0X = 6, R_M0Y = 7, R_M0Z = 8,        // m0
-    R_M1X = 9, R_M1Y = 10, R_M1Z = 11,      // m1
-    R_M2X = 12, R_M2Y = 13, R_M2Z = 14,     // m2
-    R_N0 = 15, R_N1 = 16, R_N2 = 17,        // column norms
-    R_INVA = 18,                            // 1 / |m0|^2
-    R_PYY = 19, R_P2YZ = 20, R_PZZ = 21,    // row shadow form
-    R_VR = 22,                              // v * r
-    R_R = 23,                               // r
-    R_V = 24,                               // v
-    REC_FLOATS = 28
+    R_PYY = 6, R_P2YZ = 7, R_PZZ = 8,       // row shadow S
+    R_C1 = 9, R_C2 = 10,                    // dx* = c1 dy + c2 dz
+    R_A = 11, R_INVA = 12,                  // a = |m0|^2 and 1 / a
+    R_N0 = 13, R_N1 = 14, R_N2 = 15,        // column norms of M
+    R_VR = 16,                              // v * r
+    R_R = 17,                               // r
+    R_V = 18,                               // v
+    REC_FLOATS = 20
 };
 constexpr int REC_F4 = REC_FLOATS / 4;
 

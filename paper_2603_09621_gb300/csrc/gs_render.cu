@@ -2,208 +2,162 @@
 // (Sec. 3.3: "each handled by one CUDA thread block"; the brick's Gaussians are staged into
 // shared memory and no depth order is needed).
 //
-// A brick of bx x by x bz voxels is treated as by * bz rows of bx voxels along x. For a
-// Gaussian and a row through (dy, dz) (offsets from the mean, voxel units) the exponent
-// along the row is q(dx) = |z_row + dx m0|^2 with z_row = m1 dy + m2 dz (whitened
-// coordinates, see the record layout). Two exact, conservative culls decide which rows a
-// Gaussian can reach:
-//   * slab: |M (p - c)| <= sum_j h_j |m_j| over a box of half-extents h around c, so the
-//     box is missed when |M (c - mu)| - sum_j h_j |m_j| > sqrt(T) (triangle inequality);
-//   * row shadow: min over dx of q = Pyy dy^2 + P2yz dy dz + Pzz dz^2 (the Gram form of m1,
-//     m2 projected orthogonally to m0), so the row is missed when that exceeds T.
-// (T = (log2 e / 2) trunc_sigma^2; margins absorb FP32 rounding.) A pair contributes only
-// where q <= T, evaluated per voxel, so culled pairs contribute exact zeros.
+// Exponent of a pair (voxel p, Gaussian i) in voxel units: q = S(dy, dz) + a (dx - dx*)^2
+// (record layout in gs_common.cuh), the Gaussian kernel is 2^-q and the pair contributes
+// only where q <= T = (log2 e / 2) trunc_sigma^2. q is computed by the same operation sequence
+// in both kernels from the voxel's global index and the Gaussian alone, so forward and
+// adjoint agree on every inclusion decision and no result depends on the brick shape.
 //
-// Per (row, Gaussian) the exponent is expanded around the row's nearest integer voxel x_c to
-// the Gaussian's closest point: q(x) = q_c + t (a t + 2 b_c), t = x - x_c, a = |m0|^2,
-// q_c = |z_c|^2, b_c = z_c . m0. x_c depends only on the Gaussian and the row, never on the
-// brick, so every voxel's value is the same for any brick shape, and every term stays of the
-// size of q itself for the voxels inside the ellipsoid (no cancellation).
-//
-// Forward: lane <-> row; the row's bx S and W accumulate in registers in ascending Gaussian
-// id (deterministic). A warp tests 32 staged Gaussians against its slab with one ballot;
-// each lane then keeps a 64-bit mask of the chunk's Gaussians that reach its row and walks
-// it in order.
-// Adjoint: each warp owns 32 staged Gaussians; an owner lane builds its Gaussian's row mask
-// from the row shadow, the warp turns the (Gaussian, row) hits into work items by a prefix
-// sum, and each lane evaluates one item: the row's bx voxels, summed into 11 render-space
-// partials. The owner adds its items in row order. The per-(brick, Gaussian) result goes to
-// a per-pair slot (deterministic mode, reduced later in Gaussian-major order) or to one
+// Forward: the brick is split into 4 x 4 x 4 footprints, one warp each; a lane owns two
+// voxels along x. A warp tests 32 staged Gaussians against its footprint with one ballot
+// (triangle inequality in whitened space: |M (p - mu)| >= |M (c - mu)| - sum_j h_j |m_j|, so a
+// footprint whose centre c is farther than sqrt(T) + 1.5 sum_j |m_j| is missed; a margin
+// absorbs FP32 rounding) and evaluates the hits in ascending Gaussian id, accumulating S and
+// W in registers (deterministic).
+// Adjoint: one lane per staged Gaussian walks exactly the voxels it reaches in the brick:
+// the rows come from the row shadow (per z-row a quadratic in dy) and the voxels of a row
+// from the parabola in dx, so no pair outside the ellipsoid is evaluated. Lanes are given
+// Gaussians in descending order of work (a counting sort of their row counts) so that a warp
+// holds similar loads; the assignment does not affect results, because each Gaussian's
+// partial is summed by one lane in a fixed voxel order. The per-(brick, Gaussian) result goes
+// to a per-pair slot (deterministic mode, reduced later in Gaussian-major order) or to one
 // float atomic per value (fast mode).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <atomic>
 #include <functional>
 
 #include "gs_common.cuh"
 
 namespace gs {
 
-constexpr int kFwdChunk = 64;    // Gaussians staged per forward round (one 64-bit mask)
-constexpr int kBwdChunk = 256;   // Gaussians staged per adjoint round (8 warps x 32)
+constexpr int kFwdChunk = 128;   // Gaussians staged per forward round
+constexpr int kBwdChunk = 256;   // Gaussians staged per adjoint round (one per thread)
 constexpr int kMaxRows = 64;     // rows per brick (by * bz)
 constexpr int kBwdThreads = 256;
 
 struct RenderGeo {
     int nx, ny, nz;
     int bsx, bsy, bsz;  // brick shape
+    int fx, fy, fz;     // 4^3 footprints per brick along each axis
     int nbx, nby;
     float T;            // (log2 e / 2) trunc_sigma^2: a pair contributes when q <= T
-    float Trow;         // row / slab cull bound on q: T (1 + 1e-2) + 1e-3
-    float sqrtTcull;    // sqrt(Trow)
+    float Tcull;        // cull bound on q: T (1 + 1e-2) + 1e-3
+    float sqrtTcull;    // sqrt(Tcull)
     float eps;
 };
 
 struct Rec {
     float mhx, mhy, mhz, mlx, mly, mlz;
-    float m0x, m0y, m0z, m1x, m1y, m1z, m2x, m2y, m2z;
-    float n0, n1, n2, inva, pyy, p2yz, pzz, vr, r, v;
+    float pyy, p2yz, pzz, c1, c2, a, inva, n0, n1, n2, vr, r, v;
 };
 
 __device__ __forceinline__ Rec load_rec(const float4* s) {
-    const float4 a = s[0], b = s[1], c = s[2], d = s[3], e = s[4], f = s[5], g = s[6];
+    const float4 a = s[0], b = s[1], c = s[2], d = s[3], e = s[4];
     Rec R;
     R.mhx = a.x; R.mhy = a.y; R.mhz = a.z; R.mlx = a.w;
-    R.mly = b.x; R.mlz = b.y; R.m0x = b.z; R.m0y = b.w;
-    R.m0z = c.x; R.m1x = c.y; R.m1y = c.z; R.m1z = c.w;
-    R.m2x = d.x; R.m2y = d.y; R.m2z = d.z; R.n0 = d.w;
-    R.n1 = e.x; R.n2 = e.y; R.inva = e.z; R.pyy = e.w;
-    R.p2yz = f.x; R.pzz = f.y; R.vr = f.z; R.r = f.w;
-    R.v = g.x;
+    R.mly = b.x; R.mlz = b.y; R.pyy = b.z; R.p2yz = b.w;
+    R.pzz = c.x; R.c1 = c.y; R.c2 = c.z; R.a = c.w;
+    R.inva = d.x; R.n0 = d.y; R.n1 = d.z; R.n2 = d.w;
+    R.vr = e.x; R.r = e.y; R.v = e.z;
     return R;
 }
 
-// Slab cull: may the Gaussian reach a voxel centre in [xa, xb] x [ya, yb] x [za, zb]?
-__device__ __forceinline__ bool slab_hit(const float4* s, float xa, float xb, float ya, float yb,
-                                         float za, float zb, float sqrtTcull) {
-    const float4 a = s[0], b = s[1], c = s[2], d = s[3], e = s[4];
-    const float cx = 0.5f * (xa + xb), cy = 0.5f * (ya + yb), cz = 0.5f * (za + zb);
-    const float dx = (cx - a.x) - a.w, dy = (cy - a.y) - b.x, dz = (cz - a.z) - b.y;
-    // z_c = M (c - mu) = m0 dx + m1 dy + m2 dz
-    const float zx = b.z * dx + c.y * dy + d.x * dz;
-    const float zy = b.w * dx + c.z * dy + d.y * dz;
-    const float zz = c.x * dx + c.w * dy + d.z * dz;
-    const float zc = sqrtf(zx * zx + zy * zy + zz * zz);
-    const float rad = 0.5f * ((xb - xa) * d.w + (yb - ya) * e.x + (zb - za) * e.y);
-    return zc - rad <= sqrtTcull;
+// Row quantities of the Gaussian for the row through voxel centres (., y, z): the row shadow
+// S and the position dx* of the row minimum. One operation sequence for both kernels.
+__device__ __forceinline__ void row_terms(const Rec& R, float fy, float fz, float& dy, float& dz,
+                                          float& S, float& dxs) {
+    dy = (fy - R.mhy) - R.mly;
+    dz = (fz - R.mhz) - R.mlz;
+    S = fmaf(R.pyy * dy, dy, fmaf(R.p2yz * dy, dz, R.pzz * dz * dz));
+    dxs = fmaf(R.c1, dy, R.c2 * dz);
 }
 
-// Row-shadow cull for the row through voxel centres (., y, z).
-__device__ __forceinline__ bool row_hit(const float4* s, float fy, float fz, float Trow) {
-    const float4 a = s[0], b = s[1], e = s[4], f = s[5];
-    const float dy = (fy - a.y) - b.x, dz = (fz - a.z) - b.y;
-    const float q = fmaf(e.w * dy, dy, fmaf(f.x * dy, dz, f.y * dz * dz));
-    return q <= Trow;
+// q at the voxel whose global x index is fx, given the row terms; u = dx is returned too.
+__device__ __forceinline__ float q_at(const Rec& R, float fx, float S, float dxs, float& u) {
+    u = (fx - R.mhx) - R.mlx;
+    const float t = u - dxs;
+    return fmaf(R.a * t, t, S);
 }
 
-// Row set-up: the expansion point of the exponent along the row through (y, z).
-struct RowExp {
-    float qc, twob, a, t0;  // q(x) = qc + t (a t + twob), t = x - x_c = t0 + xb
-    float dy, dz, dxc;      // offsets from the mean; dxc = x_c - mu_x
-};
-
-__device__ __forceinline__ RowExp row_setup(const Rec& R, float fy, float fz, float fx0) {
-    RowExp E;
-    E.dy = (fy - R.mhy) - R.mly;
-    E.dz = (fz - R.mhz) - R.mlz;
-    const float zrx = fmaf(R.m1x, E.dy, R.m2x * E.dz);
-    const float zry = fmaf(R.m1y, E.dy, R.m2y * E.dz);
-    const float zrz = fmaf(R.m1z, E.dy, R.m2z * E.dz);
-    const float b0 = zrx * R.m0x + zry * R.m0y + zrz * R.m0z;
-    // nearest integer voxel to the row's closest point x* = mu_x - b0 / a (brick independent)
-    float xc = rintf((R.mhx - b0 * R.inva) + R.mlx);
-    xc = fminf(fmaxf(xc, -8388608.0f), 8388608.0f);
-    E.dxc = (xc - R.mhx) - R.mlx;
-    const float zcx = fmaf(E.dxc, R.m0x, zrx);
-    const float zcy = fmaf(E.dxc, R.m0y, zry);
-    const float zcz = fmaf(E.dxc, R.m0z, zrz);
-    E.qc = zcx * zcx + zcy * zcy + zcz * zcz;
-    E.twob = 2.0f * (zcx * R.m0x + zcy * R.m0y + zcz * R.m0z);
-    E.a = R.m0x * R.m0x + R.m0y * R.m0y + R.m0z * R.m0z;
-    E.t0 = fx0 - xc;
-    return E;
+// Footprint cull: may the Gaussian reach a voxel centre within 3/2 of (cx, cy, cz) per axis?
+__device__ __forceinline__ bool foot_hit(const float4* s, float cx, float cy, float cz,
+                                         float sqrtTcull) {
+    const Rec R = load_rec(s);
+    float dy, dz, S, dxs, u;
+    row_terms(R, cy, cz, dy, dz, S, dxs);
+    const float qc = q_at(R, cx, S, dxs, u);
+    return sqrtf(fmaxf(qc, 0.0f)) - 1.5f * (R.n0 + R.n1 + R.n2) <= sqrtTcull;
 }
 
 // ------------------------------------------------------------------------ forward
 
-template <int BX, bool kStats>
-__global__ void __launch_bounds__(64) k_render_fwd(const int32_t* __restrict__ brick_off,
-                                                   const int32_t* __restrict__ pair_gid,
-                                                   const float4* __restrict__ rec4, RenderGeo G,
-                                                   float* __restrict__ I, float* __restrict__ W,
-                                                   unsigned long long* __restrict__ stats) {
+template <bool kStats>
+__global__ void __launch_bounds__(256) k_render_fwd(const int32_t* __restrict__ brick_off,
+                                                    const int32_t* __restrict__ pair_gid,
+                                                    const float4* __restrict__ rec4, RenderGeo G,
+                                                    float* __restrict__ I, float* __restrict__ W,
+                                                    unsigned long long* __restrict__ stats) {
     __shared__ float4 srec[kFwdChunk][REC_F4];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nrows = G.bsy * G.bsz;
+    const int nthreads = blockDim.x;
     const int b = blockIdx.x;
     const int bx = b % G.nbx, by = (b / G.nbx) % G.nby, bz = b / (G.nbx * G.nby);
-    const int x0 = bx * BX, y0 = by * G.bsy, z0 = bz * G.bsz;
-    const bool row_ok = tid < nrows;
-    const int y = y0 + tid % G.bsy, z = z0 + tid / G.bsy;
-    const float fy = float(y), fz = float(z), fx0 = float(x0);
-    // this warp's slab of voxel centres
-    const int r_first = warp * 32, r_last = min(nrows, warp * 32 + 32) - 1;
-    const float sxa = fx0, sxb = float(x0 + BX - 1);
-    const float sya = float(y0), syb = float(y0 + G.bsy - 1);
-    const float sza = float(z0 + r_first / G.bsy), szb = float(z0 + r_last / G.bsy);
+    const int wx = warp % G.fx, wy = (warp / G.fx) % G.fy, wz = warp / (G.fx * G.fy);
+    const int ox = bx * G.bsx + wx * 4, oy = by * G.bsy + wy * 4, oz = bz * G.bsz + wz * 4;
+    const int x0 = ox + 2 * (lane & 1), y = oy + ((lane >> 1) & 3), z = oz + (lane >> 3);
+    const float fx0 = float(x0), fx1 = float(x0 + 1), fy = float(y), fz = float(z);
+    const float cx = float(ox) + 1.5f, cy = float(oy) + 1.5f, cz = float(oz) + 1.5f;
 
-    float S[BX], Wa[BX];
-#pragma unroll
-    for (int i = 0; i < BX; ++i) {
-        S[i] = 0.f;
-        Wa[i] = 0.f;
-    }
+    float S0 = 0.f, W0 = 0.f, S1 = 0.f, W1 = 0.f;
     unsigned long long n_eff = 0, n_eval = 0;
     const int start = brick_off[b], end = brick_off[b + 1];
     for (int c0 = start; c0 < end; c0 += kFwdChunk) {
         const int cnt = min(kFwdChunk, end - c0);
         __syncthreads();
-        for (int i = tid; i < cnt * REC_F4; i += blockDim.x) {
+        for (int i = tid; i < cnt * REC_F4; i += nthreads) {
             const int k = i / REC_F4, part = i - k * REC_F4;
             srec[k][part] = rec4[int64_t(pair_gid[c0 + k]) * REC_F4 + part];
         }
         __syncthreads();
-        unsigned long long hits = 0;
-        for (int h = 0; h < cnt; h += 32) {
-            const int k = h + lane;
-            const bool sh = (k < cnt) && slab_hit(srec[k], sxa, sxb, sya, syb, sza, szb, G.sqrtTcull);
-            unsigned m = __ballot_sync(0xffffffffu, sh);
-            while (m) {
-                const int kk = h + __ffs(m) - 1;
-                m &= m - 1;
-                if (row_ok && row_hit(srec[kk], fy, fz, G.Trow)) hits |= 1ull << kk;
+        for (int k0 = 0; k0 < cnt; k0 += 32) {
+            const int k = k0 + lane;
+            const bool hit = (k < cnt) && foot_hit(srec[k], cx, cy, cz, G.sqrtTcull);
+            unsigned mask = __ballot_sync(0xffffffffu, hit);
+            while (mask) {
+                const int kk = k0 + __ffs(mask) - 1;
+                mask &= mask - 1;
+                const Rec R = load_rec(srec[kk]);
+                float dy, dz, S, dxs, u0, u1;
+                row_terms(R, fy, fz, dy, dz, S, dxs);
+                const float q0 = q_at(R, fx0, S, dxs, u0);
+                const float q1 = q_at(R, fx1, S, dxs, u1);
+                float g0 = ex2_approx(-q0), g1 = ex2_approx(-q1);
+                g0 = (q0 <= G.T) ? g0 : 0.0f;
+                g1 = (q1 <= G.T) ? g1 : 0.0f;
+                S0 = fmaf(R.vr, g0, S0);
+                W0 = fmaf(R.r, g0, W0);
+                S1 = fmaf(R.vr, g1, S1);
+                W1 = fmaf(R.r, g1, W1);
+                if (kStats) {
+                    const bool in_yz = y < G.ny && z < G.nz;
+                    n_eff += (in_yz && x0 < G.nx && q0 <= G.T) ? 1 : 0;
+                    n_eff += (in_yz && x0 + 1 < G.nx && q1 <= G.T) ? 1 : 0;
+                    n_eval += 2;
+                }
             }
-        }
-        while (hits) {
-            const int kk = __ffsll(static_cast<long long>(hits)) - 1;
-            hits &= hits - 1;
-            const Rec R = load_rec(srec[kk]);
-            const RowExp E = row_setup(R, fy, fz, fx0);
-#pragma unroll
-            for (int i = 0; i < BX; ++i) {
-                const float t = E.t0 + float(i);
-                const float q = fmaf(t, fmaf(E.a, t, E.twob), E.qc);
-                float g = ex2_approx(-q);
-                g = (q <= G.T) ? g : 0.0f;
-                S[i] = fmaf(R.vr, g, S[i]);
-                Wa[i] = fmaf(R.r, g, Wa[i]);
-                if (kStats) n_eff += (q <= G.T && x0 + i < G.nx) ? 1 : 0;
-            }
-            if (kStats) n_eval += BX;
         }
     }
-    if (row_ok && y < G.ny && z < G.nz) {
+    if (y < G.ny && z < G.nz) {
         const int64_t row = (int64_t(z) * G.ny + y) * G.nx;
-#pragma unroll
-        for (int i = 0; i < BX; ++i) {
-            if (x0 + i < G.nx) {
-                I[row + x0 + i] = S[i] / (Wa[i] > G.eps ? Wa[i] : G.eps);
-                W[row + x0 + i] = Wa[i];
-            }
+        if (x0 < G.nx) {
+            I[row + x0] = S0 / (W0 > G.eps ? W0 : G.eps);
+            W[row + x0] = W0;
         }
-    } else {
-        n_eff = 0;
+        if (x0 + 1 < G.nx) {
+            I[row + x0 + 1] = S1 / (W1 > G.eps ? W1 : G.eps);
+            W[row + x0 + 1] = W1;
+        }
     }
     if (kStats) {
 #pragma unroll
@@ -220,31 +174,8 @@ __global__ void __launch_bounds__(64) k_render_fwd(const int32_t* __restrict__ b
 
 // ------------------------------------------------------------------------ adjoint
 
-// Position of the k-th set bit (k counted from 0) of a 64-bit mask that has more than k.
-__device__ __forceinline__ int select_bit64(unsigned long long m, int k) {
-    int pos = 0;
-    unsigned w = static_cast<unsigned>(m);
-    int c = __popc(w);
-    if (k >= c) {
-        k -= c;
-        w = static_cast<unsigned>(m >> 32);
-        pos = 32;
-    }
-#pragma unroll
-    for (int half = 16; half >= 1; half >>= 1) {
-        const unsigned lowmask = (1u << half) - 1u;
-        c = __popc(w & lowmask);
-        if (k >= c) {
-            k -= c;
-            w >>= half;
-            pos += half;
-        }
-    }
-    return pos;
-}
-
 // Rows of the brick (index rz * bsy + ry) that the Gaussian may reach: per z-row the row
-// shadow is a quadratic in dy, solved for its y-interval (padded by a margin).
+// shadow S(dy, dz) <= Tcull is a quadratic in dy, solved for its y-interval (padded).
 __device__ __forceinline__ unsigned long long brick_row_mask(const Rec& R, const RenderGeo& G,
                                                              int y0, int z0) {
     unsigned long long mask = 0;
@@ -253,7 +184,7 @@ __device__ __forceinline__ unsigned long long brick_row_mask(const Rec& R, const
     for (int rz = 0; rz < G.bsz; ++rz) {
         const float dz = (float(z0 + rz) - R.mhz) - R.mlz;
         const float bq = R.p2yz * dz;
-        const float cq = R.pzz * dz * dz - G.Trow;
+        const float cq = R.pzz * dz * dz - G.Tcull;
         const float disc = bq * bq - 4.0f * R.pyy * cq;
         if (!(disc >= 0.0f)) continue;
         const float sq = sqrtf(disc);
@@ -265,8 +196,7 @@ __device__ __forceinline__ unsigned long long brick_row_mask(const Rec& R, const
         ia = max(ia, 0);
         ib = min(ib, G.bsy - 1);
         if (ia > ib) continue;
-        const unsigned long long bits = ((2ull << (ib - ia)) - 1ull) << (rz * G.bsy + ia);
-        mask |= bits;
+        mask |= ((2ull << (ib - ia)) - 1ull) << (rz * G.bsy + ia);
     }
     return mask;
 }
@@ -277,16 +207,17 @@ __global__ void __launch_bounds__(kBwdThreads) k_render_bwd(
     const int32_t* __restrict__ pair_gmj, const float4* __restrict__ rec4, RenderGeo G,
     const float* __restrict__ Iv, const float* __restrict__ Wv, const float* __restrict__ dIv,
     float* __restrict__ part, float* __restrict__ gacc) {
-    extern __shared__ float4 smem4[];
-    float4(*srec)[REC_F4] = reinterpret_cast<float4(*)[REC_F4]>(smem4);              // [256][7]
-    float2* ab = reinterpret_cast<float2*>(smem4 + kBwdChunk * REC_F4);                  // [rows][BX+1]
-    float(*ipart)[32][12] = reinterpret_cast<float(*)[32][12]>(ab + kMaxRows * (BX + 1));  // [8][32][12]
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ float4 srec[kBwdChunk][REC_F4];
+    __shared__ float2 ab[kMaxRows][BX + 1];        // (dL/dI / W', I') per row voxel
+    __shared__ unsigned long long rmask[kBwdChunk];
+    __shared__ unsigned short order[kBwdChunk];
+    __shared__ int hist[kMaxRows + 2];
+    __shared__ int cursor[kMaxRows + 2];
+    const int tid = threadIdx.x;
     const int b = blockIdx.x;
     const int bx = b % G.nbx, by = (b / G.nbx) % G.nby, bz = b / (G.nbx * G.nby);
     const int x0 = bx * BX, y0 = by * G.bsy, z0 = bz * G.bsz;
     const int nrows = G.bsy * G.bsz;
-    const float fx0 = float(x0);
 
     // Prologue: per-voxel factors. dL/dw_i = (v_i - I') alpha with alpha = dL/dI / max(W, eps)
     // and I' = I where W > eps, else 0 (Eq. 5; below the floor I = S / eps, dI/dw_i = v_i / eps).
@@ -300,7 +231,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_render_bwd(
             alpha = gI / (w > G.eps ? w : G.eps);
             ip = (w > G.eps) ? Iv[idx] : 0.0f;
         }
-        ab[r * (BX + 1) + xb] = make_float2(alpha, ip);
+        ab[r][xb] = make_float2(alpha, ip);
     }
 
     const int start = brick_off[b], end = brick_off[b + 1];
@@ -311,112 +242,94 @@ __global__ void __launch_bounds__(kBwdThreads) k_render_bwd(
             const int k = i / REC_F4, prt = i - k * REC_F4;
             srec[k][prt] = rec4[int64_t(pair_gid[c0 + k]) * REC_F4 + prt];
         }
+        if (tid < kMaxRows + 2) {
+            hist[tid] = 0;
+            cursor[tid] = 0;
+        }
         __syncthreads();
-
-        const int k = warp * 32 + lane;  // chunk-local Gaussian owned by this lane
-        const bool own = k < cnt;
-        unsigned long long rmask = 0;
-        if (own) rmask = brick_row_mask(load_rec(srec[k]), G, y0, z0);
-        const int nmine = __popcll(static_cast<long long>(rmask));
-        int incl = nmine;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
+        // work estimate (rows reached) and a counting sort, most work first
+        int bucket = 0;
+        if (tid < cnt) {
+            const unsigned long long m = brick_row_mask(load_rec(srec[tid]), G, y0, z0);
+            rmask[tid] = m;
+            bucket = kMaxRows - __popcll(static_cast<long long>(m));
+            atomicAdd(&hist[bucket], 1);
         }
-        const int mstart = incl - nmine;
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-
-        float acc[11];
-#pragma unroll
-        for (int q = 0; q < 11; ++q) acc[q] = 0.f;
-
-        for (int b0 = 0; b0 < total; b0 += 32) {
-            const int it = b0 + lane;
-            // owner of item `it`: the last lane whose start is <= it
-            int j = 0;
-#pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-                const int cand = j + step;
-                const int sc = __shfl_sync(0xffffffffu, mstart, cand & 31);
-                if (cand < 32 && sc <= it) j = cand;
+        __syncthreads();
+        if (tid == 0) {
+            int run = 0;
+            for (int i = 0; i <= kMaxRows; ++i) {
+                const int c = hist[i];
+                hist[i] = run;
+                run += c;
             }
-            const unsigned mlo = __shfl_sync(0xffffffffu, static_cast<unsigned>(rmask), j);
-            const unsigned mhi = __shfl_sync(0xffffffffu, static_cast<unsigned>(rmask >> 32), j);
-            const int jstart = __shfl_sync(0xffffffffu, mstart, j);
-            if (it < total) {
-                const unsigned long long om = (static_cast<unsigned long long>(mhi) << 32) | mlo;
-                const int r = select_bit64(om, it - jstart);
-                const int ry = r % G.bsy, rz = r / G.bsy;
-                const Rec R = load_rec(srec[warp * 32 + j]);
-                const RowExp E = row_setup(R, float(y0 + ry), float(z0 + rz), fx0);
-                const float2* abr = ab + r * (BX + 1);
-                float s0 = 0.f, s1 = 0.f, s2 = 0.f, dv = 0.f, dr = 0.f;
-#pragma unroll
-                for (int i = 0; i < BX; ++i) {
-                    const float t = E.t0 + float(i);
-                    const float q = fmaf(t, fmaf(E.a, t, E.twob), E.qc);
-                    float g = ex2_approx(-q);
-                    g = (q <= G.T) ? g : 0.0f;
-                    const float2 av = abr[i];
-                    const float w = R.r * g;
-                    const float gam = (R.v - av.y) * av.x;
-                    dv = fmaf(av.x, w, dv);
-                    dr = fmaf(gam, g, dr);
-                    const float Gw = gam * w;
-                    const float dx = E.dxc + t;
-                    s0 += Gw;
-                    const float tg = Gw * dx;
-                    s1 += tg;
-                    s2 = fmaf(tg, dx, s2);
-                }
-                const float dy = E.dy, dz = E.dz;
-                float* ip = ipart[warp][lane];
-                ip[G_M1X] = s1;
-                ip[G_M1Y] = dy * s0;
-                ip[G_M1Z] = dz * s0;
-                ip[G_M2XX] = s2;
-                ip[G_M2YY] = dy * dy * s0;
-                ip[G_M2ZZ] = dz * dz * s0;
-                ip[G_M2XY] = dy * s1;
-                ip[G_M2XZ] = dz * s1;
-                ip[G_M2YZ] = dy * dz * s0;
-                ip[G_DV] = dv;
-                ip[G_DR] = dr;
-            }
-            __syncwarp();
-            if (own) {
-                const int lo = max(mstart, b0), hi = min(mstart + nmine, b0 + 32);
-                for (int q = lo; q < hi; ++q) {
-                    const float* ip = ipart[warp][q - b0];
-#pragma unroll
-                    for (int m = 0; m < 11; ++m) acc[m] += ip[m];
-                }
-            }
-            __syncwarp();
         }
+        __syncthreads();
+        if (tid < cnt) order[hist[bucket] + atomicAdd(&cursor[bucket], 1)] = static_cast<unsigned short>(tid);
+        __syncthreads();
+        if (tid >= cnt) continue;
 
-        if (own) {
-            const int64_t pos = int64_t(c0) + k;
-            if (kDet) {
-                const int64_t j = pair_gmj[pos];
-                float4* dst = reinterpret_cast<float4*>(part + j * GRAD_FLOATS);
-                dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-                dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
-                dst[2] = make_float4(acc[8], acc[9], acc[10], 0.f);
-            } else if (nmine > 0) {
-                float* dst = gacc + int64_t(pair_gid[pos]) * GRAD_FLOATS;
-#pragma unroll
-                for (int m = 0; m < 11; ++m) atomicAdd(dst + m, acc[m]);
+        const int k = order[tid];
+        const Rec R = load_rec(srec[k]);
+        unsigned long long m = rmask[k];
+        float m1x = 0.f, m1y = 0.f, m1z = 0.f, m2xx = 0.f, m2yy = 0.f, m2zz = 0.f;
+        float m2xy = 0.f, m2xz = 0.f, m2yz = 0.f, dv = 0.f, dr = 0.f;
+        const float mu_x = R.mhx + R.mlx;
+        while (m) {
+            const int r = __ffsll(static_cast<long long>(m)) - 1;
+            m &= m - 1;
+            const int ry = r % G.bsy, rz = r / G.bsy;
+            float dy, dz, S, dxs;
+            row_terms(R, float(y0 + ry), float(z0 + rz), dy, dz, S, dxs);
+            const float hw2 = (G.Tcull - S) * R.inva;
+            if (!(hw2 >= 0.0f)) continue;
+            const float hw = sqrtf(hw2);
+            const float xs = mu_x + dxs;
+            const float pad = 1e-3f + 1e-5f * fabsf(xs);
+            const int xa = max(static_cast<int>(ceilf(fmaxf(xs - hw - pad, float(x0) - 1.0f))), x0);
+            const int xb = min(static_cast<int>(floorf(fminf(xs + hw + pad, float(x0 + BX)))), x0 + BX - 1);
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+            for (int x = xa; x <= xb; ++x) {
+                float u;
+                const float q = q_at(R, float(x), S, dxs, u);
+                float g = ex2_approx(-q);
+                g = (q <= G.T) ? g : 0.0f;
+                const float2 av = ab[r][x - x0];
+                const float w = R.r * g;
+                const float gam = (R.v - av.y) * av.x;
+                dv = fmaf(av.x, w, dv);
+                dr = fmaf(gam, g, dr);
+                const float Gw = gam * w;
+                s0 += Gw;
+                const float tg = Gw * u;
+                s1 += tg;
+                s2 = fmaf(tg, u, s2);
             }
+            m1x += s1;
+            m1y = fmaf(dy, s0, m1y);
+            m1z = fmaf(dz, s0, m1z);
+            m2xx += s2;
+            m2xy = fmaf(dy, s1, m2xy);
+            m2xz = fmaf(dz, s1, m2xz);
+            const float ty = dy * s0;
+            m2yy = fmaf(ty, dy, m2yy);
+            m2yz = fmaf(ty, dz, m2yz);
+            m2zz = fmaf(dz * s0, dz, m2zz);
+        }
+        const int64_t pos = int64_t(c0) + k;
+        if (kDet) {
+            const int64_t j = pair_gmj[pos];
+            float4* dst = reinterpret_cast<float4*>(part + j * GRAD_FLOATS);
+            dst[0] = make_float4(m1x, m1y, m1z, m2xx);
+            dst[1] = make_float4(m2yy, m2zz, m2xy, m2xz);
+            dst[2] = make_float4(m2yz, dv, dr, 0.f);
+        } else if (rmask[k] != 0ull) {
+            float* dst = gacc + int64_t(pair_gid[pos]) * GRAD_FLOATS;
+            const float vals[11] = {m1x, m1y, m1z, m2xx, m2yy, m2zz, m2xy, m2xz, m2yz, dv, dr};
+#pragma unroll
+            for (int q = 0; q < 11; ++q) atomicAdd(dst + q, vals[q]);
         }
     }
-}
-
-template <int BX>
-constexpr size_t bwd_smem_bytes() {
-    return sizeof(float4) * kBwdChunk * REC_F4 + sizeof(float2) * kMaxRows * (BX + 1) +
-           sizeof(float) * 8 * 32 * 12;
 }
 
 // Deterministic reduction: per Gaussian, sum its per-brick partials in Gaussian-major order
@@ -455,37 +368,27 @@ RenderGeo make_geo(const gs_grid* grid, const gs_config* cfg) {
     RenderGeo G;
     G.nx = grid->nx; G.ny = grid->ny; G.nz = grid->nz;
     G.bsx = b.bx; G.bsy = b.by; G.bsz = b.bz;
+    G.fx = b.bx / 4; G.fy = b.by / 4; G.fz = b.bz / 4;
     G.nbx = b.nbx; G.nby = b.nby;
     G.T = kHalfLog2e * cfg->trunc_sigma * cfg->trunc_sigma;
-    G.Trow = G.T * (1.0f + 1e-2f) + 1e-3f;
-    G.sqrtTcull = sqrtf(G.Trow);
+    G.Tcull = G.T * (1.0f + 1e-2f) + 1e-3f;
+    G.sqrtTcull = sqrtf(G.Tcull);
     G.eps = cfg->eps;
     return G;
-}
-
-template <int BX>
-static gs_status launch_fwd(const gs_bins* bins, const RenderGeo& G, float* I, float* W,
-                            unsigned long long* stats, cudaStream_t st) {
-    const int threads = ((G.bsy * G.bsz + 31) / 32) * 32;
-    const float4* rec4 = reinterpret_cast<const float4*>(bins->rec);
-    if (stats)
-        k_render_fwd<BX, true><<<bins->n_bricks, threads, 0, st>>>(bins->brick_off, bins->pair_gid,
-                                                                   rec4, G, I, W, stats);
-    else
-        k_render_fwd<BX, false><<<bins->n_bricks, threads, 0, st>>>(bins->brick_off, bins->pair_gid,
-                                                                    rec4, G, I, W, nullptr);
-    return last_launch_status();
 }
 
 gs_status render_fwd_impl(const gs_bins* bins, const gs_grid* grid, const gs_config* cfg,
                           float* I, float* W, unsigned long long* stats, cudaStream_t st) {
     RenderGeo G = make_geo(grid, cfg);
-    switch (G.bsx) {
-        case 4: return launch_fwd<4>(bins, G, I, W, stats, st);
-        case 8: return launch_fwd<8>(bins, G, I, W, stats, st);
-        case 16: return launch_fwd<16>(bins, G, I, W, stats, st);
-    }
-    return GS_ERR_INVALID_ARG;
+    const int threads = 32 * G.fx * G.fy * G.fz;
+    const float4* rec4 = reinterpret_cast<const float4*>(bins->rec);
+    if (stats)
+        k_render_fwd<true><<<bins->n_bricks, threads, 0, st>>>(bins->brick_off, bins->pair_gid, rec4,
+                                                               G, I, W, stats);
+    else
+        k_render_fwd<false><<<bins->n_bricks, threads, 0, st>>>(bins->brick_off, bins->pair_gid,
+                                                                rec4, G, I, W, nullptr);
+    return last_launch_status();
 }
 
 gs_status bind_workspace(void* base, size_t bytes, int64_t n_gauss, int64_t capacity,
@@ -495,20 +398,8 @@ bool bins_match(const gs_bins* b, const gs_grid* grid, const gs_config* cfg);
 template <int BX, bool kDet>
 static gs_status launch_bwd(const gs_bins* bins, const RenderGeo& G, const float* I, const float* W,
                             const float* dI, const Workspace& ws, cudaStream_t st) {
-    const size_t smem = bwd_smem_bytes<BX>();
-    // Opt in to more than 48 KB of dynamic shared memory once per device.
-    static std::atomic<unsigned long long> attr_done{0};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return GS_ERR_CUDA;
-    const unsigned long long bit = 1ull << (dev & 63);
-    if (!(attr_done.load() & bit)) {
-        if (cudaFuncSetAttribute(k_render_bwd<BX, kDet>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(smem)) != cudaSuccess)
-            return GS_ERR_CUDA;
-        attr_done.fetch_or(bit);
-    }
     const float4* rec4 = reinterpret_cast<const float4*>(bins->rec);
-    k_render_bwd<BX, kDet><<<bins->n_bricks, kBwdThreads, smem, st>>>(
+    k_render_bwd<BX, kDet><<<bins->n_bricks, kBwdThreads, 0, st>>>(
         bins->brick_off, bins->pair_gid, bins->pair_gmj, rec4, G, I, W, dI,
         kDet ? ws.part : nullptr, kDet ? nullptr : ws.gacc);
     return last_launch_status();
