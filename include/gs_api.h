@@ -89,8 +89,9 @@ typedef struct {
  *   brick_off [n_bricks + 1]: pairs of brick b are [brick_off[b], brick_off[b+1]).
  *   pair_gid  [capacity]: Gaussian id of each pair, brick-major, ascending inside a brick.
  *   pair_gmj  [capacity]: position of each brick-major pair in the Gaussian-major order.
+ *   pair_brick [capacity]: linear brick index of each brick-major pair.
  *   gm_off    [n_gauss + 1]: Gaussian-major pair offsets (bricks of one Gaussian ascend).
- *   rec       [n_gauss, 16] float: per-Gaussian render record (internal layout).
+ *   rec       [n_gauss, 20] float: per-Gaussian render record (internal layout).
  *   brange    [n_gauss, 8] int32: brick range lo (x, y, z), hi (x, y, z), pair count, valid.
  *   d_npairs  device int64: pairs needed by the last gs_bin_bricks call.
  *   d_status  device int32: GS_STATUS_* bits of the last gs_bin_bricks call. */
@@ -102,6 +103,7 @@ typedef struct {
     int32_t* brick_off;
     int32_t* pair_gid;
     int32_t* pair_gmj;
+    int32_t* pair_brick;
     int32_t* gm_off;
     float* rec;
     int32_t* brange;

@@ -12,7 +12,8 @@
 //                  histograms, a digit-major scan, and a stable scatter whose in-tile ranks
 //                  come from warp match masks. Stability keeps ascending Gaussian ids inside
 //                  each brick, so the lists are deterministic.
-//   k_finalize     pair_gmj (Gaussian-major position) and pair_gid (owner) per brick-major pair.
+//   k_finalize     pair_gmj (Gaussian-major position), pair_gid (owner) and pair_brick per
+//                  brick-major pair.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -314,7 +315,15 @@ __global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ pa
     r4[0] = make_float4(mh[0], mh[1], mh[2], ml[0]);
     r4[1] = make_float4(ml[1], ml[2], Pyy, P2yz);
     r4[2] = make_float4(Pzz, -d1, -d2, am0);
-    r4[3] = make_float4(inv_a, nrm[0], nrm[1], nrm[2]);
+    // radius of a 4^3 footprint in whitened units: |M d|^2 <= sum_jk |m_j . m_k| (3/2)^2
+    float gsum = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            gsum += fabsf(col[j][0] * col[k][0] + col[j][1] * col[k][1] + col[j][2] * col[k][2]);
+    const float rho4 = 1.5f * sqrtf(gsum);
+    r4[3] = make_float4(inv_a, rho4, nrm[1], nrm[2]);
     r4[4] = make_float4(v * r, r, v, 0.0f);
 }
 
@@ -437,17 +446,20 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     }
 }
 
-__global__ void __launch_bounds__(256) k_finalize(const int32_t* __restrict__ vals,
+__global__ void __launch_bounds__(256) k_finalize(const int32_t* __restrict__ keys,
+                                                  const int32_t* __restrict__ vals,
                                                   const int32_t* __restrict__ gm_gid,
                                                   const int64_t* __restrict__ npairs, int64_t capacity,
                                                   int32_t* __restrict__ pair_gmj,
-                                                  int32_t* __restrict__ pair_gid) {
+                                                  int32_t* __restrict__ pair_gid,
+                                                  int32_t* __restrict__ pair_brick) {
     const int64_t P = valid_pairs(npairs, capacity);
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P;
          i += int64_t(gridDim.x) * blockDim.x) {
         int j = vals[i];
         pair_gmj[i] = j;
         pair_gid[i] = gm_gid[j];
+        pair_brick[i] = keys[i];
     }
 }
 
@@ -460,7 +472,8 @@ using namespace gs;
 namespace {
 
 struct BinsLayout {
-    size_t off_brick_off, off_pair_gid, off_pair_gmj, off_gm_off, off_rec, off_brange, off_npairs,
+    size_t off_brick_off, off_pair_gid, off_pair_gmj, off_pair_brick, off_gm_off, off_rec, off_brange,
+        off_npairs,
         off_status, bytes;
 };
 
@@ -478,6 +491,7 @@ bool bins_layout(int64_t n_gauss, int64_t capacity, int32_t n_bricks, BinsLayout
     L->off_brick_off = take(sizeof(int32_t) * (int64_t(n_bricks) + 1));
     L->off_pair_gid = take(sizeof(int32_t) * cap);
     L->off_pair_gmj = take(sizeof(int32_t) * cap);
+    L->off_pair_brick = take(sizeof(int32_t) * cap);
     L->off_gm_off = take(sizeof(int32_t) * (n + 1));
     L->off_rec = take(sizeof(float) * REC_FLOATS * n);
     L->off_brange = take(sizeof(int32_t) * 8 * n);
@@ -491,6 +505,8 @@ int32_t n_bricks_of(const gs_grid* g, const gs_config* c) {
     BrickGeom b = brick_geom(g, c);
     return b.nbx * b.nby * b.nbz;
 }
+
+int64_t n_voxels_of(const gs_grid* g) { return int64_t(g->nx) * g->ny * g->nz; }
 
 }  // namespace
 
@@ -524,6 +540,7 @@ extern "C" gs_status gs_bins_bind(void* arena, size_t arena_bytes, int64_t n_gau
     out->brick_off = reinterpret_cast<int32_t*>(a + L.off_brick_off);
     out->pair_gid = reinterpret_cast<int32_t*>(a + L.off_pair_gid);
     out->pair_gmj = reinterpret_cast<int32_t*>(a + L.off_pair_gmj);
+    out->pair_brick = reinterpret_cast<int32_t*>(a + L.off_pair_brick);
     out->gm_off = reinterpret_cast<int32_t*>(a + L.off_gm_off);
     out->rec = reinterpret_cast<float*>(a + L.off_rec);
     out->brange = reinterpret_cast<int32_t*>(a + L.off_brange);
@@ -537,8 +554,8 @@ extern "C" size_t gs_workspace_bytes(int64_t n_gauss, int64_t capacity, const gs
     if (validate_grid_cfg(grid, cfg) != GS_OK) return 0;
     if (n_gauss < 0 || capacity < 0 || capacity > kMaxCapacity) return 0;
     Workspace ws;
-    carve_workspace(nullptr, n_gauss, capacity, n_bricks_of(grid, cfg), cfg->deterministic != 0,
-                    &ws);
+    carve_workspace(nullptr, n_gauss, capacity, n_bricks_of(grid, cfg), n_voxels_of(grid),
+                    cfg->deterministic != 0, &ws);
     return ws.bytes;
 }
 
@@ -548,14 +565,16 @@ gs_status bind_workspace(void* base, size_t bytes, int64_t n_gauss, int64_t capa
                          const gs_grid* grid, const gs_config* cfg, Workspace* ws) {
     if (!base) return GS_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(base) % 256 != 0) return GS_ERR_INVALID_ARG;
-    carve_workspace(nullptr, n_gauss, capacity, n_bricks_of(grid, cfg), cfg->deterministic != 0, ws);
+    carve_workspace(nullptr, n_gauss, capacity, n_bricks_of(grid, cfg), n_voxels_of(grid),
+                    cfg->deterministic != 0, ws);
     if (bytes < ws->bytes) return GS_ERR_WORKSPACE;
-    carve_workspace(base, n_gauss, capacity, n_bricks_of(grid, cfg), cfg->deterministic != 0, ws);
+    carve_workspace(base, n_gauss, capacity, n_bricks_of(grid, cfg), n_voxels_of(grid),
+                    cfg->deterministic != 0, ws);
     return GS_OK;
 }
 
 bool bins_match(const gs_bins* b, const gs_grid* grid, const gs_config* cfg) {
-    if (!b || !b->brick_off || !b->pair_gid || !b->pair_gmj || !b->gm_off || !b->rec ||
+    if (!b || !b->brick_off || !b->pair_gid || !b->pair_gmj || !b->pair_brick || !b->gm_off || !b->rec ||
         !b->brange || !b->d_npairs || !b->d_status)
         return false;
     BrickGeom g = brick_geom(grid, cfg);
@@ -649,8 +668,8 @@ gs_status bin_bricks_impl(const float* params, const gs_grid* grid, const gs_con
         int32_t* t = kin; kin = kout; kout = t;
         t = vin; vin = vout; vout = t;
     }
-    k_finalize<<<1184, 256, 0, st>>>(vin, ws.gm_gid, bins->d_npairs, cap, bins->pair_gmj,
-                                     bins->pair_gid);
+    k_finalize<<<1184, 256, 0, st>>>(kin, vin, ws.gm_gid, bins->d_npairs, cap, bins->pair_gmj,
+                                     bins->pair_gid, bins->pair_brick);
     return last_launch_status();
 }
 

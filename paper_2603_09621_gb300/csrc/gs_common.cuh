@@ -25,14 +25,16 @@ namespace gs {
 // with their components along m0 removed. Every term of this form has the size of q itself
 // for voxels inside the ellipsoid, so FP32 keeps its accuracy for strongly anisotropic
 // Gaussians, and the value at a voxel depends only on the voxel and the Gaussian.
-// n_j = |m_j| bound |M (p - c)| <= sum_j h_j n_j over a box of half-extents h (culling).
+// rho4 bounds |M (p - c)| over a 4 x 4 x 4 voxel footprint around its centre c:
+// |M d|^2 <= sum_jk |m_j . m_k| |d_j| |d_k| <= (3/2)^2 sum_jk |m_j . m_k| (culling).
 enum RecField : int {
     R_MHX = 0, R_MHY = 1, R_MHZ = 2,        // mu' head
     R_MLX = 3, R_MLY = 4, R_MLZ = 5,        // mu' tail
     R_PYY = 6, R_P2YZ = 7, R_PZZ = 8,       // row shadow S
     R_C1 = 9, R_C2 = 10,                    // dx* = c1 dy + c2 dz
     R_A = 11, R_INVA = 12,                  // a = |m0|^2 and 1 / a
-    R_N0 = 13, R_N1 = 14, R_N2 = 15,        // column norms of M
+    R_RHO4 = 13,                            // footprint radius (see above)
+    R_N1 = 14, R_N2 = 15,                   // |m1|, |m2| (unused by the kernels)
     R_VR = 16,                              // v * r
     R_R = 17,                               // r
     R_V = 18,                               // v
@@ -85,6 +87,7 @@ struct Workspace {
     long long* scan_tmp;     // block sums of the multi-level scan
     float* part;             // [capacity, 12] per-pair partial gradients (deterministic mode)
     float* gacc;             // [n_gauss, 12] render-space gradient per Gaussian
+    float2* aip;             // [n_voxels] (dL/dI / max(W, eps), I') for the adjoint
     float* l1_part;          // [kL1Blocks]
     int64_t scan_tmp_len;
     int32_t n_tiles;
@@ -105,7 +108,7 @@ inline int64_t scan_tmp_len_for(int64_t n) {
 
 // Carve (or size, if base == nullptr) the workspace. Returns false on overflow.
 inline bool carve_workspace(void* base, int64_t n_gauss, int64_t capacity, int32_t n_bricks,
-                            bool deterministic, Workspace* ws) {
+                            int64_t n_voxels, bool deterministic, Workspace* ws) {
     size_t off = 0;
     auto take = [&](size_t bytes) -> char* {
         size_t o = off;
@@ -132,6 +135,7 @@ inline bool carve_workspace(void* base, int64_t n_gauss, int64_t capacity, int32
     ws->part = reinterpret_cast<float*>(
         take(deterministic ? sizeof(float) * GRAD_FLOATS * cap : 256));
     ws->gacc = reinterpret_cast<float*>(take(sizeof(float) * GRAD_FLOATS * n));
+    ws->aip = reinterpret_cast<float2*>(take(sizeof(float2) * (n_voxels > 0 ? n_voxels : 1)));
     ws->l1_part = reinterpret_cast<float*>(take(sizeof(float) * kL1Blocks));
     ws->bytes = off;
     return true;

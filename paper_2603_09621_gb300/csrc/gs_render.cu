@@ -14,14 +14,13 @@
 // footprint whose centre c is farther than sqrt(T) + 1.5 sum_j |m_j| is missed; a margin
 // absorbs FP32 rounding) and evaluates the hits in ascending Gaussian id, accumulating S and
 // W in registers (deterministic).
-// Adjoint: one lane per staged Gaussian walks exactly the voxels it reaches in the brick:
-// the rows come from the row shadow (per z-row a quadratic in dy) and the voxels of a row
-// from the parabola in dx, so no pair outside the ellipsoid is evaluated. Lanes are given
-// Gaussians in descending order of work (a counting sort of their row counts) so that a warp
-// holds similar loads; the assignment does not affect results, because each Gaussian's
-// partial is summed by one lane in a fixed voxel order. The per-(brick, Gaussian) result goes
-// to a per-pair slot (deterministic mode, reduced later in Gaussian-major order) or to one
-// float atomic per value (fast mode).
+// Adjoint: one thread per (brick, Gaussian) pair walks exactly the voxels the Gaussian
+// reaches in the brick: the rows come from the row shadow (per z-row a quadratic in dy) and
+// the voxels of a row from the parabola in dx, so no pair outside the ellipsoid is evaluated.
+// The per-voxel factors (dL/dI / max(W, eps), I') are precomputed into one float2 volume that
+// stays in L2, so threads need no block-level staging. Each pair's partial is summed by one
+// thread in a fixed voxel order and goes to a per-pair slot (deterministic mode, reduced
+// later in Gaussian-major order) or to one float atomic per value (fast mode).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,8 +31,6 @@
 namespace gs {
 
 constexpr int kFwdChunk = 128;   // Gaussians staged per forward round
-constexpr int kBwdChunk = 256;   // Gaussians staged per adjoint round (one per thread)
-constexpr int kMaxRows = 64;     // rows per brick (by * bz)
 constexpr int kBwdThreads = 256;
 
 struct RenderGeo {
@@ -49,7 +46,7 @@ struct RenderGeo {
 
 struct Rec {
     float mhx, mhy, mhz, mlx, mly, mlz;
-    float pyy, p2yz, pzz, c1, c2, a, inva, n0, n1, n2, vr, r, v;
+    float pyy, p2yz, pzz, c1, c2, a, inva, rho4, vr, r, v;
 };
 
 __device__ __forceinline__ Rec load_rec(const float4* s) {
@@ -58,7 +55,7 @@ __device__ __forceinline__ Rec load_rec(const float4* s) {
     R.mhx = a.x; R.mhy = a.y; R.mhz = a.z; R.mlx = a.w;
     R.mly = b.x; R.mlz = b.y; R.pyy = b.z; R.p2yz = b.w;
     R.pzz = c.x; R.c1 = c.y; R.c2 = c.z; R.a = c.w;
-    R.inva = d.x; R.n0 = d.y; R.n1 = d.z; R.n2 = d.w;
+    R.inva = d.x; R.rho4 = d.y;
     R.vr = e.x; R.r = e.y; R.v = e.z;
     return R;
 }
@@ -87,7 +84,7 @@ __device__ __forceinline__ bool foot_hit(const float4* s, float cx, float cy, fl
     float dy, dz, S, dxs, u;
     row_terms(R, cy, cz, dy, dz, S, dxs);
     const float qc = q_at(R, cx, S, dxs, u);
-    return sqrtf(fmaxf(qc, 0.0f)) - 1.5f * (R.n0 + R.n1 + R.n2) <= sqrtTcull;
+    return sqrtf(fmaxf(qc, 0.0f)) - R.rho4 <= sqrtTcull;
 }
 
 // ------------------------------------------------------------------------ forward
@@ -201,100 +198,62 @@ __device__ __forceinline__ unsigned long long brick_row_mask(const Rec& R, const
     return mask;
 }
 
-template <int BX, bool kDet>
-__global__ void __launch_bounds__(kBwdThreads) k_render_bwd(
-    const int32_t* __restrict__ brick_off, const int32_t* __restrict__ pair_gid,
-    const int32_t* __restrict__ pair_gmj, const float4* __restrict__ rec4, RenderGeo G,
-    const float* __restrict__ Iv, const float* __restrict__ Wv, const float* __restrict__ dIv,
-    float* __restrict__ part, float* __restrict__ gacc) {
-    __shared__ float4 srec[kBwdChunk][REC_F4];
-    __shared__ float2 ab[kMaxRows][BX + 1];        // (dL/dI / W', I') per row voxel
-    __shared__ unsigned long long rmask[kBwdChunk];
-    __shared__ unsigned short order[kBwdChunk];
-    __shared__ int hist[kMaxRows + 2];
-    __shared__ int cursor[kMaxRows + 2];
-    const int tid = threadIdx.x;
-    const int b = blockIdx.x;
-    const int bx = b % G.nbx, by = (b / G.nbx) % G.nby, bz = b / (G.nbx * G.nby);
-    const int x0 = bx * BX, y0 = by * G.bsy, z0 = bz * G.bsz;
-    const int nrows = G.bsy * G.bsz;
-
-    // Prologue: per-voxel factors. dL/dw_i = (v_i - I') alpha with alpha = dL/dI / max(W, eps)
-    // and I' = I where W > eps, else 0 (Eq. 5; below the floor I = S / eps, dI/dw_i = v_i / eps).
-    for (int i = tid; i < nrows * BX; i += blockDim.x) {
-        const int r = i / BX, xb = i - r * BX;
-        const int x = x0 + xb, y = y0 + r % G.bsy, z = z0 + r / G.bsy;
-        float alpha = 0.f, ip = 0.f;
-        if (x < G.nx && y < G.ny && z < G.nz) {
-            const int64_t idx = (int64_t(z) * G.ny + y) * G.nx + x;
-            const float w = Wv[idx], gI = dIv[idx];
-            alpha = gI / (w > G.eps ? w : G.eps);
-            ip = (w > G.eps) ? Iv[idx] : 0.0f;
-        }
-        ab[r][xb] = make_float2(alpha, ip);
+// Per-voxel adjoint factors: dL/dw_i = (v_i - I') alpha with alpha = dL/dI / max(W, eps) and
+// I' = I where W > eps, else 0 (Eq. 5; below the floor I = S / eps, so dI/dw_i = v_i / eps).
+__global__ void __launch_bounds__(256) k_bwd_prep(const float* __restrict__ Iv,
+                                                  const float* __restrict__ Wv,
+                                                  const float* __restrict__ dIv, int64_t n,
+                                                  float eps, float2* __restrict__ aip) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const float w = Wv[i], gI = dIv[i];
+        aip[i] = make_float2(gI / (w > eps ? w : eps), (w > eps) ? Iv[i] : 0.0f);
     }
+}
 
-    const int start = brick_off[b], end = brick_off[b + 1];
-    for (int c0 = start; c0 < end; c0 += kBwdChunk) {
-        const int cnt = min(kBwdChunk, end - c0);
-        __syncthreads();
-        for (int i = tid; i < cnt * REC_F4; i += blockDim.x) {
-            const int k = i / REC_F4, prt = i - k * REC_F4;
-            srec[k][prt] = rec4[int64_t(pair_gid[c0 + k]) * REC_F4 + prt];
-        }
-        if (tid < kMaxRows + 2) {
-            hist[tid] = 0;
-            cursor[tid] = 0;
-        }
-        __syncthreads();
-        // work estimate (rows reached) and a counting sort, most work first
-        int bucket = 0;
-        if (tid < cnt) {
-            const unsigned long long m = brick_row_mask(load_rec(srec[tid]), G, y0, z0);
-            rmask[tid] = m;
-            bucket = kMaxRows - __popcll(static_cast<long long>(m));
-            atomicAdd(&hist[bucket], 1);
-        }
-        __syncthreads();
-        if (tid == 0) {
-            int run = 0;
-            for (int i = 0; i <= kMaxRows; ++i) {
-                const int c = hist[i];
-                hist[i] = run;
-                run += c;
-            }
-        }
-        __syncthreads();
-        if (tid < cnt) order[hist[bucket] + atomicAdd(&cursor[bucket], 1)] = static_cast<unsigned short>(tid);
-        __syncthreads();
-        if (tid >= cnt) continue;
-
-        const int k = order[tid];
-        const Rec R = load_rec(srec[k]);
-        unsigned long long m = rmask[k];
+template <bool kDet>
+__global__ void __launch_bounds__(kBwdThreads) k_render_bwd(
+    const int32_t* __restrict__ pair_gid, const int32_t* __restrict__ pair_gmj,
+    const int32_t* __restrict__ pair_brick, const int64_t* __restrict__ npairs, int64_t capacity,
+    const float4* __restrict__ rec4, RenderGeo G, const float2* __restrict__ aip,
+    float* __restrict__ part, float* __restrict__ gacc) {
+    int64_t P = *npairs;
+    if (P < 0 || P > capacity) P = 0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const int gid = pair_gid[i];
+        const int b = pair_brick[i];
+        const int bx = b % G.nbx, by = (b / G.nbx) % G.nby, bz = b / (G.nbx * G.nby);
+        const int x0 = bx * G.bsx, y0 = by * G.bsy, z0 = bz * G.bsz;
+        const int x1 = min(x0 + G.bsx, G.nx) - 1;
+        const Rec R = load_rec(rec4 + int64_t(gid) * REC_F4);
+        unsigned long long m = brick_row_mask(R, G, y0, z0);
+        const bool any = m != 0ull;
         float m1x = 0.f, m1y = 0.f, m1z = 0.f, m2xx = 0.f, m2yy = 0.f, m2zz = 0.f;
         float m2xy = 0.f, m2xz = 0.f, m2yz = 0.f, dv = 0.f, dr = 0.f;
         const float mu_x = R.mhx + R.mlx;
         while (m) {
             const int r = __ffsll(static_cast<long long>(m)) - 1;
             m &= m - 1;
-            const int ry = r % G.bsy, rz = r / G.bsy;
+            const int y = y0 + r % G.bsy, z = z0 + r / G.bsy;
+            if (y >= G.ny || z >= G.nz) continue;
             float dy, dz, S, dxs;
-            row_terms(R, float(y0 + ry), float(z0 + rz), dy, dz, S, dxs);
+            row_terms(R, float(y), float(z), dy, dz, S, dxs);
             const float hw2 = (G.Tcull - S) * R.inva;
             if (!(hw2 >= 0.0f)) continue;
             const float hw = sqrtf(hw2);
             const float xs = mu_x + dxs;
             const float pad = 1e-3f + 1e-5f * fabsf(xs);
             const int xa = max(static_cast<int>(ceilf(fmaxf(xs - hw - pad, float(x0) - 1.0f))), x0);
-            const int xb = min(static_cast<int>(floorf(fminf(xs + hw + pad, float(x0 + BX)))), x0 + BX - 1);
+            const int xb = min(static_cast<int>(floorf(fminf(xs + hw + pad, float(x1) + 1.0f))), x1);
+            const float2* arow = aip + (int64_t(z) * G.ny + y) * G.nx;
             float s0 = 0.f, s1 = 0.f, s2 = 0.f;
             for (int x = xa; x <= xb; ++x) {
                 float u;
                 const float q = q_at(R, float(x), S, dxs, u);
                 float g = ex2_approx(-q);
                 g = (q <= G.T) ? g : 0.0f;
-                const float2 av = ab[r][x - x0];
+                const float2 av = arow[x];
                 const float w = R.r * g;
                 const float gam = (R.v - av.y) * av.x;
                 dv = fmaf(av.x, w, dv);
@@ -316,15 +275,14 @@ __global__ void __launch_bounds__(kBwdThreads) k_render_bwd(
             m2yz = fmaf(ty, dz, m2yz);
             m2zz = fmaf(dz * s0, dz, m2zz);
         }
-        const int64_t pos = int64_t(c0) + k;
         if (kDet) {
-            const int64_t j = pair_gmj[pos];
+            const int64_t j = pair_gmj[i];
             float4* dst = reinterpret_cast<float4*>(part + j * GRAD_FLOATS);
             dst[0] = make_float4(m1x, m1y, m1z, m2xx);
             dst[1] = make_float4(m2yy, m2zz, m2xy, m2xz);
             dst[2] = make_float4(m2yz, dv, dr, 0.f);
-        } else if (rmask[k] != 0ull) {
-            float* dst = gacc + int64_t(pair_gid[pos]) * GRAD_FLOATS;
+        } else if (any) {
+            float* dst = gacc + int64_t(gid) * GRAD_FLOATS;
             const float vals[11] = {m1x, m1y, m1z, m2xx, m2yy, m2zz, m2xy, m2xz, m2yz, dv, dr};
 #pragma unroll
             for (int q = 0; q < 11; ++q) atomicAdd(dst + q, vals[q]);
@@ -395,26 +353,22 @@ gs_status bind_workspace(void* base, size_t bytes, int64_t n_gauss, int64_t capa
                          const gs_grid* grid, const gs_config* cfg, Workspace* ws);
 bool bins_match(const gs_bins* b, const gs_grid* grid, const gs_config* cfg);
 
-template <int BX, bool kDet>
+template <bool kDet>
 static gs_status launch_bwd(const gs_bins* bins, const RenderGeo& G, const float* I, const float* W,
                             const float* dI, const Workspace& ws, cudaStream_t st) {
+    const int64_t nv = int64_t(G.nx) * G.ny * G.nz;
+    const int64_t pb = (nv + 255) / 256;
+    k_bwd_prep<<<static_cast<unsigned>(pb < 65536 ? pb : 65536), 256, 0, st>>>(I, W, dI, nv, G.eps,
+                                                                              ws.aip);
+    gs_status s = last_launch_status();
+    if (s != GS_OK) return s;
+    if (bins->capacity == 0) return GS_OK;
+    const int64_t gb = (bins->capacity + kBwdThreads - 1) / kBwdThreads;
     const float4* rec4 = reinterpret_cast<const float4*>(bins->rec);
-    k_render_bwd<BX, kDet><<<bins->n_bricks, kBwdThreads, 0, st>>>(
-        bins->brick_off, bins->pair_gid, bins->pair_gmj, rec4, G, I, W, dI,
-        kDet ? ws.part : nullptr, kDet ? nullptr : ws.gacc);
+    k_render_bwd<kDet><<<static_cast<unsigned>(gb < 1048576 ? gb : 1048576), kBwdThreads, 0, st>>>(
+        bins->pair_gid, bins->pair_gmj, bins->pair_brick, bins->d_npairs, bins->capacity, rec4, G,
+        ws.aip, kDet ? ws.part : nullptr, kDet ? nullptr : ws.gacc);
     return last_launch_status();
-}
-
-template <bool kDet>
-static gs_status launch_bwd_bx(const gs_bins* bins, const RenderGeo& G, const float* I,
-                               const float* W, const float* dI, const Workspace& ws,
-                               cudaStream_t st) {
-    switch (G.bsx) {
-        case 4: return launch_bwd<4, kDet>(bins, G, I, W, dI, ws, st);
-        case 8: return launch_bwd<8, kDet>(bins, G, I, W, dI, ws, st);
-        case 16: return launch_bwd<16, kDet>(bins, G, I, W, dI, ws, st);
-    }
-    return GS_ERR_INVALID_ARG;
 }
 
 // Render-space adjoint into ws.gacc [N, 12] (no parameter chain).
@@ -424,7 +378,7 @@ gs_status render_bwd_geo(const gs_bins* bins, const gs_grid* grid, const gs_conf
     RenderGeo G = make_geo(grid, cfg);
     const int64_t N = bins->n_gauss;
     if (cfg->deterministic) {
-        gs_status s = launch_bwd_bx<true>(bins, G, I, W, dI, ws, st);
+        gs_status s = launch_bwd<true>(bins, G, I, W, dI, ws, st);
         if (s != GS_OK) return s;
         if (after_kernel && !after_kernel()) return GS_ERR_CUDA;
         if (N > 0) {
@@ -436,7 +390,7 @@ gs_status render_bwd_geo(const gs_bins* bins, const gs_grid* grid, const gs_conf
     }
     if (N > 0 && cudaMemsetAsync(ws.gacc, 0, sizeof(float) * GRAD_FLOATS * N, st) != cudaSuccess)
         return GS_ERR_CUDA;
-    gs_status s = launch_bwd_bx<false>(bins, G, I, W, dI, ws, st);
+    gs_status s = launch_bwd<false>(bins, G, I, W, dI, ws, st);
     if (s != GS_OK) return s;
     if (after_kernel && !after_kernel()) return GS_ERR_CUDA;
     return GS_OK;

@@ -39,7 +39,8 @@ class gs_bins(ctypes.Structure):
                 ("n_bricks", ctypes.c_int32), ("nbx", ctypes.c_int32), ("nby", ctypes.c_int32),
                 ("nbz", ctypes.c_int32), ("brick_off", ctypes.c_void_p),
                 ("pair_gid", ctypes.c_void_p), ("pair_gmj", ctypes.c_void_p),
-                ("gm_off", ctypes.c_void_p), ("rec", ctypes.c_void_p),
+                ("pair_brick", ctypes.c_void_p), ("gm_off", ctypes.c_void_p),
+                ("rec", ctypes.c_void_p),
                 ("brange", ctypes.c_void_p), ("d_npairs", ctypes.c_void_p),
                 ("d_status", ctypes.c_void_p)]
 
@@ -235,11 +236,14 @@ class Bins:
     def pair_gmj(self, n=None):
         return self._view(self.c.pair_gmj, self.capacity if n is None else n, torch.int32)
 
+    def pair_brick(self, n=None):
+        return self._view(self.c.pair_brick, self.capacity if n is None else n, torch.int32)
+
     def gm_off(self):
         return self._view(self.c.gm_off, self.n_gauss + 1, torch.int32)
 
     def rec(self):
-        return self._view(self.c.rec, self.n_gauss * 16, torch.float32).view(-1, 16)
+        return self._view(self.c.rec, self.n_gauss * 20, torch.float32).view(-1, 20)
 
     def brange(self):
         return self._view(self.c.brange, self.n_gauss * 8, torch.int32).view(-1, 8)

@@ -61,7 +61,7 @@ def test_bins_forward_workload_bit_exact():
     assert _compare(params, og) > 4096
 
 
-@pytest.mark.parametrize("brick", [(8, 8, 8), (8, 8, 4), (4, 4, 4), (16, 8, 8)])
+@pytest.mark.parametrize("brick", [(8, 8, 8), (8, 8, 4), (4, 4, 4), (16, 8, 4)])
 def test_bins_ragged_offset_grid(brick):
     """Ragged dims (partial edge bricks), non-unit spacing, offset origin, brick shapes."""
     import oracle
