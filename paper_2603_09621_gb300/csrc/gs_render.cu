@@ -14,13 +14,14 @@
 // footprint whose centre c is farther than sqrt(T) + 1.5 sum_j |m_j| is missed; a margin
 // absorbs FP32 rounding) and evaluates the hits in ascending Gaussian id, accumulating S and
 // W in registers (deterministic).
-// Adjoint: one thread per (brick, Gaussian) pair walks exactly the voxels the Gaussian
-// reaches in the brick: the rows come from the row shadow (per z-row a quadratic in dy) and
-// the voxels of a row from the parabola in dx, so no pair outside the ellipsoid is evaluated.
-// The per-voxel factors (dL/dI / max(W, eps), I') are precomputed into one float2 volume that
-// stays in L2, so threads need no block-level staging. Each pair's partial is summed by one
-// thread in a fixed voxel order and goes to a per-pair slot (deterministic mode, reduced
-// later in Gaussian-major order) or to one float atomic per value (fast mode).
+// Adjoint: one thread per (brick, Gaussian) pair evaluates the brick rows the Gaussian
+// reaches (the row shadow, per z-row a quadratic in dy), each row as bx predicated voxel
+// slots, so lanes never diverge inside a row. A planning pass stores every pair's row mask
+// and counting-sorts the pairs by their number of rows, so a warp runs pairs of equal
+// length. The per-voxel factors (dL/dI / max(W, eps), I') are precomputed into one float2
+// volume that stays in L2. Each pair's partial is summed by one thread in a fixed voxel order
+// (the processing order does not change results) and goes to a per-pair slot (deterministic
+// mode, reduced later in Gaussian-major order) or to one float atomic per value (fast mode).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -211,82 +212,137 @@ __global__ void __launch_bounds__(256) k_bwd_prep(const float* __restrict__ Iv,
     }
 }
 
-template <bool kDet>
+// Planning: each pair's row mask and a block-aggregated histogram of row counts.
+__global__ void __launch_bounds__(kBwdThreads) k_bwd_plan(
+    const int32_t* __restrict__ pair_gid, const int32_t* __restrict__ pair_brick,
+    const int64_t* __restrict__ npairs, int64_t capacity, const float4* __restrict__ rec4,
+    RenderGeo G, unsigned long long* __restrict__ rowmask, int32_t* __restrict__ hist) {
+    __shared__ int sh[65];
+    for (int i = threadIdx.x; i < 65; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    int64_t P = *npairs;
+    if (P < 0 || P > capacity) P = 0;
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < P) {
+        const int b = pair_brick[i];
+        const int by = (b / G.nbx) % G.nby, bz = b / (G.nbx * G.nby);
+        const Rec R = load_rec(rec4 + int64_t(pair_gid[i]) * REC_F4);
+        const unsigned long long m = brick_row_mask(R, G, by * G.bsy, bz * G.bsz);
+        rowmask[i] = m;
+        atomicAdd(&sh[__popcll(static_cast<long long>(m))], 1);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 65; k += blockDim.x)
+        if (sh[k]) atomicAdd(&hist[k], sh[k]);
+}
+
+// Offsets of the row-count buckets, most rows first; resets the cursors.
+__global__ void k_bwd_plan_offsets(int32_t* __restrict__ hist) {
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int k = 64; k >= 0; --k) {
+            hist[68 + k] = run;
+            run += hist[k];
+            hist[136 + k] = 0;
+        }
+    }
+}
+
+// Scatter pair indices into row-count order (block-aggregated cursors).
+__global__ void __launch_bounds__(kBwdThreads) k_bwd_plan_scatter(
+    const int64_t* __restrict__ npairs, int64_t capacity,
+    const unsigned long long* __restrict__ rowmask, int32_t* __restrict__ hist,
+    int32_t* __restrict__ order) {
+    __shared__ int sh[65];
+    __shared__ int base[65];
+    for (int k = threadIdx.x; k < 65; k += blockDim.x) sh[k] = 0;
+    __syncthreads();
+    int64_t P = *npairs;
+    if (P < 0 || P > capacity) P = 0;
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    int c = 0, local = 0;
+    if (i < P) {
+        c = __popcll(static_cast<long long>(rowmask[i]));
+        local = atomicAdd(&sh[c], 1);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 65; k += blockDim.x)
+        base[k] = sh[k] ? hist[68 + k] + atomicAdd(&hist[136 + k], sh[k]) : 0;
+    __syncthreads();
+    if (i < P) order[base[c] + local] = static_cast<int32_t>(i);
+}
+
+template <int BX, bool kDet>
 __global__ void __launch_bounds__(kBwdThreads) k_render_bwd(
     const int32_t* __restrict__ pair_gid, const int32_t* __restrict__ pair_gmj,
     const int32_t* __restrict__ pair_brick, const int64_t* __restrict__ npairs, int64_t capacity,
     const float4* __restrict__ rec4, RenderGeo G, const float2* __restrict__ aip,
+    const unsigned long long* __restrict__ rowmask, const int32_t* __restrict__ order,
     float* __restrict__ part, float* __restrict__ gacc) {
     int64_t P = *npairs;
     if (P < 0 || P > capacity) P = 0;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P;
-         i += int64_t(gridDim.x) * blockDim.x) {
-        const int gid = pair_gid[i];
-        const int b = pair_brick[i];
-        const int bx = b % G.nbx, by = (b / G.nbx) % G.nby, bz = b / (G.nbx * G.nby);
-        const int x0 = bx * G.bsx, y0 = by * G.bsy, z0 = bz * G.bsz;
-        const int x1 = min(x0 + G.bsx, G.nx) - 1;
-        const Rec R = load_rec(rec4 + int64_t(gid) * REC_F4);
-        unsigned long long m = brick_row_mask(R, G, y0, z0);
-        const bool any = m != 0ull;
-        float m1x = 0.f, m1y = 0.f, m1z = 0.f, m2xx = 0.f, m2yy = 0.f, m2zz = 0.f;
-        float m2xy = 0.f, m2xz = 0.f, m2yz = 0.f, dv = 0.f, dr = 0.f;
-        const float mu_x = R.mhx + R.mlx;
-        while (m) {
-            const int r = __ffsll(static_cast<long long>(m)) - 1;
-            m &= m - 1;
-            const int y = y0 + r % G.bsy, z = z0 + r / G.bsy;
-            if (y >= G.ny || z >= G.nz) continue;
-            float dy, dz, S, dxs;
-            row_terms(R, float(y), float(z), dy, dz, S, dxs);
-            const float hw2 = (G.Tcull - S) * R.inva;
-            if (!(hw2 >= 0.0f)) continue;
-            const float hw = sqrtf(hw2);
-            const float xs = mu_x + dxs;
-            const float pad = 1e-3f + 1e-5f * fabsf(xs);
-            const int xa = max(static_cast<int>(ceilf(fmaxf(xs - hw - pad, float(x0) - 1.0f))), x0);
-            const int xb = min(static_cast<int>(floorf(fminf(xs + hw + pad, float(x1) + 1.0f))), x1);
-            const float2* arow = aip + (int64_t(z) * G.ny + y) * G.nx;
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-            for (int x = xa; x <= xb; ++x) {
-                float u;
-                const float q = q_at(R, float(x), S, dxs, u);
-                float g = ex2_approx(-q);
-                g = (q <= G.T) ? g : 0.0f;
-                const float2 av = arow[x];
-                const float w = R.r * g;
-                const float gam = (R.v - av.y) * av.x;
-                dv = fmaf(av.x, w, dv);
-                dr = fmaf(gam, g, dr);
-                const float Gw = gam * w;
-                s0 += Gw;
-                const float tg = Gw * u;
-                s1 += tg;
-                s2 = fmaf(tg, u, s2);
-            }
-            m1x += s1;
-            m1y = fmaf(dy, s0, m1y);
-            m1z = fmaf(dz, s0, m1z);
-            m2xx += s2;
-            m2xy = fmaf(dy, s1, m2xy);
-            m2xz = fmaf(dz, s1, m2xz);
-            const float ty = dy * s0;
-            m2yy = fmaf(ty, dy, m2yy);
-            m2yz = fmaf(ty, dz, m2yz);
-            m2zz = fmaf(dz * s0, dz, m2zz);
-        }
-        if (kDet) {
-            const int64_t j = pair_gmj[i];
-            float4* dst = reinterpret_cast<float4*>(part + j * GRAD_FLOATS);
-            dst[0] = make_float4(m1x, m1y, m1z, m2xx);
-            dst[1] = make_float4(m2yy, m2zz, m2xy, m2xz);
-            dst[2] = make_float4(m2yz, dv, dr, 0.f);
-        } else if (any) {
-            float* dst = gacc + int64_t(gid) * GRAD_FLOATS;
-            const float vals[11] = {m1x, m1y, m1z, m2xx, m2yy, m2zz, m2xy, m2xz, m2yz, dv, dr};
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= P) return;
+    const int64_t i = order[t];
+    const int gid = pair_gid[i];
+    const int b = pair_brick[i];
+    const int bx = b % G.nbx, by = (b / G.nbx) % G.nby, bz = b / (G.nbx * G.nby);
+    const int x0 = bx * BX, y0 = by * G.bsy, z0 = bz * G.bsz;
+    const int x1 = min(x0 + BX, G.nx) - 1;
+    const Rec R = load_rec(rec4 + int64_t(gid) * REC_F4);
+    unsigned long long m = rowmask[i];
+    const bool any = m != 0ull;
+    float m1x = 0.f, m1y = 0.f, m1z = 0.f, m2xx = 0.f, m2yy = 0.f, m2zz = 0.f;
+    float m2xy = 0.f, m2xz = 0.f, m2yz = 0.f, dv = 0.f, dr = 0.f;
+    while (m) {
+        const int r = __ffsll(static_cast<long long>(m)) - 1;
+        m &= m - 1;
+        const int y = min(y0 + r % G.bsy, G.ny - 1), z = min(z0 + r / G.bsy, G.nz - 1);
+        const bool row_in = (y0 + r % G.bsy < G.ny) && (z0 + r / G.bsy < G.nz);
+        float dy, dz, S, dxs;
+        row_terms(R, float(y), float(z), dy, dz, S, dxs);
+        const float2* arow = aip + (int64_t(z) * G.ny + y) * G.nx;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
 #pragma unroll
-            for (int q = 0; q < 11; ++q) atomicAdd(dst + q, vals[q]);
+        for (int xb = 0; xb < BX; ++xb) {
+            const int x = x0 + xb;
+            float u;
+            const float q = q_at(R, float(x), S, dxs, u);
+            const bool in = row_in && (x <= x1) && (q <= G.T);
+            const float g = in ? ex2_approx(-q) : 0.0f;
+            const float2 av = arow[min(x, x1)];
+            const float w = R.r * g;
+            const float gam = (R.v - av.y) * av.x;
+            dv = fmaf(av.x, w, dv);
+            dr = fmaf(gam, g, dr);
+            const float Gw = gam * w;
+            s0 += Gw;
+            const float tg = Gw * u;
+            s1 += tg;
+            s2 = fmaf(tg, u, s2);
         }
+        m1x += s1;
+        m1y = fmaf(dy, s0, m1y);
+        m1z = fmaf(dz, s0, m1z);
+        m2xx += s2;
+        m2xy = fmaf(dy, s1, m2xy);
+        m2xz = fmaf(dz, s1, m2xz);
+        const float ty = dy * s0;
+        m2yy = fmaf(ty, dy, m2yy);
+        m2yz = fmaf(ty, dz, m2yz);
+        m2zz = fmaf(dz * s0, dz, m2zz);
+    }
+    if (kDet) {
+        const int64_t j = pair_gmj[i];
+        float4* dst = reinterpret_cast<float4*>(part + j * GRAD_FLOATS);
+        dst[0] = make_float4(m1x, m1y, m1z, m2xx);
+        dst[1] = make_float4(m2yy, m2zz, m2xy, m2xz);
+        dst[2] = make_float4(m2yz, dv, dr, 0.f);
+    } else if (any) {
+        float* dst = gacc + int64_t(gid) * GRAD_FLOATS;
+        const float vals[11] = {m1x, m1y, m1z, m2xx, m2yy, m2zz, m2xy, m2xz, m2yz, dv, dr};
+#pragma unroll
+        for (int q = 0; q < 11; ++q) atomicAdd(dst + q, vals[q]);
     }
 }
 
@@ -353,7 +409,7 @@ gs_status bind_workspace(void* base, size_t bytes, int64_t n_gauss, int64_t capa
                          const gs_grid* grid, const gs_config* cfg, Workspace* ws);
 bool bins_match(const gs_bins* b, const gs_grid* grid, const gs_config* cfg);
 
-template <bool kDet>
+template <int BX, bool kDet>
 static gs_status launch_bwd(const gs_bins* bins, const RenderGeo& G, const float* I, const float* W,
                             const float* dI, const Workspace& ws, cudaStream_t st) {
     const int64_t nv = int64_t(G.nx) * G.ny * G.nz;
@@ -363,12 +419,33 @@ static gs_status launch_bwd(const gs_bins* bins, const RenderGeo& G, const float
     gs_status s = last_launch_status();
     if (s != GS_OK) return s;
     if (bins->capacity == 0) return GS_OK;
-    const int64_t gb = (bins->capacity + kBwdThreads - 1) / kBwdThreads;
+    const unsigned gb = static_cast<unsigned>((bins->capacity + kBwdThreads - 1) / kBwdThreads);
     const float4* rec4 = reinterpret_cast<const float4*>(bins->rec);
-    k_render_bwd<kDet><<<static_cast<unsigned>(gb < 1048576 ? gb : 1048576), kBwdThreads, 0, st>>>(
+    if (cudaMemsetAsync(ws.bwd_hist, 0, sizeof(int32_t) * 68, st) != cudaSuccess) return GS_ERR_CUDA;
+    k_bwd_plan<<<gb, kBwdThreads, 0, st>>>(bins->pair_gid, bins->pair_brick, bins->d_npairs,
+                                           bins->capacity, rec4, G, ws.rowmask, ws.bwd_hist);
+    if ((s = last_launch_status()) != GS_OK) return s;
+    k_bwd_plan_offsets<<<1, 32, 0, st>>>(ws.bwd_hist);
+    if ((s = last_launch_status()) != GS_OK) return s;
+    k_bwd_plan_scatter<<<gb, kBwdThreads, 0, st>>>(bins->d_npairs, bins->capacity, ws.rowmask,
+                                                   ws.bwd_hist, ws.order);
+    if ((s = last_launch_status()) != GS_OK) return s;
+    k_render_bwd<BX, kDet><<<gb, kBwdThreads, 0, st>>>(
         bins->pair_gid, bins->pair_gmj, bins->pair_brick, bins->d_npairs, bins->capacity, rec4, G,
-        ws.aip, kDet ? ws.part : nullptr, kDet ? nullptr : ws.gacc);
+        ws.aip, ws.rowmask, ws.order, kDet ? ws.part : nullptr, kDet ? nullptr : ws.gacc);
     return last_launch_status();
+}
+
+template <bool kDet>
+static gs_status launch_bwd_bx(const gs_bins* bins, const RenderGeo& G, const float* I,
+                               const float* W, const float* dI, const Workspace& ws,
+                               cudaStream_t st) {
+    switch (G.bsx) {
+        case 4: return launch_bwd<4, kDet>(bins, G, I, W, dI, ws, st);
+        case 8: return launch_bwd<8, kDet>(bins, G, I, W, dI, ws, st);
+        case 16: return launch_bwd<16, kDet>(bins, G, I, W, dI, ws, st);
+    }
+    return GS_ERR_INVALID_ARG;
 }
 
 // Render-space adjoint into ws.gacc [N, 12] (no parameter chain).
@@ -378,7 +455,7 @@ gs_status render_bwd_geo(const gs_bins* bins, const gs_grid* grid, const gs_conf
     RenderGeo G = make_geo(grid, cfg);
     const int64_t N = bins->n_gauss;
     if (cfg->deterministic) {
-        gs_status s = launch_bwd<true>(bins, G, I, W, dI, ws, st);
+        gs_status s = launch_bwd_bx<true>(bins, G, I, W, dI, ws, st);
         if (s != GS_OK) return s;
         if (after_kernel && !after_kernel()) return GS_ERR_CUDA;
         if (N > 0) {
@@ -390,7 +467,7 @@ gs_status render_bwd_geo(const gs_bins* bins, const gs_grid* grid, const gs_conf
     }
     if (N > 0 && cudaMemsetAsync(ws.gacc, 0, sizeof(float) * GRAD_FLOATS * N, st) != cudaSuccess)
         return GS_ERR_CUDA;
-    gs_status s = launch_bwd<false>(bins, G, I, W, dI, ws, st);
+    gs_status s = launch_bwd_bx<false>(bins, G, I, W, dI, ws, st);
     if (s != GS_OK) return s;
     if (after_kernel && !after_kernel()) return GS_ERR_CUDA;
     return GS_OK;
