@@ -88,9 +88,6 @@ struct Workspace {
     float* part;             // [capacity, 12] per-pair partial gradients (deterministic mode)
     float* gacc;             // [n_gauss, 12] render-space gradient per Gaussian
     float2* aip;             // [n_voxels] (dL/dI / max(W, eps), I') for the adjoint
-    unsigned long long* rowmask;  // [capacity] rows of its brick that each pair reaches
-    int32_t* order;          // [capacity] pairs sorted by descending row count
-    int32_t* bwd_hist;       // [3 * 68] row-count histogram, offsets, cursors
     float* l1_part;          // [kL1Blocks]
     int64_t scan_tmp_len;
     int32_t n_tiles;
@@ -139,9 +136,6 @@ inline bool carve_workspace(void* base, int64_t n_gauss, int64_t capacity, int32
         take(deterministic ? sizeof(float) * GRAD_FLOATS * cap : 256));
     ws->gacc = reinterpret_cast<float*>(take(sizeof(float) * GRAD_FLOATS * n));
     ws->aip = reinterpret_cast<float2*>(take(sizeof(float2) * (n_voxels > 0 ? n_voxels : 1)));
-    ws->rowmask = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * cap));
-    ws->order = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * cap));
-    ws->bwd_hist = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * 3 * 68));
     ws->l1_part = reinterpret_cast<float*>(take(sizeof(float) * kL1Blocks));
     ws->bytes = off;
     return true;

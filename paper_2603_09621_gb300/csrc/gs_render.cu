@@ -16,12 +16,13 @@
 // W in registers (deterministic).
 // Adjoint: one thread per (brick, Gaussian) pair evaluates the brick rows the Gaussian
 // reaches (the row shadow, per z-row a quadratic in dy), each row as bx predicated voxel
-// slots, so lanes never diverge inside a row. A planning pass stores every pair's row mask
-// and counting-sorts the pairs by their number of rows, so a warp runs pairs of equal
-// length. The per-voxel factors (dL/dI / max(W, eps), I') are precomputed into one float2
-// volume that stays in L2. Each pair's partial is summed by one thread in a fixed voxel order
-// (the processing order does not change results) and goes to a per-pair slot (deterministic
-// mode, reduced later in Gaussian-major order) or to one float atomic per value (fast mode).
+// slots, so lanes never diverge inside a row. A block takes 256 consecutive brick-major pairs
+// (one or two bricks), computes their row masks and counting-sorts them by number of rows in
+// shared memory, so each warp runs pairs of equal length while the block keeps its bricks'
+// locality in L1/L2. The per-voxel factors (dL/dI / max(W, eps), I') are precomputed into
+// one float2 volume. Each pair's partial is summed by one thread in a fixed voxel order (the
+// processing order does not change results) and goes to a per-pair slot (deterministic mode,
+// reduced later in Gaussian-major order) or to one float atomic per value (fast mode).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -212,93 +213,73 @@ __global__ void __launch_bounds__(256) k_bwd_prep(const float* __restrict__ Iv,
     }
 }
 
-// Planning: each pair's row mask and a block-aggregated histogram of row counts.
-__global__ void __launch_bounds__(kBwdThreads) k_bwd_plan(
-    const int32_t* __restrict__ pair_gid, const int32_t* __restrict__ pair_brick,
-    const int64_t* __restrict__ npairs, int64_t capacity, const float4* __restrict__ rec4,
-    RenderGeo G, unsigned long long* __restrict__ rowmask, int32_t* __restrict__ hist) {
-    __shared__ int sh[65];
-    for (int i = threadIdx.x; i < 65; i += blockDim.x) sh[i] = 0;
-    __syncthreads();
-    int64_t P = *npairs;
-    if (P < 0 || P > capacity) P = 0;
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < P) {
-        const int b = pair_brick[i];
-        const int by = (b / G.nbx) % G.nby, bz = b / (G.nbx * G.nby);
-        const Rec R = load_rec(rec4 + int64_t(pair_gid[i]) * REC_F4);
-        const unsigned long long m = brick_row_mask(R, G, by * G.bsy, bz * G.bsz);
-        rowmask[i] = m;
-        atomicAdd(&sh[__popcll(static_cast<long long>(m))], 1);
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < 65; k += blockDim.x)
-        if (sh[k]) atomicAdd(&hist[k], sh[k]);
-}
-
-// Offsets of the row-count buckets, most rows first; resets the cursors.
-__global__ void k_bwd_plan_offsets(int32_t* __restrict__ hist) {
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int k = 64; k >= 0; --k) {
-            hist[68 + k] = run;
-            run += hist[k];
-            hist[136 + k] = 0;
-        }
-    }
-}
-
-// Scatter pair indices into row-count order (block-aggregated cursors).
-__global__ void __launch_bounds__(kBwdThreads) k_bwd_plan_scatter(
-    const int64_t* __restrict__ npairs, int64_t capacity,
-    const unsigned long long* __restrict__ rowmask, int32_t* __restrict__ hist,
-    int32_t* __restrict__ order) {
-    __shared__ int sh[65];
-    __shared__ int base[65];
-    for (int k = threadIdx.x; k < 65; k += blockDim.x) sh[k] = 0;
-    __syncthreads();
-    int64_t P = *npairs;
-    if (P < 0 || P > capacity) P = 0;
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    int c = 0, local = 0;
-    if (i < P) {
-        c = __popcll(static_cast<long long>(rowmask[i]));
-        local = atomicAdd(&sh[c], 1);
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < 65; k += blockDim.x)
-        base[k] = sh[k] ? hist[68 + k] + atomicAdd(&hist[136 + k], sh[k]) : 0;
-    __syncthreads();
-    if (i < P) order[base[c] + local] = static_cast<int32_t>(i);
-}
-
 template <int BX, bool kDet>
-__global__ void __launch_bounds__(kBwdThreads) k_render_bwd(
+__global__ void __launch_bounds__(kBwdThreads, 4) k_render_bwd(
     const int32_t* __restrict__ pair_gid, const int32_t* __restrict__ pair_gmj,
     const int32_t* __restrict__ pair_brick, const int64_t* __restrict__ npairs, int64_t capacity,
     const float4* __restrict__ rec4, RenderGeo G, const float2* __restrict__ aip,
-    const unsigned long long* __restrict__ rowmask, const int32_t* __restrict__ order,
     float* __restrict__ part, float* __restrict__ gacc) {
+    __shared__ float4 srec[kBwdThreads][REC_F4];
+    __shared__ unsigned long long smask[kBwdThreads];
+    __shared__ unsigned short sorder[kBwdThreads];
+    __shared__ int hist[66];
+    __shared__ int cursor[66];
     int64_t P = *npairs;
     if (P < 0 || P > capacity) P = 0;
-    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (t >= P) return;
-    const int64_t i = order[t];
-    const int gid = pair_gid[i];
+    const int64_t base = int64_t(blockIdx.x) * kBwdThreads;
+    if (base >= P) return;
+    const int tid = threadIdx.x;
+    const int nvalid = static_cast<int>(min(int64_t(kBwdThreads), P - base));
+    if (tid < 66) {
+        hist[tid] = 0;
+        cursor[tid] = 0;
+    }
+    __syncthreads();
+    // row mask of this thread's pair, staged record, histogram of row counts (most first)
+    int bucket = 0;
+    if (tid < nvalid) {
+        const int64_t i = base + tid;
+        const int b = pair_brick[i];
+        const int by = (b / G.nbx) % G.nby, bz = b / (G.nbx * G.nby);
+        const float4* src = rec4 + int64_t(pair_gid[i]) * REC_F4;
+#pragma unroll
+        for (int k = 0; k < REC_F4; ++k) srec[tid][k] = src[k];
+        const unsigned long long m = brick_row_mask(load_rec(srec[tid]), G, by * G.bsy, bz * G.bsz);
+        smask[tid] = m;
+        bucket = 64 - __popcll(static_cast<long long>(m));
+        atomicAdd(&hist[bucket], 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int run = 0;
+        for (int k = 0; k <= 64; ++k) {
+            const int c = hist[k];
+            hist[k] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    if (tid < nvalid) sorder[hist[bucket] + atomicAdd(&cursor[bucket], 1)] = static_cast<unsigned short>(tid);
+    __syncthreads();
+    if (tid >= nvalid) return;
+
+    const int lt = sorder[tid];
+    const int64_t i = base + lt;
     const int b = pair_brick[i];
     const int bx = b % G.nbx, by = (b / G.nbx) % G.nby, bz = b / (G.nbx * G.nby);
     const int x0 = bx * BX, y0 = by * G.bsy, z0 = bz * G.bsz;
     const int x1 = min(x0 + BX, G.nx) - 1;
-    const Rec R = load_rec(rec4 + int64_t(gid) * REC_F4);
-    unsigned long long m = rowmask[i];
+    const Rec R = load_rec(srec[lt]);
+    unsigned long long m = smask[lt];
     const bool any = m != 0ull;
     float m1x = 0.f, m1y = 0.f, m1z = 0.f, m2xx = 0.f, m2yy = 0.f, m2zz = 0.f;
     float m2xy = 0.f, m2xz = 0.f, m2yz = 0.f, dv = 0.f, dr = 0.f;
     while (m) {
         const int r = __ffsll(static_cast<long long>(m)) - 1;
         m &= m - 1;
-        const int y = min(y0 + r % G.bsy, G.ny - 1), z = min(z0 + r / G.bsy, G.nz - 1);
-        const bool row_in = (y0 + r % G.bsy < G.ny) && (z0 + r / G.bsy < G.nz);
+        const int yr = y0 + r % G.bsy, zr = z0 + r / G.bsy;
+        const bool row_in = (yr < G.ny) && (zr < G.nz);
+        const int y = min(yr, G.ny - 1), z = min(zr, G.nz - 1);
         float dy, dz, S, dxs;
         row_terms(R, float(y), float(z), dy, dz, S, dxs);
         const float2* arow = aip + (int64_t(z) * G.ny + y) * G.nx;
@@ -339,7 +320,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_render_bwd(
         dst[1] = make_float4(m2yy, m2zz, m2xy, m2xz);
         dst[2] = make_float4(m2yz, dv, dr, 0.f);
     } else if (any) {
-        float* dst = gacc + int64_t(gid) * GRAD_FLOATS;
+        float* dst = gacc + int64_t(pair_gid[i]) * GRAD_FLOATS;
         const float vals[11] = {m1x, m1y, m1z, m2xx, m2yy, m2zz, m2xy, m2xz, m2yz, dv, dr};
 #pragma unroll
         for (int q = 0; q < 11; ++q) atomicAdd(dst + q, vals[q]);
@@ -421,18 +402,9 @@ static gs_status launch_bwd(const gs_bins* bins, const RenderGeo& G, const float
     if (bins->capacity == 0) return GS_OK;
     const unsigned gb = static_cast<unsigned>((bins->capacity + kBwdThreads - 1) / kBwdThreads);
     const float4* rec4 = reinterpret_cast<const float4*>(bins->rec);
-    if (cudaMemsetAsync(ws.bwd_hist, 0, sizeof(int32_t) * 68, st) != cudaSuccess) return GS_ERR_CUDA;
-    k_bwd_plan<<<gb, kBwdThreads, 0, st>>>(bins->pair_gid, bins->pair_brick, bins->d_npairs,
-                                           bins->capacity, rec4, G, ws.rowmask, ws.bwd_hist);
-    if ((s = last_launch_status()) != GS_OK) return s;
-    k_bwd_plan_offsets<<<1, 32, 0, st>>>(ws.bwd_hist);
-    if ((s = last_launch_status()) != GS_OK) return s;
-    k_bwd_plan_scatter<<<gb, kBwdThreads, 0, st>>>(bins->d_npairs, bins->capacity, ws.rowmask,
-                                                   ws.bwd_hist, ws.order);
-    if ((s = last_launch_status()) != GS_OK) return s;
     k_render_bwd<BX, kDet><<<gb, kBwdThreads, 0, st>>>(
         bins->pair_gid, bins->pair_gmj, bins->pair_brick, bins->d_npairs, bins->capacity, rec4, G,
-        ws.aip, ws.rowmask, ws.order, kDet ? ws.part : nullptr, kDet ? nullptr : ws.gacc);
+        ws.aip, kDet ? ws.part : nullptr, kDet ? nullptr : ws.gacc);
     return last_launch_status();
 }
 
