@@ -63,7 +63,7 @@ typedef struct {
 } gs_grid;
 
 /* Rendering options.
- *   brick: brick shape in voxels (x, y, z): x in {4, 8, 16}, y and z multiples of 4,
+ *   brick: brick shape in voxels (x, y, z): x and y in {4, 8, 16}, z a multiple of 4,
  *          y * z <= 64 and x * y * z <= 512. Sec. 3.3 uses 8 x 8 x 4; the default is 8 x 8 x 8.
  *          Output does not depend on it.
  *   trunc_sigma: Mahalanobis truncation radius (3.0: the 3-sigma ellipsoids of Sec. 3.3).

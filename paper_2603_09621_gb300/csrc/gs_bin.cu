@@ -36,6 +36,7 @@ gs_status validate_grid_cfg(const gs_grid* g, const gs_config* c) {
     }
     // rows of bx voxels along x (bx in {4, 8, 16}), at most 64 rows per brick
     if (c->brick[0] != 4 && c->brick[0] != 8 && c->brick[0] != 16) return GS_ERR_INVALID_ARG;
+    if (c->brick[1] != 4 && c->brick[1] != 8 && c->brick[1] != 16) return GS_ERR_INVALID_ARG;
     if (c->brick[1] * c->brick[2] > 64) return GS_ERR_INVALID_ARG;
     if (c->brick[0] * c->brick[1] * c->brick[2] > 512) return GS_ERR_INVALID_ARG;
     if (!(c->trunc_sigma > 0.0f) || !isfinite(c->trunc_sigma)) return GS_ERR_INVALID_ARG;

@@ -40,6 +40,7 @@ struct RenderGeo {
     int bsx, bsy, bsz;  // brick shape
     int fx, fy, fz;     // 4^3 footprints per brick along each axis
     int nbx, nby;
+    int bsy_shift, bsy_mask;  // row r of a brick is (y, z) = (r & mask, r >> shift)
     float T;            // (log2 e / 2) trunc_sigma^2: a pair contributes when q <= T
     float Tcull;        // cull bound on q: T (1 + 1e-2) + 1e-3
     float sqrtTcull;    // sqrt(Tcull)
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(256) k_bwd_prep(const float* __restrict__ Iv,
 }
 
 template <int BX, bool kDet>
-__global__ void __launch_bounds__(kBwdThreads, 4) k_render_bwd(
+__global__ void __launch_bounds__(kBwdThreads, 3) k_render_bwd(
     const int32_t* __restrict__ pair_gid, const int32_t* __restrict__ pair_gmj,
     const int32_t* __restrict__ pair_brick, const int64_t* __restrict__ npairs, int64_t capacity,
     const float4* __restrict__ rec4, RenderGeo G, const float2* __restrict__ aip,
@@ -269,39 +270,53 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_render_bwd(
     const int bx = b % G.nbx, by = (b / G.nbx) % G.nby, bz = b / (G.nbx * G.nby);
     const int x0 = bx * BX, y0 = by * G.bsy, z0 = bz * G.bsz;
     const int x1 = min(x0 + BX, G.nx) - 1;
+    const bool full_row = (x1 == x0 + BX - 1) && ((G.nx & 1) == 0);  // 16-byte aligned rows
     const Rec R = load_rec(srec[lt]);
     unsigned long long m = smask[lt];
     const bool any = m != 0ull;
+    // Accumulated per pair with h = gamma g (gamma = dL/dw): dr = sum h, dv = r sum alpha g,
+    // and the moments of G = gamma w = r h are r times the moments of h.
     float m1x = 0.f, m1y = 0.f, m1z = 0.f, m2xx = 0.f, m2yy = 0.f, m2zz = 0.f;
-    float m2xy = 0.f, m2xz = 0.f, m2yz = 0.f, dv = 0.f, dr = 0.f;
+    float m2xy = 0.f, m2xz = 0.f, m2yz = 0.f, dvp = 0.f, dr = 0.f;
+    const float ux0 = (float(x0) - R.mhx) - R.mlx;
     while (m) {
         const int r = __ffsll(static_cast<long long>(m)) - 1;
         m &= m - 1;
-        const int yr = y0 + r % G.bsy, zr = z0 + r / G.bsy;
+        const int yr = y0 + (r & G.bsy_mask), zr = z0 + (r >> G.bsy_shift);
         const bool row_in = (yr < G.ny) && (zr < G.nz);
         const int y = min(yr, G.ny - 1), z = min(zr, G.nz - 1);
         float dy, dz, S, dxs;
         row_terms(R, float(y), float(z), dy, dz, S, dxs);
-        const float2* arow = aip + (int64_t(z) * G.ny + y) * G.nx;
+        const float2* arow = aip + (int64_t(z) * G.ny + y) * G.nx + x0;
+        float2 av[BX];
+        if (full_row) {
+            const float4* a4 = reinterpret_cast<const float4*>(arow);
+#pragma unroll
+            for (int k = 0; k < BX / 2; ++k) {
+                const float4 v = a4[k];
+                av[2 * k] = make_float2(v.x, v.y);
+                av[2 * k + 1] = make_float2(v.z, v.w);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < BX; ++k) av[k] = arow[min(k, x1 - x0)];
+        }
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
 #pragma unroll
         for (int xb = 0; xb < BX; ++xb) {
-            const int x = x0 + xb;
-            float u;
-            const float q = q_at(R, float(x), S, dxs, u);
-            const bool in = row_in && (x <= x1) && (q <= G.T);
+            const float u = ux0 + float(xb);
+            const float t = u - dxs;
+            const float q = fmaf(R.a * t, t, S);
+            const bool in = row_in && (x0 + xb <= x1) && (q <= G.T);
             const float g = in ? ex2_approx(-q) : 0.0f;
-            const float2 av = arow[min(x, x1)];
-            const float w = R.r * g;
-            const float gam = (R.v - av.y) * av.x;
-            dv = fmaf(av.x, w, dv);
-            dr = fmaf(gam, g, dr);
-            const float Gw = gam * w;
-            s0 += Gw;
-            const float tg = Gw * u;
+            const float h = (R.v - av[xb].y) * av[xb].x * g;
+            dvp = fmaf(av[xb].x, g, dvp);
+            s0 += h;
+            const float tg = h * u;
             s1 += tg;
             s2 = fmaf(tg, u, s2);
         }
+        dr += s0;
         m1x += s1;
         m1y = fmaf(dy, s0, m1y);
         m1z = fmaf(dz, s0, m1z);
@@ -313,6 +328,10 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_render_bwd(
         m2yz = fmaf(ty, dz, m2yz);
         m2zz = fmaf(dz * s0, dz, m2zz);
     }
+    const float rr = R.r;
+    const float dv = rr * dvp;
+    m1x *= rr; m1y *= rr; m1z *= rr;
+    m2xx *= rr; m2yy *= rr; m2zz *= rr; m2xy *= rr; m2xz *= rr; m2yz *= rr;
     if (kDet) {
         const int64_t j = pair_gmj[i];
         float4* dst = reinterpret_cast<float4*>(part + j * GRAD_FLOATS);
@@ -364,6 +383,8 @@ RenderGeo make_geo(const gs_grid* grid, const gs_config* cfg) {
     G.nx = grid->nx; G.ny = grid->ny; G.nz = grid->nz;
     G.bsx = b.bx; G.bsy = b.by; G.bsz = b.bz;
     G.fx = b.bx / 4; G.fy = b.by / 4; G.fz = b.bz / 4;
+    G.bsy_shift = (b.by == 4) ? 2 : ((b.by == 8) ? 3 : 4);
+    G.bsy_mask = b.by - 1;
     G.nbx = b.nbx; G.nby = b.nby;
     G.T = kHalfLog2e * cfg->trunc_sigma * cfg->trunc_sigma;
     G.Tcull = G.T * (1.0f + 1e-2f) + 1e-3f;
