@@ -345,7 +345,7 @@ def run_ours(args, world, rank, local):
     ms_step = 1000.0 * t_max / args.steps
 
     # roofline of the dominant render kernel (effective pairs per launch / mean duration)
-    names = ["binning", "forward_render", "profile_l1", "adjoint_render", "reduce_chain", "adam"]
+    names = ["binning", "forward_render", "profile_l1", "adjoint_render", "reduce_chain_adam", "end"]
     per_phase = {n: phase_ms[i] / args.steps for i, n in enumerate(names)}
     kern = "k_render_bwd" if per_phase["adjoint_render"] >= per_phase["forward_render"] else "k_render_fwd"
     t_k = (per_phase["adjoint_render"] if kern == "k_render_bwd" else per_phase["forward_render"]) / 1e3

@@ -222,14 +222,15 @@ gs_status gs_init_lattice(const float* lr, const gs_grid* hr_grid, int32_t s, in
 /* One zero-shot fitting iteration (all device work, no host synchronisation; the step can
  * be captured in a CUDA graph): bin, forward render, z box slice profile, L1 loss against
  * lr_target, its adjoint, adjoint render, Adam. Every pointer is device memory:
- *   params, grad, m, v [n_gauss, 12]; I, W, dI [nz, ny, nx]; lr_pred [nz / s, ny, nx]
- *   (after the step it holds dL/dLR); lr_target [nz / s, ny, nx]; d_loss float scalar (the
- *   loss of this step's forward pass); d_step int32 (Adam step counter); bins bound for
- *   n_gauss; ws workspace. On return grad holds dL/d(params) of this step.
+ *   params, grad, m, v [n_gauss, 12]; I, W [nz, ny, nx]; lr_pred [nz / s, ny, nx] (after the
+ *   step it holds dL/dLR); lr_target [nz / s, ny, nx]; d_loss float scalar (the loss of this
+ *   step's forward pass); d_step int32 (Adam step counter); bins bound for n_gauss; ws
+ *   workspace. On return grad holds dL/d(params) of this step.
  * phase_events: NULL, or GS_FIT_PHASES cudaEvent_t handles (host) recorded on `stream` at
  *   the start and after each phase: [0] start, [1] binning, [2] forward render, [3] slice
- *   profile + L1 + adjoint profile, [4] adjoint render kernel, [5] gradient reduction and
- *   parameter chain, [6] Adam. n_phase_events is 0 or GS_FIT_PHASES. */
+ *   profile + L1 + adjoint profile (with the adjoint's per-voxel factors), [4] adjoint render
+ *   kernel, [5] gradient reduction + parameter chain + Adam, [6] end (same as [5]).
+ *   n_phase_events is 0 or GS_FIT_PHASES. */
 #define GS_FIT_PHASES 7
 typedef struct {
     gs_grid grid;
@@ -245,7 +246,6 @@ typedef struct {
     gs_bins bins;
     float* I;
     float* W;
-    float* dI;
     float* lr_pred;
     const float* lr_target;
     float* d_loss;

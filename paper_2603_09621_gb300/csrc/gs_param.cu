@@ -31,15 +31,10 @@ struct ChainGeo {
     int signal_mode, a_act, t_act;
 };
 
-__global__ void __launch_bounds__(256) k_param_bwd(const float* __restrict__ params,
-                                                   const float* __restrict__ gacc, int64_t N,
-                                                   ChainGeo C, float* __restrict__ dparams) {
-    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (g >= N) return;
-    const float4* p4 = reinterpret_cast<const float4*>(params + g * 12);
-    const float4 a0 = p4[0], a1 = p4[1], a2 = p4[2];
-    const float p[12] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
-    float4* d4 = reinterpret_cast<float4*>(dparams + g * 12);
+// dL/d(raw params) of one Gaussian from its render-space gradient g[11] (see above).
+// Returns false (and zeros) for an invalid Gaussian.
+__device__ __forceinline__ void chain_one(const float* p, const float* gv, const ChainGeo& C,
+                                          float* out) {
     bool ok = true;
 #pragma unroll
     for (int k = 0; k < 12; ++k) ok = ok && isfinite(p[k]);
@@ -48,22 +43,20 @@ __global__ void __launch_bounds__(256) k_param_bwd(const float* __restrict__ par
     const float nn = p[6] * p[6] + p[7] * p[7] + p[8] * p[8] + p[9] * p[9];
     ok = ok && (nn > 0.0f);
     if (!ok) {
-        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        d4[0] = z; d4[1] = z; d4[2] = z;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) out[k] = 0.0f;
         return;
     }
-    const float4* g4 = reinterpret_cast<const float4*>(gacc + g * GRAD_FLOATS);
-    const float4 b0 = g4[0], b1 = g4[1], b2 = g4[2];
-    const float m1[3] = {b0.x * C.h[0], b0.y * C.h[1], b0.z * C.h[2]};  // H m1
+    const float m1[3] = {gv[G_M1X] * C.h[0], gv[G_M1Y] * C.h[1], gv[G_M1Z] * C.h[2]};  // H m1
     // M2 (index space) -> G = -1/2 H M2 H
     float Gm[3][3];
-    Gm[0][0] = -0.5f * C.h[0] * C.h[0] * b0.w;
-    Gm[1][1] = -0.5f * C.h[1] * C.h[1] * b1.x;
-    Gm[2][2] = -0.5f * C.h[2] * C.h[2] * b1.y;
-    Gm[0][1] = Gm[1][0] = -0.5f * C.h[0] * C.h[1] * b1.z;
-    Gm[0][2] = Gm[2][0] = -0.5f * C.h[0] * C.h[2] * b1.w;
-    Gm[1][2] = Gm[2][1] = -0.5f * C.h[1] * C.h[2] * b2.x;
-    const float dv = b2.y, dr = b2.z;
+    Gm[0][0] = -0.5f * C.h[0] * C.h[0] * gv[G_M2XX];
+    Gm[1][1] = -0.5f * C.h[1] * C.h[1] * gv[G_M2YY];
+    Gm[2][2] = -0.5f * C.h[2] * C.h[2] * gv[G_M2ZZ];
+    Gm[0][1] = Gm[1][0] = -0.5f * C.h[0] * C.h[1] * gv[G_M2XY];
+    Gm[0][2] = Gm[2][0] = -0.5f * C.h[0] * C.h[2] * gv[G_M2XZ];
+    Gm[1][2] = Gm[2][1] = -0.5f * C.h[1] * C.h[2] * gv[G_M2YZ];
+    const float dv = gv[G_DV], dr = gv[G_DR];
 
     float s[3], D[3];
 #pragma unroll
@@ -90,7 +83,6 @@ __global__ void __launch_bounds__(256) k_param_bwd(const float* __restrict__ par
 #pragma unroll
         for (int b = 0; b < 3; ++b)
             Ci[a][b] = R[a][0] * R[b][0] * D[0] + R[a][1] * R[b][1] * D[1] + R[a][2] * R[b][2] * D[2];
-    float out[12];
 #pragma unroll
     for (int a = 0; a < 3; ++a) out[a] = Ci[a][0] * m1[0] + Ci[a][1] * m1[1] + Ci[a][2] * m1[2];
     // G R (3x3)
@@ -135,9 +127,33 @@ __global__ void __launch_bounds__(256) k_param_bwd(const float* __restrict__ par
     }
     out[10] = C.a_act ? dA * A * (1.0f - A) : dA;
     out[11] = C.t_act ? dT * T * (1.0f - T) : dT;
-    d4[0] = make_float4(out[0], out[1], out[2], out[3]);
-    d4[1] = make_float4(out[4], out[5], out[6], out[7]);
-    d4[2] = make_float4(out[8], out[9], out[10], out[11]);
+}
+
+__device__ __forceinline__ void load12(const float* src, float* d) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    const float4 a = s4[0], b = s4[1], c = s4[2];
+    d[0] = a.x; d[1] = a.y; d[2] = a.z; d[3] = a.w;
+    d[4] = b.x; d[5] = b.y; d[6] = b.z; d[7] = b.w;
+    d[8] = c.x; d[9] = c.y; d[10] = c.z; d[11] = c.w;
+}
+
+__device__ __forceinline__ void store12(float* dst, const float* d) {
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    d4[0] = make_float4(d[0], d[1], d[2], d[3]);
+    d4[1] = make_float4(d[4], d[5], d[6], d[7]);
+    d4[2] = make_float4(d[8], d[9], d[10], d[11]);
+}
+
+__global__ void __launch_bounds__(256) k_param_bwd(const float* __restrict__ params,
+                                                   const float* __restrict__ gacc, int64_t N,
+                                                   ChainGeo C, float* __restrict__ dparams) {
+    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= N) return;
+    float p[12], gv[12], out[12];
+    load12(params + g * 12, p);
+    load12(gacc + g * GRAD_FLOATS, gv);
+    chain_one(p, gv, C, out);
+    store12(dparams + g * 12, out);
 }
 
 gs_status launch_param_bwd(const float* params, const float* gacc, int64_t n, const gs_grid* grid,
@@ -164,25 +180,84 @@ __device__ __forceinline__ int lr_group(int col) {
     return col < 3 ? 0 : (col < 6 ? 1 : (col < 10 ? 2 : (col == 10 ? 3 : 4)));
 }
 
+struct AdamCoef {
+    float bc1, rs_bc2;
+};
+
+__device__ __forceinline__ AdamCoef adam_coef(const AdamLr& hp, const int32_t* d_step) {
+    const int t = *d_step + 1;
+    // bias corrections 1 - beta^t = -expm1(t log beta), accurate for small t (1 - beta ~ 1e-3)
+    AdamCoef c;
+    c.bc1 = -expm1f(float(t) * hp.log_b1);
+    c.rs_bc2 = 1.0f / sqrtf(-expm1f(float(t) * hp.log_b2));
+    return c;
+}
+
+__device__ __forceinline__ float adam_one(float& p, float gr, float& m, float& v, float lr,
+                                          const AdamLr& hp, const AdamCoef& c) {
+    const float mi = hp.beta1 * m + hp.omb1 * gr;
+    const float vi = hp.beta2 * v + hp.omb2 * gr * gr;
+    m = mi;
+    v = vi;
+    const float denom = sqrtf(vi) * c.rs_bc2 + hp.eps;
+    p -= (lr / c.bc1) * mi / denom;
+    return p;
+}
+
 __global__ void __launch_bounds__(256) k_adam(float* __restrict__ params, const float* __restrict__ grad,
                                               float* __restrict__ m, float* __restrict__ v, int64_t n,
                                               AdamLr hp, const int32_t* __restrict__ d_step) {
-    const int t = *d_step + 1;
-    // bias corrections 1 - beta^t = -expm1(t log beta), accurate for small t (1 - beta ~ 1e-3)
-    const float bc1 = -expm1f(float(t) * hp.log_b1);
-    const float bc2 = -expm1f(float(t) * hp.log_b2);
-    const float rs_bc2 = 1.0f / sqrtf(bc2);
+    const AdamCoef c = adam_coef(hp, d_step);
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += int64_t(gridDim.x) * blockDim.x) {
-        const float gr = grad[i];
-        const float mi = hp.beta1 * m[i] + hp.omb1 * gr;
-        const float vi = hp.beta2 * v[i] + hp.omb2 * gr * gr;
+        float p = params[i], mi = m[i], vi = v[i];
+        adam_one(p, grad[i], mi, vi, hp.lr[lr_group(static_cast<int>(i % 12))], hp, c);
+        params[i] = p;
         m[i] = mi;
         v[i] = vi;
-        const float lr = hp.lr[lr_group(static_cast<int>(i % 12))];
-        const float denom = sqrtf(vi) * rs_bc2 + hp.eps;
-        params[i] -= (lr / bc1) * mi / denom;
     }
+}
+
+// Fitting step tail, one thread per Gaussian: sum the per-brick partials in Gaussian-major
+// order (deterministic mode) or take the atomically accumulated gradient, chain it to the
+// raw parameters (written to grad), and apply Adam to params, m, v.
+template <bool kDet>
+__global__ void __launch_bounds__(256) k_chain_adam(
+    float* __restrict__ params, float* __restrict__ grad, float* __restrict__ m,
+    float* __restrict__ v, const float* __restrict__ part, const float* __restrict__ gacc,
+    const int32_t* __restrict__ gm_off, const int64_t* __restrict__ npairs, int64_t capacity,
+    int64_t N, ChainGeo C, AdamLr hp, const int32_t* __restrict__ d_step) {
+    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= N) return;
+    float gv[12];
+    if (kDet) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) gv[k] = 0.f;
+        const int64_t P = *npairs;
+        if (P >= 0 && P <= capacity) {
+            const int a = gm_off[g], e = gm_off[g + 1];
+            for (int j = a; j < e; ++j) {
+                float t[12];
+                load12(part + int64_t(j) * GRAD_FLOATS, t);
+#pragma unroll
+                for (int k = 0; k < 11; ++k) gv[k] += t[k];
+            }
+        }
+    } else {
+        load12(gacc + g * GRAD_FLOATS, gv);
+    }
+    float p[12], out[12], mm[12], vv[12];
+    load12(params + g * 12, p);
+    chain_one(p, gv, C, out);
+    store12(grad + g * 12, out);
+    load12(m + g * 12, mm);
+    load12(v + g * 12, vv);
+    const AdamCoef c = adam_coef(hp, d_step);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) adam_one(p[k], out[k], mm[k], vv[k], hp.lr[lr_group(k)], hp, c);
+    store12(params + g * 12, p);
+    store12(m + g * 12, mm);
+    store12(v + g * 12, vv);
 }
 
 __global__ void k_step_inc(int32_t* d_step) { *d_step += 1; }
@@ -242,6 +317,54 @@ __global__ void __launch_bounds__(256) k_init_lattice(const float* __restrict__ 
 
 using namespace gs;
 
+namespace gs {
+static AdamLr make_adam_lr(const gs_adam* hp) {
+    AdamLr a;
+    a.lr[0] = hp->lr_mu;
+    a.lr[1] = hp->lr_scale;
+    a.lr[2] = hp->lr_rot;
+    a.lr[3] = hp->lr_a;
+    a.lr[4] = hp->lr_t;
+    a.beta1 = static_cast<float>(hp->beta1);
+    a.beta2 = static_cast<float>(hp->beta2);
+    a.omb1 = static_cast<float>(1.0 - hp->beta1);
+    a.omb2 = static_cast<float>(1.0 - hp->beta2);
+    a.log_b1 = static_cast<float>(log(hp->beta1 > 0.0 ? hp->beta1 : 1e-300));
+    a.log_b2 = static_cast<float>(log(hp->beta2 > 0.0 ? hp->beta2 : 1e-300));
+    a.eps = static_cast<float>(hp->eps);
+    return a;
+}
+
+static bool adam_ok(const gs_adam* hp) {
+    return hp->beta1 >= 0.0 && hp->beta1 < 1.0 && hp->beta2 >= 0.0 && hp->beta2 < 1.0 &&
+           hp->eps > 0.0;
+}
+
+gs_status launch_chain_adam(float* params, float* grad, float* m, float* v, const float* part,
+                            const float* gacc, const gs_bins* bins, int64_t n,
+                            const gs_grid* grid, const gs_config* cfg, const gs_adam* hp,
+                            int32_t* d_step, cudaStream_t st) {
+    if (!adam_ok(hp)) return GS_ERR_INVALID_ARG;
+    ChainGeo C;
+    for (int k = 0; k < 3; ++k) C.h[k] = grid->h[k];
+    C.signal_mode = cfg->signal_mode;
+    C.a_act = cfg->a_act;
+    C.t_act = cfg->t_act;
+    const AdamLr a = make_adam_lr(hp);
+    const unsigned gb = static_cast<unsigned>((n + 255) / 256);
+    if (cfg->deterministic)
+        k_chain_adam<true><<<gb, 256, 0, st>>>(params, grad, m, v, part, gacc, bins->gm_off,
+                                               bins->d_npairs, bins->capacity, n, C, a, d_step);
+    else
+        k_chain_adam<false><<<gb, 256, 0, st>>>(params, grad, m, v, part, gacc, bins->gm_off,
+                                                bins->d_npairs, bins->capacity, n, C, a, d_step);
+    gs_status s = last_launch_status();
+    if (s != GS_OK) return s;
+    k_step_inc<<<1, 1, 0, st>>>(d_step);
+    return last_launch_status();
+}
+}  // namespace gs
+
 extern "C" gs_status gs_signal_proxy(const float* T1, const float* T2, int64_t n, float TR, float TE,
                                      float* T_out, gs_stream stream) {
     if (n < 0) return GS_ERR_INVALID_ARG;
@@ -260,22 +383,8 @@ extern "C" gs_status gs_adam_step(float* params, const float* grad, float* m, fl
     if (n_gauss > 0 && (!params || !grad || !m || !v)) return GS_ERR_INVALID_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (n_gauss > 0) {
-        AdamLr a;
-        a.lr[0] = hp->lr_mu;
-        a.lr[1] = hp->lr_scale;
-        a.lr[2] = hp->lr_rot;
-        a.lr[3] = hp->lr_a;
-        a.lr[4] = hp->lr_t;
-        if (!(hp->beta1 >= 0.0 && hp->beta1 < 1.0 && hp->beta2 >= 0.0 && hp->beta2 < 1.0 &&
-              hp->eps > 0.0))
-            return GS_ERR_INVALID_ARG;
-        a.beta1 = static_cast<float>(hp->beta1);
-        a.beta2 = static_cast<float>(hp->beta2);
-        a.omb1 = static_cast<float>(1.0 - hp->beta1);
-        a.omb2 = static_cast<float>(1.0 - hp->beta2);
-        a.log_b1 = static_cast<float>(log(hp->beta1 > 0.0 ? hp->beta1 : 1e-300));
-        a.log_b2 = static_cast<float>(log(hp->beta2 > 0.0 ? hp->beta2 : 1e-300));
-        a.eps = static_cast<float>(hp->eps);
+        if (!adam_ok(hp)) return GS_ERR_INVALID_ARG;
+        const AdamLr a = make_adam_lr(hp);
         const int64_t n = n_gauss * 12;
         const int64_t blocks64 = (n + 255) / 256;
         const unsigned blocks = static_cast<unsigned>(blocks64 < 65536 ? blocks64 : 65536);

@@ -26,14 +26,13 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <functional>
 
 #include "gs_common.cuh"
 
 namespace gs {
 
 constexpr int kFwdChunk = 128;   // Gaussians staged per forward round
-constexpr int kBwdThreads = 256;
+constexpr int kBwdThreads = 128;
 
 struct RenderGeo {
     int nx, ny, nz;
@@ -215,7 +214,7 @@ __global__ void __launch_bounds__(256) k_bwd_prep(const float* __restrict__ Iv,
 }
 
 template <int BX, bool kDet>
-__global__ void __launch_bounds__(kBwdThreads, 3) k_render_bwd(
+__global__ void __launch_bounds__(kBwdThreads, 6) k_render_bwd(
     const int32_t* __restrict__ pair_gid, const int32_t* __restrict__ pair_gmj,
     const int32_t* __restrict__ pair_brick, const int64_t* __restrict__ npairs, int64_t capacity,
     const float4* __restrict__ rec4, RenderGeo G, const float2* __restrict__ aip,
@@ -231,9 +230,9 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_render_bwd(
     if (base >= P) return;
     const int tid = threadIdx.x;
     const int nvalid = static_cast<int>(min(int64_t(kBwdThreads), P - base));
-    if (tid < 66) {
-        hist[tid] = 0;
-        cursor[tid] = 0;
+    for (int k = tid; k < 66; k += blockDim.x) {
+        hist[k] = 0;
+        cursor[k] = 0;
     }
     __syncthreads();
     // row mask of this thread's pair, staged record, histogram of row counts (most first)
@@ -411,15 +410,18 @@ gs_status bind_workspace(void* base, size_t bytes, int64_t n_gauss, int64_t capa
                          const gs_grid* grid, const gs_config* cfg, Workspace* ws);
 bool bins_match(const gs_bins* b, const gs_grid* grid, const gs_config* cfg);
 
-template <int BX, bool kDet>
-static gs_status launch_bwd(const gs_bins* bins, const RenderGeo& G, const float* I, const float* W,
-                            const float* dI, const Workspace& ws, cudaStream_t st) {
+gs_status launch_bwd_prep(const float* I, const float* W, const float* dI, const RenderGeo& G,
+                          const Workspace& ws, cudaStream_t st) {
     const int64_t nv = int64_t(G.nx) * G.ny * G.nz;
     const int64_t pb = (nv + 255) / 256;
     k_bwd_prep<<<static_cast<unsigned>(pb < 65536 ? pb : 65536), 256, 0, st>>>(I, W, dI, nv, G.eps,
                                                                               ws.aip);
-    gs_status s = last_launch_status();
-    if (s != GS_OK) return s;
+    return last_launch_status();
+}
+
+template <int BX, bool kDet>
+static gs_status launch_bwd_pairs(const gs_bins* bins, const RenderGeo& G, const Workspace& ws,
+                                  cudaStream_t st) {
     if (bins->capacity == 0) return GS_OK;
     const unsigned gb = static_cast<unsigned>((bins->capacity + kBwdThreads - 1) / kBwdThreads);
     const float4* rec4 = reinterpret_cast<const float4*>(bins->rec);
@@ -429,41 +431,40 @@ static gs_status launch_bwd(const gs_bins* bins, const RenderGeo& G, const float
     return last_launch_status();
 }
 
-template <bool kDet>
-static gs_status launch_bwd_bx(const gs_bins* bins, const RenderGeo& G, const float* I,
-                               const float* W, const float* dI, const Workspace& ws,
-                               cudaStream_t st) {
+// Adjoint render kernel over ws.aip (already prepared): per-pair partials (deterministic) or
+// atomically accumulated ws.gacc (fast; zeroed here).
+gs_status launch_adjoint_pairs(const gs_bins* bins, const gs_grid* grid, const gs_config* cfg,
+                               const Workspace& ws, cudaStream_t st) {
+    RenderGeo G = make_geo(grid, cfg);
+    const int64_t N = bins->n_gauss;
+    if (!cfg->deterministic && N > 0 &&
+        cudaMemsetAsync(ws.gacc, 0, sizeof(float) * GRAD_FLOATS * N, st) != cudaSuccess)
+        return GS_ERR_CUDA;
+    const bool det = cfg->deterministic != 0;
     switch (G.bsx) {
-        case 4: return launch_bwd<4, kDet>(bins, G, I, W, dI, ws, st);
-        case 8: return launch_bwd<8, kDet>(bins, G, I, W, dI, ws, st);
-        case 16: return launch_bwd<16, kDet>(bins, G, I, W, dI, ws, st);
+        case 4: return det ? launch_bwd_pairs<4, true>(bins, G, ws, st) : launch_bwd_pairs<4, false>(bins, G, ws, st);
+        case 8: return det ? launch_bwd_pairs<8, true>(bins, G, ws, st) : launch_bwd_pairs<8, false>(bins, G, ws, st);
+        case 16: return det ? launch_bwd_pairs<16, true>(bins, G, ws, st) : launch_bwd_pairs<16, false>(bins, G, ws, st);
     }
     return GS_ERR_INVALID_ARG;
 }
 
 // Render-space adjoint into ws.gacc [N, 12] (no parameter chain).
-gs_status render_bwd_geo(const gs_bins* bins, const gs_grid* grid, const gs_config* cfg,
-                         const float* I, const float* W, const float* dI, const Workspace& ws,
-                         cudaStream_t st, const std::function<bool()>& after_kernel) {
+static gs_status render_bwd_geo(const gs_bins* bins, const gs_grid* grid, const gs_config* cfg,
+                                const float* I, const float* W, const float* dI,
+                                const Workspace& ws, cudaStream_t st) {
     RenderGeo G = make_geo(grid, cfg);
-    const int64_t N = bins->n_gauss;
-    if (cfg->deterministic) {
-        gs_status s = launch_bwd_bx<true>(bins, G, I, W, dI, ws, st);
-        if (s != GS_OK) return s;
-        if (after_kernel && !after_kernel()) return GS_ERR_CUDA;
-        if (N > 0) {
-            k_pair_reduce<<<static_cast<unsigned>((N + 255) / 256), 256, 0, st>>>(
-                ws.part, bins->gm_off, bins->d_npairs, bins->capacity, N, ws.gacc);
-            s = last_launch_status();
-        }
-        return s;
-    }
-    if (N > 0 && cudaMemsetAsync(ws.gacc, 0, sizeof(float) * GRAD_FLOATS * N, st) != cudaSuccess)
-        return GS_ERR_CUDA;
-    gs_status s = launch_bwd_bx<false>(bins, G, I, W, dI, ws, st);
+    gs_status s = launch_bwd_prep(I, W, dI, G, ws, st);
     if (s != GS_OK) return s;
-    if (after_kernel && !after_kernel()) return GS_ERR_CUDA;
-    return GS_OK;
+    s = launch_adjoint_pairs(bins, grid, cfg, ws, st);
+    if (s != GS_OK) return s;
+    const int64_t N = bins->n_gauss;
+    if (cfg->deterministic && N > 0) {
+        k_pair_reduce<<<static_cast<unsigned>((N + 255) / 256), 256, 0, st>>>(
+            ws.part, bins->gm_off, bins->d_npairs, bins->capacity, N, ws.gacc);
+        s = last_launch_status();
+    }
+    return s;
 }
 
 }  // namespace gs
@@ -491,7 +492,7 @@ extern "C" gs_status gs_render_bwd(const float* params, const gs_bins* bins, con
     s = bind_workspace(ws, ws_bytes, bins->n_gauss, bins->capacity, grid, cfg, &w);
     if (s != GS_OK) return s;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    s = render_bwd_geo(bins, grid, cfg, I, W, dI, w, st, nullptr);
+    s = render_bwd_geo(bins, grid, cfg, I, W, dI, w, st);
     if (s != GS_OK) return s;
     if (bins->n_gauss == 0) return GS_OK;
     return launch_param_bwd(params, w.gacc, bins->n_gauss, grid, cfg, dparams, st);

@@ -5,7 +5,6 @@
 #include <stdint.h>
 
 #include <atomic>
-#include <functional>
 
 #include "gs_common.cuh"
 
@@ -117,9 +116,32 @@ gs_status bin_bricks_impl(const float* params, const gs_grid* grid, const gs_con
                           gs_bins* bins, const Workspace& ws, cudaStream_t st);
 gs_status render_fwd_impl(const gs_bins* bins, const gs_grid* grid, const gs_config* cfg, float* I,
                           float* W, unsigned long long* stats, cudaStream_t st);
-gs_status render_bwd_geo(const gs_bins* bins, const gs_grid* grid, const gs_config* cfg,
-                         const float* I, const float* W, const float* dI, const Workspace& ws,
-                         cudaStream_t st, const std::function<bool()>& after_kernel);
+gs_status launch_adjoint_pairs(const gs_bins* bins, const gs_grid* grid, const gs_config* cfg,
+                               const Workspace& ws, cudaStream_t st);
+gs_status launch_chain_adam(float* params, float* grad, float* m, float* v, const float* part,
+                            const float* gacc, const gs_bins* bins, int64_t n,
+                            const gs_grid* grid, const gs_config* cfg, const gs_adam* hp,
+                            int32_t* d_step, cudaStream_t st);
+
+// Slice-profile adjoint fused with the adjoint render's per-voxel factors: for each HR voxel
+// dL/dI = dL/dLR[z / s] / s (0 below the last full slab), alpha = dL/dI / max(W, eps) and
+// I' = I where W > eps, else 0.
+__global__ void __launch_bounds__(256) k_profile_adj_prep(const float* __restrict__ dlr,
+                                                          const float* __restrict__ Iv,
+                                                          const float* __restrict__ Wv, int nz,
+                                                          int ny, int nx, int s, float inv_s,
+                                                          float eps, float2* __restrict__ aip) {
+    const int64_t plane = int64_t(ny) * nx;
+    const int64_t n = plane * nz;
+    const int zmax = s * (nz / s);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t z = i / plane, r = i - z * plane;
+        const float gI = (z < zmax) ? dlr[(z / s) * plane + r] * inv_s : 0.0f;
+        const float w = Wv[i];
+        aip[i] = make_float2(gI / (w > eps ? w : eps), (w > eps) ? Iv[i] : 0.0f);
+    }
+}
 
 }  // namespace gs
 
@@ -157,7 +179,7 @@ extern "C" gs_status gs_fit_step(gs_fit_state* st, gs_stream stream) {
     if (s != GS_OK) return s;
     if (st->n_gauss <= 0 || st->s <= 0 || st->grid.nz / st->s <= 0) return GS_ERR_INVALID_ARG;
     if (!st->params || !st->grad || !st->m || !st->v || !st->d_step || !st->I || !st->W ||
-        !st->dI || !st->lr_pred || !st->lr_target || !st->d_loss)
+        !st->lr_pred || !st->lr_target || !st->d_loss)
         return GS_ERR_INVALID_ARG;
     if (!bins_match(&st->bins, &st->grid, &st->cfg) || st->bins.n_gauss != st->n_gauss)
         return GS_ERR_INVALID_ARG;
@@ -185,16 +207,22 @@ extern "C" gs_status gs_fit_step(gs_fit_state* st, gs_stream stream) {
     // L1 loss; its gradient overwrites lr_pred in place.
     s = launch_l1(st->lr_pred, st->lr_target, n_lr, st->d_loss, st->lr_pred, w.l1_part, cs);
     if (s != GS_OK) return s;
-    s = downsample_bwd_impl(st->lr_pred, g.nz, g.ny, g.nx, st->s, st->dI, cs);
-    if (s != GS_OK) return s;
+    {
+        const int64_t nv = int64_t(g.nz) * g.ny * g.nx;
+        k_profile_adj_prep<<<grid_for(nv), 256, 0, cs>>>(st->lr_pred, st->I, st->W, g.nz, g.ny, g.nx,
+                                                         st->s, 1.0f / float(st->s), st->cfg.eps,
+                                                         w.aip);
+        s = last_launch_status();
+        if (s != GS_OK) return s;
+    }
     if (!mark(3)) return GS_ERR_CUDA;
-    s = render_bwd_geo(&st->bins, &g, &st->cfg, st->I, st->W, st->dI, w, cs, [&]() { return mark(4); });
+    s = launch_adjoint_pairs(&st->bins, &g, &st->cfg, w, cs);
     if (s != GS_OK) return s;
-    s = launch_param_bwd(st->params, w.gacc, st->n_gauss, &g, &st->cfg, st->grad, cs);
+    if (!mark(4)) return GS_ERR_CUDA;
+    s = launch_chain_adam(st->params, st->grad, st->m, st->v, w.part, w.gacc, &st->bins, st->n_gauss,
+                          &g, &st->cfg, &st->adam, st->d_step, cs);
     if (s != GS_OK) return s;
     if (!mark(5)) return GS_ERR_CUDA;
-    s = gs_adam_step(st->params, st->grad, st->m, st->v, st->n_gauss, &st->adam, st->d_step, stream);
-    if (s != GS_OK) return s;
     if (!mark(6)) return GS_ERR_CUDA;
     return GS_OK;
 }

@@ -56,8 +56,7 @@ class gs_fit_state(ctypes.Structure):
                 ("n_gauss", ctypes.c_int64), ("s", ctypes.c_int32),
                 ("params", ctypes.c_void_p), ("grad", ctypes.c_void_p), ("m", ctypes.c_void_p),
                 ("v", ctypes.c_void_p), ("d_step", ctypes.c_void_p), ("bins", gs_bins),
-                ("I", ctypes.c_void_p), ("W", ctypes.c_void_p), ("dI", ctypes.c_void_p),
-                ("lr_pred", ctypes.c_void_p), ("lr_target", ctypes.c_void_p),
+                ("I", ctypes.c_void_p), ("W", ctypes.c_void_p), ("lr_pred", ctypes.c_void_p), ("lr_target", ctypes.c_void_p),
                 ("d_loss", ctypes.c_void_p), ("ws", ctypes.c_void_p),
                 ("ws_bytes", ctypes.c_size_t), ("phase_events", ctypes.c_void_p),
                 ("n_phase_events", ctypes.c_int32)]
@@ -416,7 +415,6 @@ class FitState:
         self.d_step = torch.zeros((), dtype=torch.int32, device=dev)
         self.I = torch.zeros(grid.shape, dtype=torch.float32, device=dev)
         self.W = torch.zeros_like(self.I)
-        self.dI = torch.zeros_like(self.I)
         self.lr_target = lr_target.contiguous()
         self.lr_pred = torch.zeros_like(self.lr_target)
         self.d_loss = torch.zeros((), dtype=torch.float32, device=dev)
@@ -435,7 +433,7 @@ class FitState:
         st.params, st.grad = self.params.data_ptr(), self.grad.data_ptr()
         st.m, st.v, st.d_step = self.m.data_ptr(), self.v.data_ptr(), self.d_step.data_ptr()
         st.bins = self.bins.c
-        st.I, st.W, st.dI = self.I.data_ptr(), self.W.data_ptr(), self.dI.data_ptr()
+        st.I, st.W = self.I.data_ptr(), self.W.data_ptr()
         st.lr_pred, st.lr_target = self.lr_pred.data_ptr(), self.lr_target.data_ptr()
         st.d_loss, st.ws, st.ws_bytes = self.d_loss.data_ptr(), self.ws.buf.data_ptr(), self.ws.nbytes
         self.c = st
