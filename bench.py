@@ -58,6 +58,10 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--fast", action="store_true", help="non-deterministic (atomic) reduction")
+    ap.add_argument("--workload", choices=["fit", "stress"], default="fit",
+                    help="fit: the fitting step (default); stress: forward + adjoint render of "
+                         "4M clustered anisotropic Gaussians on 512 x 512 x 256, deterministic "
+                         "reduction on and off")
     return ap.parse_args()
 
 
@@ -405,11 +409,70 @@ def run_ours(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_stress(args, world, rank, local):
+    """Forward + adjoint render of the stress cloud (not the headline line): 512 x 512 x 256
+    grid, 4M Gaussians in 20 Gaussian-mixture blobs (blob std 24 voxels), one axis scale
+    log-uniform in [4, 8] voxels and the others in [0.5, 1.5], random rotations; a random
+    upstream gradient; deterministic reduction on and off."""
+    import torch
+    from paper_2603_09621_gb300 import build as gbuild
+    gbuild.build()
+    from paper_2603_09621_gb300 import gs, inputs, workloads
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    shape = (256, 512, 512)
+    g = gs.Grid(512, 512, 256)
+    d = inputs.gmm_cloud(rank, 4_000_000, shape)
+    params = workloads.cloud_params(d, device=dev)
+    dI = torch.randn(shape, device=dev, generator=torch.Generator(device=dev).manual_seed(rank))
+    out = {}
+    for det in (1, 0):
+        cfg = gs.Config(deterministic=det)
+        I, W, bins, ws = gs.render(params, g, cfg, capacity=None)
+        stats = torch.zeros(2, dtype=torch.int64, device=dev)
+        gs.gs_render_fwd(bins, g, cfg, I, W, stats=stats)
+        dparams = torch.empty_like(params)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        for _ in range(args.warmup):
+            gs.gs_bin_bricks(params, g, cfg, bins, ws)
+            gs.gs_render_fwd(bins, g, cfg, I, W)
+            gs.gs_render_bwd(params, bins, g, cfg, I, W, dI, ws, dparams)
+        torch.cuda.synchronize()
+        t_bin = t_fwd = t_bwd = 0.0
+        for _ in range(args.steps):
+            ev[0].record()
+            gs.gs_bin_bricks(params, g, cfg, bins, ws)
+            ev[1].record()
+            gs.gs_render_fwd(bins, g, cfg, I, W)
+            ev[2].record()
+            gs.gs_render_bwd(params, bins, g, cfg, I, W, dI, ws, dparams)
+            ev[3].record()
+            ev[3].synchronize()
+            t_bin += ev[0].elapsed_time(ev[1])
+            t_fwd += ev[1].elapsed_time(ev[2])
+            t_bwd += ev[2].elapsed_time(ev[3])
+        n_eff, n_eval = [int(x) for x in stats.cpu()]
+        k = args.steps
+        out["det" if det else "fast"] = {
+            "ms_bin": t_bin / k, "ms_fwd": t_fwd / k, "ms_bwd": t_bwd / k,
+            "pair_evals_per_s": n_eff * k / ((t_bin + t_fwd + t_bwd) / 1000.0),
+            "effective_pairs": n_eff, "evaluated": n_eval, "brick_pairs": bins.npairs(),
+            "dparams_finite": bool(torch.isfinite(dparams).all().item())}
+        del I, W, bins, ws, dparams
+        torch.cuda.empty_cache()
+    if rank == 0:
+        print(json.dumps({"workload": "stress 512x512x256, 4M clustered anisotropic Gaussians, "
+                                      "bin + forward + adjoint render", "steps": args.steps,
+                          "warmup": args.warmup, "results": out}), flush=True)
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "stress":
+        run_stress(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:
