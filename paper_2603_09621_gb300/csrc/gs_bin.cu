@@ -6,14 +6,13 @@
 //                  bit-exact against the oracle's binning specification), render record.
 //   scan           exclusive scan of per-Gaussian pair counts -> gm_off, total -> d_npairs.
 //   k_capacity     flags GS_STATUS_CAPACITY when the total exceeds the bins' capacity.
-//   k_emit         Gaussian-major pair emission (brick key, owner) + per-brick counts.
-//   scan           exclusive scan of per-brick counts -> brick_off.
+//   k_emit         Gaussian-major pair emission (brick key, owner).
 //   radix passes   stable LSD radix sort of the brick keys, 8 bits per pass: per-tile digit
 //                  histograms, a digit-major scan, and a stable scatter whose in-tile ranks
 //                  come from warp match masks. Stability keeps ascending Gaussian ids inside
 //                  each brick, so the lists are deterministic.
 //   k_finalize     pair_gmj (Gaussian-major position), pair_gid (owner) and pair_brick per
-//                  brick-major pair.
+//                  brick-major pair; brick_off from the boundaries of the sorted keys.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -346,8 +345,7 @@ __global__ void __launch_bounds__(256) k_emit(const int32_t* __restrict__ brange
                                               const int32_t* __restrict__ gm_off, int64_t N, int nbx,
                                               int nby, const int64_t* __restrict__ npairs,
                                               int64_t capacity, int32_t* __restrict__ keys,
-                                              int32_t* __restrict__ gm_gid,
-                                              int32_t* __restrict__ brick_cnt) {
+                                              int32_t* __restrict__ gm_gid) {
     const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= N) return;
     if (valid_pairs(npairs, capacity) == 0) return;
@@ -360,7 +358,6 @@ __global__ void __launch_bounds__(256) k_emit(const int32_t* __restrict__ brange
                 int b = (bz * nby + by) * nbx + bx;
                 keys[j] = b;
                 gm_gid[j] = static_cast<int32_t>(g);
-                atomicAdd(&brick_cnt[b], 1);
                 ++j;
             }
 }
@@ -385,9 +382,13 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const int32_t* __re
         hist[int64_t(d) * n_tiles + blockIdx.x] = cnt[d];
 }
 
-// Stable scatter of one tile. Items are visited in kSortItems rounds of kSortThreads
-// consecutive keys; the rank of an item among equal digits is (items of that digit in
-// earlier rounds) + (in earlier warps of this round) + (in lower lanes of its warp).
+// Stable scatter of one tile of kSortTile keys. Warp w owns the contiguous sub-tile
+// [w * 512, (w + 1) * 512) and visits it in 16 rounds of 32 consecutive keys (kept in
+// registers). Pass 1 counts each warp's digits; one block-wide prefix over the warps (plus
+// the tile's global offset) gives every warp its starting slot per digit; pass 2 places each
+// key at that slot + its rank among equal digits in lower lanes (warp match masks), then
+// advances the warp's counter. Order is preserved: warps in tile order, rounds in order,
+// lanes in order.
 template <bool kFirst>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in,
@@ -395,72 +396,80 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const int32_t* __restrict__ hist_off, const int64_t* __restrict__ npairs, int64_t capacity,
     int shift, int n_tiles) {
     constexpr int kWarps = kSortThreads / 32;
-    __shared__ int base[kRadix];
+    constexpr int kPerWarp = kSortTile / kWarps;
+    constexpr int kRounds = kPerWarp / 32;
     __shared__ int wcnt[kWarps][kRadix];
-    __shared__ int tot[kRadix];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int d = tid; d < kRadix; d += kSortThreads) {
-        base[d] = hist_off[int64_t(d) * n_tiles + blockIdx.x];
+    for (int d = tid; d < kRadix; d += kSortThreads)
         for (int w = 0; w < kWarps; ++w) wcnt[w][d] = 0;
-    }
     __syncthreads();
     const int64_t P = valid_pairs(npairs, capacity);
-    const int64_t tile0 = int64_t(blockIdx.x) * kSortTile;
+    const int64_t sub0 = int64_t(blockIdx.x) * kSortTile + int64_t(warp) * kPerWarp;
     const unsigned lt_mask = (1u << lane) - 1u;
-    for (int r = 0; r < kSortItems; ++r) {
-        const int64_t idx = tile0 + int64_t(r) * kSortThreads + tid;
+    int kr[kRounds], vr[kRounds];
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const int64_t idx = sub0 + r * 32 + lane;
         const bool valid = idx < P;
-        int key = 0, val = 0, d = 0;
-        if (valid) {
-            key = keys_in[idx];
-            val = kFirst ? static_cast<int>(idx) : vals_in[idx];
-            d = (key >> shift) & (kRadix - 1);
-        }
-        // Invalid lanes get a unique tag outside the digit range so they match nobody.
+        kr[r] = valid ? keys_in[idx] : 0;
+        vr[r] = valid ? (kFirst ? static_cast<int>(idx) : vals_in[idx]) : 0;
+        const int d = (kr[r] >> shift) & (kRadix - 1);
         const unsigned tag = valid ? static_cast<unsigned>(d) : static_cast<unsigned>(kRadix + lane);
         const unsigned peers = __match_any_sync(0xffffffffu, tag);
-        const int rank = __popc(peers & lt_mask);
-        const int leader = __ffs(peers) - 1;
-        if (valid && lane == leader) wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        for (int dd = tid; dd < kRadix; dd += kSortThreads) {
-            int run = 0;
-            for (int w = 0; w < kWarps; ++w) {
-                int c = wcnt[w][dd];
-                wcnt[w][dd] = run;
-                run += c;
-            }
-            tot[dd] = run;
+        if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int d = tid; d < kRadix; d += kSortThreads) {
+        int run = hist_off[int64_t(d) * n_tiles + blockIdx.x];
+        for (int w = 0; w < kWarps; ++w) {
+            const int c = wcnt[w][d];
+            wcnt[w][d] = run;
+            run += c;
         }
-        __syncthreads();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const int64_t idx = sub0 + r * 32 + lane;
+        const bool valid = idx < P;
+        const int d = (kr[r] >> shift) & (kRadix - 1);
+        const unsigned tag = valid ? static_cast<unsigned>(d) : static_cast<unsigned>(kRadix + lane);
+        const unsigned peers = __match_any_sync(0xffffffffu, tag);
         if (valid) {
-            const int pos = base[d] + wcnt[warp][d] + rank;
-            keys_out[pos] = key;
-            vals_out[pos] = val;
+            const int pos = wcnt[warp][d] + __popc(peers & lt_mask);
+            keys_out[pos] = kr[r];
+            vals_out[pos] = vr[r];
         }
-        __syncthreads();
-        for (int dd = tid; dd < kRadix; dd += kSortThreads) {
-            base[dd] += tot[dd];
-            for (int w = 0; w < kWarps; ++w) wcnt[w][dd] = 0;
-        }
-        __syncthreads();
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] += __popc(peers);
+        __syncwarp();
     }
 }
 
+// Per brick-major pair: Gaussian-major position, owner and brick; and the brick offsets,
+// read off the sorted keys (brick_off[b] = first pair of brick b, or the next non-empty
+// brick's first pair; brick_off[nb] = P).
 __global__ void __launch_bounds__(256) k_finalize(const int32_t* __restrict__ keys,
                                                   const int32_t* __restrict__ vals,
                                                   const int32_t* __restrict__ gm_gid,
                                                   const int64_t* __restrict__ npairs, int64_t capacity,
-                                                  int32_t* __restrict__ pair_gmj,
+                                                  int nb, int32_t* __restrict__ pair_gmj,
                                                   int32_t* __restrict__ pair_gid,
-                                                  int32_t* __restrict__ pair_brick) {
+                                                  int32_t* __restrict__ pair_brick,
+                                                  int32_t* __restrict__ brick_off) {
     const int64_t P = valid_pairs(npairs, capacity);
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i <= P;
          i += int64_t(gridDim.x) * blockDim.x) {
-        int j = vals[i];
-        pair_gmj[i] = j;
-        pair_gid[i] = gm_gid[j];
-        pair_brick[i] = keys[i];
+        const int cur = (i < P) ? keys[i] : nb;
+        const int prev = (i > 0) ? keys[i - 1] : -1;
+        for (int bb = prev + 1; bb <= cur; ++bb) brick_off[bb] = static_cast<int32_t>(i);
+        if (i < P) {
+            const int j = vals[i];
+            pair_gmj[i] = j;
+            pair_gid[i] = gm_gid[j];
+            pair_brick[i] = keys[i];
+        }
     }
 }
 
@@ -608,9 +617,6 @@ gs_status bin_bricks_impl(const float* params, const gs_grid* grid, const gs_con
     G.nb[0] = b.nbx; G.nb[1] = b.nby; G.nb[2] = b.nbz;
 
     if (cudaMemsetAsync(bins->d_status, 0, sizeof(int32_t), st) != cudaSuccess) return GS_ERR_CUDA;
-    if (cudaMemsetAsync(ws.brick_cnt, 0, sizeof(int32_t) * (int64_t(bins->n_bricks) + 1), st) !=
-        cudaSuccess)
-        return GS_ERR_CUDA;
     long long* total = ws.scan_tmp + ws.scan_tmp_len - 1;
     if (N > 0) {
         const unsigned gb = static_cast<unsigned>((N + 255) / 256);
@@ -633,15 +639,16 @@ gs_status bin_bricks_impl(const float* params, const gs_grid* grid, const gs_con
     if (s != GS_OK) return s;
     if (N > 0) {
         k_emit<<<static_cast<unsigned>((N + 255) / 256), 256, 0, st>>>(
-            bins->brange, bins->gm_off, N, b.nbx, b.nby, bins->d_npairs, cap, ws.keys0, ws.gm_gid,
-            ws.brick_cnt);
+            bins->brange, bins->gm_off, N, b.nbx, b.nby, bins->d_npairs, cap, ws.keys0, ws.gm_gid);
         s = last_launch_status();
         if (s != GS_OK) return s;
     }
-    s = exclusive_scan_i32(ws.brick_cnt, bins->brick_off, int64_t(bins->n_bricks) + 1, nullptr,
-                           ws.scan_tmp, ws.scan_tmp_len - 1, st);
-    if (s != GS_OK) return s;
-    if (cap == 0) return GS_OK;
+    if (cap == 0) {
+        if (cudaMemsetAsync(bins->brick_off, 0, sizeof(int32_t) * (int64_t(bins->n_bricks) + 1), st) !=
+            cudaSuccess)
+            return GS_ERR_CUDA;
+        return GS_OK;
+    }
 
     // Stable LSD radix sort of brick keys; values are Gaussian-major positions.
     const int passes = radix_passes(bins->n_bricks);
@@ -669,8 +676,9 @@ gs_status bin_bricks_impl(const float* params, const gs_grid* grid, const gs_con
         int32_t* t = kin; kin = kout; kout = t;
         t = vin; vin = vout; vout = t;
     }
-    k_finalize<<<1184, 256, 0, st>>>(kin, vin, ws.gm_gid, bins->d_npairs, cap, bins->pair_gmj,
-                                     bins->pair_gid, bins->pair_brick);
+    k_finalize<<<1184, 256, 0, st>>>(kin, vin, ws.gm_gid, bins->d_npairs, cap, bins->n_bricks,
+                                     bins->pair_gmj, bins->pair_gid, bins->pair_brick,
+                                     bins->brick_off);
     return last_launch_status();
 }
 

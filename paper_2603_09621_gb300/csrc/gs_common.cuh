@@ -82,7 +82,6 @@ struct Workspace {
     int32_t* vals1;
     int32_t* gm_gid;
     int32_t* gm_cnt;
-    int32_t* brick_cnt;
     int32_t* hist;
     long long* scan_tmp;     // block sums of the multi-level scan
     float* part;             // [capacity, 12] per-pair partial gradients (deterministic mode)
@@ -129,7 +128,6 @@ inline bool carve_workspace(void* base, int64_t n_gauss, int64_t capacity, int32
     ws->vals1 = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * cap));
     ws->gm_gid = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * cap));
     ws->gm_cnt = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * (n + 1)));
-    ws->brick_cnt = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * (int64_t(n_bricks) + 1)));
     ws->hist = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * (hist_len + 1)));
     ws->scan_tmp = reinterpret_cast<long long*>(take(sizeof(long long) * ws->scan_tmp_len));
     ws->part = reinterpret_cast<float*>(
