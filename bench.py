@@ -14,8 +14,9 @@ forward and once through the adjoint render of a step. Also reported: ms per ste
 seconds per scan (2,000 iterations at this size), voxels per second.
 
 Timing: W warm-up steps, then K steps timed with CUDA events recorded by the library on the
-launching stream at the step's phase boundaries; L2 is flushed (256 MB write) between timed
-steps; barrier + synchronize on both sides; max over ranks. `--gpus N` under torchrun runs
+launching stream at the step's phase boundaries; the step is captured once in a CUDA graph
+and replayed (it has no host synchronisation; --no-graph times eager calls); L2 is flushed
+(256 MB write) between timed steps; barrier + synchronize on both sides; max over ranks. `--gpus N` under torchrun runs
 N independent replicas (one scan per GPU; the path does not shard).
 
 `--impl reference` times the FP64 CPU oracle (the only reference: the paper ships no code)
@@ -58,6 +59,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--fast", action="store_true", help="non-deterministic (atomic) reduction")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="time eager gs_fit_step calls instead of CUDA-graph replays")
     ap.add_argument("--workload", choices=["fit", "stress"], default="fit",
                     help="fit: the fitting step (default); stress: forward + adjoint render of "
                          "4M clustered anisotropic Gaussians on 512 x 512 x 256, deterministic "
@@ -274,6 +277,7 @@ def config_dict(args):
                         f"z box x{S_FACTOR}, L1, Adam",
             "grid": [nx, ny, nz], "n_gauss": N_GAUSS, "slice_factor": S_FACTOR,
             "brick": [8, 8, 8], "deterministic": 0 if args.fast else 1,
+            "launch": "eager" if args.no_graph else "cuda graph replay of gs_fit_step",
             "l2": "flushed between timed steps (256 MB write)"}
 
 
@@ -318,6 +322,22 @@ def run_ours(args, world, rank, local):
         pass
     clocks = ClockSampler(gpu_id)
     st.set_phase_events(events)
+    # The step has no host synchronisation: capture it (with its phase events) in a CUDA graph
+    # and replay it, as a fitting loop would.
+    graph = None
+    if not args.no_graph:
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            st.step()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        launches_per_step = gs.gs_launch_count()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            st.step()
+        launches_per_step = gs.gs_launch_count() - launches_per_step
+        torch.cuda.synchronize()
     phase_ms = [0.0] * (gs.GS_FIT_PHASES - 1)
     step_ms = []
     barrier(world)
@@ -327,7 +347,10 @@ def run_ours(args, world, rank, local):
     wall0 = time.perf_counter()
     for _ in range(args.steps):
         flush.fill_(1.0)                      # evict L2 between timed steps
-        st.step()
+        if graph is not None:
+            graph.replay()
+        else:
+            st.step()
         events[-1].synchronize()
         for i in range(gs.GS_FIT_PHASES - 1):
             phase_ms[i] += events[i].elapsed_time(events[i + 1])
@@ -335,6 +358,8 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     launches = gs.gs_launch_count() - launches0
+    if graph is not None:
+        launches = launches_per_step * args.steps  # graph replays launch the captured kernels
     barrier(world)
     clk = clocks.stop()
     st.set_phase_events(None)
