@@ -189,9 +189,16 @@ extern "C" gs_status gs_fit_step(gs_fit_state* st, gs_stream stream) {
     if (st->n_phase_events != 0 && (st->n_phase_events != GS_FIT_PHASES || !st->phase_events))
         return GS_ERR_INVALID_ARG;
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    // Phase events: during stream capture they must be external event-record nodes, or they
+    // would only serve as capture-internal dependencies.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (st->n_phase_events && cudaStreamIsCapturing(cs, &cap) != cudaSuccess) return GS_ERR_CUDA;
     auto mark = [&](int phase) -> bool {
         if (!st->n_phase_events) return true;
-        return cudaEventRecord(static_cast<cudaEvent_t>(st->phase_events[phase]), cs) == cudaSuccess;
+        cudaEvent_t ev = static_cast<cudaEvent_t>(st->phase_events[phase]);
+        if (cap == cudaStreamCaptureStatusActive)
+            return cudaEventRecordWithFlags(ev, cs, cudaEventRecordExternal) == cudaSuccess;
+        return cudaEventRecord(ev, cs) == cudaSuccess;
     };
     const gs_grid& g = st->grid;
     if (!mark(0)) return GS_ERR_CUDA;
