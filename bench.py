@@ -89,12 +89,18 @@ def barrier(world):
         dist.barrier()
 
 
+def _collective_device():
+    """The process group's tensors live on the GPU under NCCL and on the host under gloo."""
+    import torch.distributed as dist
+    return "cuda" if dist.get_backend() == "nccl" else "cpu"
+
+
 def allreduce_max(x: float, world: int) -> float:
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_collective_device())
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -104,9 +110,17 @@ def allreduce_sum(x: float, world: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_collective_device())
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def replica_throughput(units: float, seconds: float, world: int):
+    """Whole-job throughput of independent replicas: the units every rank processed over the
+    slowest rank's timed seconds. Returns (value, max seconds, total units)."""
+    t_max = allreduce_max(seconds, world)
+    total = allreduce_sum(units, world)
+    return total / t_max, t_max, total
 
 
 def measured_peaks():
@@ -368,9 +382,7 @@ def run_ours(args, world, rank, local):
         raise RuntimeError(f"fit step status {gs.STATUS.get(rc, rc)} bits {bits}")
 
     t_dev = sum(step_ms) / 1000.0
-    t_max = allreduce_max(t_dev, world)
-    units = allreduce_sum(float(n_eff) * args.steps, world)
-    value = units / t_max
+    value, t_max, _ = replica_throughput(float(n_eff) * args.steps, t_dev, world)
     ms_step = 1000.0 * t_max / args.steps
 
     # roofline of the dominant render kernel (effective pairs per launch / mean duration)
@@ -408,8 +420,9 @@ def run_ours(args, world, rank, local):
             e2e_ms.append(e0.elapsed_time(e1))
     e2e = None
     if e2e_ms:
-        t_e2e = allreduce_max(sum(e2e_ms) / 1000.0, world)
-        e2e = {"value": allreduce_sum(float(n_eff) * len(e2e_ms), world) / t_e2e,
+        e2e_value, t_e2e, _ = replica_throughput(float(n_eff) * len(e2e_ms),
+                                                 sum(e2e_ms) / 1000.0, world)
+        e2e = {"value": e2e_value,
                "unit": "pair-evals/s",
                "h2d_bytes_per_step": h_params.numel() * 4 + h_lr.numel() * 4,
                "d2h_bytes_per_step": 4, "ms_per_step": 1000.0 * t_e2e / len(e2e_ms)}
