@@ -61,10 +61,16 @@ def parse_args():
     ap.add_argument("--fast", action="store_true", help="non-deterministic (atomic) reduction")
     ap.add_argument("--no-graph", action="store_true",
                     help="time eager gs_fit_step calls instead of CUDA-graph replays")
-    ap.add_argument("--workload", choices=["fit", "stress"], default="fit",
+    ap.add_argument("--workload", choices=["fit", "stress", "serve"], default="fit",
                     help="fit: the fitting step (default); stress: forward + adjoint render of "
                          "4M clustered anisotropic Gaussians on 512 x 512 x 256, deterministic "
-                         "reduction on and off")
+                         "reduction on and off; serve: a stream of fitting and re-rendering "
+                         "requests through the serving runtime")
+    ap.add_argument("--serve-active", type=int, default=4,
+                    help="serve: requests resident at once in the concurrent runs")
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0,
+                    help="serve: device arena of the server")
+    ap.add_argument("--serve-requests", type=int, default=32, help="serve: stream length")
     return ap.parse_args()
 
 
@@ -504,6 +510,72 @@ def run_stress(args, world, rank, local):
                           "warmup": args.warmup, "results": out}), flush=True)
 
 
+def run_serve(args, world, rank, local):
+    """Serving stream (not the headline line): Poisson arrivals at 2 per second of requests
+    that fit a new scan (75 %: 128^3 to 256 x 256 x 192 voxels, slice factor 2-4, 100k-1M
+    Gaussians, 500 steps) or re-render an earlier fit on a new isotropic grid (25 %), through
+    the serving runtime with `--serve-active` requests resident, against the same stream one
+    request at a time; and the same requests all arriving at once (closed batch)."""
+    import numpy as np
+    import torch
+    from paper_2603_09621_gb300 import build as gbuild
+    gbuild.build()
+    from paper_2603_09621_gb300 import inputs, serve, workloads
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    draws = inputs.serving_draws(seed=rank, n=args.serve_requests)
+    t0 = time.perf_counter()
+    reqs = workloads.serving_workload(draws, device=dev)
+    torch.cuda.synchronize()
+    prep_s = time.perf_counter() - t0
+    torch.cuda.empty_cache()
+    budget = int(args.serve_budget_gb * (1 << 30))
+    chunk = 25
+
+    def play(max_active, arrivals, subset=None):
+        use = reqs if subset is None else subset
+        with serve.Server(budget, max_active=max_active, chunk_steps=chunk) as sv:
+            t_base = sv.stats()["now_s"] + 0.05
+            ids = []
+            for r in use:
+                arr = t_base + (r["arrival_s"] if arrivals else 0.0)
+                if r["kind"] == "fit":
+                    ids.append(sv.submit_fit(r["params0"], r["lr"], r["grid"], r["s"],
+                                             r["iters"], arrival_s=arr))
+                else:
+                    ids.append(sv.submit_render(r["grid"], source=ids[r["source"]],
+                                                arrival_s=arr))
+            sv.run(timeout_s=3600)
+            res = [sv.result(i) for i in ids]
+            st = sv.stats()
+        lat = np.array([x["done_s"] - x["arrival_s"] for x in res])
+        span = max(x["done_s"] for x in res) - t_base
+        kinds = [r["kind"] for r in use]
+        return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                "mean_s": float(lat.mean()),
+                "p50_fit_s": float(np.percentile(lat[[k == "fit" for k in kinds]], 50)),
+                "makespan_s": span, "scans_per_h": len(res) * 3600.0 / span,
+                "done": sum(x["state"] == "done" for x in res),
+                "failed": sum(x["state"] != "done" for x in res),
+                "peak_arena_gb": st["peak_bytes"] / (1 << 30),
+                "chunks": st["chunks_launched"], "graphs": st["graphs_captured"],
+                "grows": st["grows"]}
+
+    # warm-up: the smallest fit once (module loading, first graph instantiation)
+    small = min((r for r in reqs if r["kind"] == "fit"), key=lambda r: r["n_gauss"])
+    play(1, False, [dict(small, iters=2 * chunk)])
+    k = args.serve_active
+    out = {"stream": {f"active_{k}": play(k, True), "active_1": play(1, True)},
+           "batch": {f"active_{k}": play(k, False), "active_1": play(1, False)}}
+    n_fit = sum(r["kind"] == "fit" for r in reqs)
+    if rank == 0:
+        print(json.dumps({
+            "workload": f"serving stream: {len(reqs)} requests ({n_fit} fits of 500 steps, "
+                        f"{len(reqs) - n_fit} re-renders), Poisson 2/s, "
+                        f"{args.serve_budget_gb:.0f} GB arena, chunks of {chunk} steps",
+            "prep_s": prep_s, "results": out}), flush=True)
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup(args)
@@ -511,6 +583,8 @@ def main():
         run_reference(args, world, rank)
     elif args.workload == "stress":
         run_stress(args, world, rank, local)
+    elif args.workload == "serve":
+        run_serve(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -226,6 +226,10 @@ gs_status gs_init_lattice(const float* lr, const gs_grid* hr_grid, int32_t s, in
  *   step it holds dL/dLR); lr_target [nz / s, ny, nx]; d_loss float scalar (the loss of this
  *   step's forward pass); d_step int32 (Adam step counter); bins bound for n_gauss; ws
  *   workspace. On return grad holds dL/d(params) of this step.
+ *   If this step's binning overflows the bins' capacity, the step is a no-op: params, m, v
+ *   and d_step keep their values (grad is zeroed) and the status word carries
+ *   GS_STATUS_CAPACITY, so a caller can grow the bins and repeat the step with the same
+ *   result as if the capacity had sufficed.
  * phase_events: NULL, or GS_FIT_PHASES cudaEvent_t handles (host) recorded on `stream` at
  *   the start and after each phase: [0] start, [1] binning, [2] forward render, [3] slice
  *   profile + L1 + adjoint profile (with the adjoint's per-voxel factors), [4] adjoint render

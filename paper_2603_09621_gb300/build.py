@@ -34,8 +34,8 @@ def _sources():
 
 
 def _deps():
-    return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [
-        os.path.join(INCLUDE, "gs_api.h")]
+    return (_sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) +
+            sorted(glob.glob(os.path.join(INCLUDE, "*.h"))))
 
 
 def up_to_date() -> bool:

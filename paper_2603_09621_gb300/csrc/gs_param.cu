@@ -230,18 +230,24 @@ __global__ void __launch_bounds__(256) k_chain_adam(
     const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= N) return;
     float gv[12];
+    const int64_t P = *npairs;
+    if (P < 0 || P > capacity) {
+        // The binning overflowed: this step rendered nothing, so it leaves the parameters and
+        // moments as they are (the caller grows the bins and repeats the step).
+#pragma unroll
+        for (int k = 0; k < 12; ++k) gv[k] = 0.f;
+        store12(grad + g * 12, gv);
+        return;
+    }
     if (kDet) {
 #pragma unroll
         for (int k = 0; k < 12; ++k) gv[k] = 0.f;
-        const int64_t P = *npairs;
-        if (P >= 0 && P <= capacity) {
-            const int a = gm_off[g], e = gm_off[g + 1];
-            for (int j = a; j < e; ++j) {
-                float t[12];
-                load12(part + int64_t(j) * GRAD_FLOATS, t);
+        const int a = gm_off[g], e = gm_off[g + 1];
+        for (int j = a; j < e; ++j) {
+            float t[12];
+            load12(part + int64_t(j) * GRAD_FLOATS, t);
 #pragma unroll
-                for (int k = 0; k < 11; ++k) gv[k] += t[k];
-            }
+            for (int k = 0; k < 11; ++k) gv[k] += t[k];
         }
     } else {
         load12(gacc + g * GRAD_FLOATS, gv);
@@ -260,7 +266,15 @@ __global__ void __launch_bounds__(256) k_chain_adam(
     store12(v + g * 12, vv);
 }
 
-__global__ void k_step_inc(int32_t* d_step) { *d_step += 1; }
+// Counts a step, unless npairs is given and the step's binning overflowed the pair capacity
+// (then the fitting step was a no-op).
+__global__ void k_step_inc(int32_t* d_step, const int64_t* __restrict__ npairs, int64_t capacity) {
+    if (npairs) {
+        const int64_t P = *npairs;
+        if (P < 0 || P > capacity) return;
+    }
+    *d_step += 1;
+}
 
 // ------------------------------------------------------------------------ init
 struct InitGeo {
@@ -360,7 +374,7 @@ gs_status launch_chain_adam(float* params, float* grad, float* m, float* v, cons
                                                 bins->d_npairs, bins->capacity, n, C, a, d_step);
     gs_status s = last_launch_status();
     if (s != GS_OK) return s;
-    k_step_inc<<<1, 1, 0, st>>>(d_step);
+    k_step_inc<<<1, 1, 0, st>>>(d_step, bins->d_npairs, bins->capacity);
     return last_launch_status();
 }
 }  // namespace gs
@@ -392,7 +406,7 @@ extern "C" gs_status gs_adam_step(float* params, const float* grad, float* m, fl
         gs_status s = last_launch_status();
         if (s != GS_OK) return s;
     }
-    k_step_inc<<<1, 1, 0, st>>>(d_step);
+    k_step_inc<<<1, 1, 0, st>>>(d_step, nullptr, 0);
     return last_launch_status();
 }
 

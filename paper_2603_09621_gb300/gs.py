@@ -1,4 +1,4 @@
-"""Thin Python binding of libgsmri (C ABI in include/gs_api.h).
+"""Thin Python binding of libgsmri (C ABI in include/gs_api.h and include/gs_serve.h).
 
 Argument marshalling only: every step of the rendering path runs in the CUDA library; torch
 provides device memory and streams. Importing this module loads the library and raises if it
@@ -65,6 +65,43 @@ class gs_fit_state(ctypes.Structure):
 GS_FIT_PHASES = 7
 
 
+# serving runtime (include/gs_serve.h)
+class gs_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_active", ctypes.c_int32),
+                ("chunk_steps", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
+                ("max_bypass", ctypes.c_int32), ("pairs_per_gauss", ctypes.c_float),
+                ("cfg", gs_config), ("adam", gs_adam)]
+
+
+class gs_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("grid", gs_grid), ("s", ctypes.c_int32),
+                ("iters", ctypes.c_int32), ("n_gauss", ctypes.c_int64),
+                ("params", ctypes.c_void_p), ("lr_target", ctypes.c_void_p),
+                ("source", ctypes.c_int64), ("arrival_s", ctypes.c_double)]
+
+
+class gs_result(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("error", ctypes.c_int), ("status_bits", ctypes.c_int32),
+                ("steps_done", ctypes.c_int32), ("capacity", ctypes.c_int64),
+                ("grows", ctypes.c_int32), ("chunks", ctypes.c_int32), ("loss", ctypes.c_float),
+                ("arrival_s", ctypes.c_double), ("admit_s", ctypes.c_double),
+                ("done_s", ctypes.c_double), ("output", ctypes.c_void_p),
+                ("bytes", ctypes.c_size_t)]
+
+
+class gs_server_stats(ctypes.Structure):
+    _fields_ = [("now_s", ctypes.c_double), ("n_pending", ctypes.c_int32),
+                ("n_active", ctypes.c_int32), ("n_done", ctypes.c_int32),
+                ("n_failed", ctypes.c_int32), ("arena_bytes", ctypes.c_size_t),
+                ("used_bytes", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t),
+                ("chunks_launched", ctypes.c_int64), ("graphs_captured", ctypes.c_int64),
+                ("grows", ctypes.c_int64)]
+
+
+GS_REQ_FIT, GS_REQ_RENDER = 0, 1
+GS_REQ_PENDING, GS_REQ_ACTIVE, GS_REQ_DONE, GS_REQ_FAILED = 0, 1, 2, 3
+
+
 STATUS = {0: "GS_OK", -1: "GS_ERR_INVALID_ARG", -2: "GS_ERR_CAPACITY", -3: "GS_ERR_WORKSPACE",
           -4: "GS_ERR_CUDA", -5: "GS_ERR_TIMEOUT", -6: "GS_ERR_NONFINITE"}
 GS_STATUS_CAPACITY = 1
@@ -92,6 +129,22 @@ SIGNATURES = {
     "gs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "gs_launch_count": (ctypes.c_ulonglong, []),
     "gs_version": (ctypes.c_char_p, []),
+    # serving runtime
+    "gs_arena_create": (ctypes.c_int, [_P, _SZ, _P]),
+    "gs_arena_alloc": (ctypes.c_int, [_P, _SZ, _P]),
+    "gs_arena_alloc_top": (ctypes.c_int, [_P, _SZ, _P]),
+    "gs_arena_free": (ctypes.c_int, [_P, _P]),
+    "gs_arena_stats": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "gs_arena_destroy": (None, [_P]),
+    "gs_server_request_bytes": (_SZ, [_P, _P]),
+    "gs_server_create": (ctypes.c_int, [_P, _P]),
+    "gs_server_submit": (ctypes.c_int, [_P, _P, _P]),
+    "gs_server_poll": (ctypes.c_int, [_P, _P]),
+    "gs_server_run": (ctypes.c_int, [_P, ctypes.c_double, _I32]),
+    "gs_server_result": (ctypes.c_int, [_P, _I64, _P]),
+    "gs_server_release": (ctypes.c_int, [_P, _I64]),
+    "gs_server_stats_read": (ctypes.c_int, [_P, _P]),
+    "gs_server_destroy": (None, [_P]),
 }
 
 

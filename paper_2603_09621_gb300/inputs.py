@@ -14,6 +14,8 @@ Workloads (all coordinates in world units, mm; grids are 1 mm isotropic unless s
     scan. It stands in for the MSD / FeTA brain volumes of Sec. 4.1, which are not used.
   * ``gmm_cloud``: clustered, strongly anisotropic clouds (Gaussian-mixture blobs; one axis
     scale log-uniform in [4, 8] voxels, the others in [0.5, 1.5]).
+  * ``serving_draws``: a stream of fitting and re-rendering requests for the serving runtime
+    (Poisson arrivals, scan sizes, slice factors, output grids).
 """
 from __future__ import annotations
 
@@ -142,3 +144,50 @@ def crop_dI(seed: int, crop_shape_zyx) -> np.ndarray:
     """Random upstream gradient dL/dI on a crop (standard normal, float32)."""
     rng = np.random.default_rng(seed)
     return rng.standard_normal(size=crop_shape_zyx).astype(np.float32)
+
+
+# Scan sizes (nz, ny, nx) of the serving stream: 128^3, 192 x 192 x 128 and 256 x 256 x
+# 160 / 192 (brain-MRI-like fields of view at 1 mm).
+SERVE_SHAPES = ((128, 128, 128), (128, 192, 192), (160, 256, 256), (192, 256, 256))
+SERVE_RENDER_SPACINGS = (0.8, 1.0, 1.25)
+
+
+def serve_n_gauss(shape_zyx) -> int:
+    """Cloud size of a scan: 1M Gaussians for 256 x 256 x 192 voxels, in proportion to the
+    voxel count, at least 100k."""
+    v = int(np.prod(shape_zyx))
+    return max(100_000, int(round(1e6 * v / (256 * 256 * 192))))
+
+
+def serving_draws(seed: int = 0, n: int = 32, rate_hz: float = 2.0, fit_frac: float = 0.75,
+                  iters: int = 500) -> list:
+    """Request stream: arrivals of a Poisson process of `rate_hz` (the first at t = 0); each
+    request fits a new scan (probability fit_frac; shape from SERVE_SHAPES, slice factor in
+    {2, 3, 4}, `iters` steps) or re-renders the cloud of an earlier fit request on the same
+    field of view at isotropic spacing from SERVE_RENDER_SPACINGS. The first request is a fit.
+    Each entry: dict(kind 'fit' | 'render', arrival_s, shape (nz, ny, nx), s, iters, n_gauss,
+    seed) for a fit; dict(kind, arrival_s, source (index of the fit), spacing, shape) for a
+    render (shape = the source's field of view / spacing, rounded)."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate_hz, size=n)
+    arrivals = np.concatenate([[0.0], np.cumsum(gaps[1:])])
+    out = []
+    fits = []
+    for i in range(n):
+        u_kind = rng.uniform()
+        i_shape = int(rng.integers(len(SERVE_SHAPES)))
+        s = int(rng.integers(2, 5))
+        i_src = rng.uniform()
+        i_sp = int(rng.integers(len(SERVE_RENDER_SPACINGS)))
+        if not fits or u_kind < fit_frac:
+            shape = SERVE_SHAPES[i_shape]
+            out.append(dict(kind="fit", arrival_s=float(arrivals[i]), shape=shape, s=s,
+                            iters=iters, n_gauss=serve_n_gauss(shape), seed=1000 + i))
+            fits.append(i)
+        else:
+            src = fits[int(i_src * len(fits))]
+            h = SERVE_RENDER_SPACINGS[i_sp]
+            shape = tuple(int(round(d / h)) for d in out[src]["shape"])
+            out.append(dict(kind="render", arrival_s=float(arrivals[i]), source=src,
+                            spacing=h, shape=shape))
+    return out

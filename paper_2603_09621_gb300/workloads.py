@@ -59,3 +59,25 @@ def phantom_fit(shape=(128, 256, 256), s=4, n_gauss=500_000, seed=0, n_ell=12,
     nl = lattice_dims(grid, n_gauss)
     params0 = gs.gs_init_lattice(lr, grid, s, nl, t_act=1, t_init=0.5)
     return dict(grid=grid, hr=hr, lr=lr, params0=params0, s=s, nl=nl)
+
+
+def serving_workload(draws: list, device="cuda") -> list:
+    """Device inputs of a serving request stream (``inputs.serving_draws``): each fit gets its
+    own phantom scan (seeded by its draw), noisy LR target and lattice-initialised cloud; each
+    render gets its output grid. Returns the draws with ``grid`` added, and ``params0``,
+    ``lr`` for fits."""
+    out = []
+    for d in draws:
+        e = dict(d)
+        if d["kind"] == "fit":
+            w = phantom_fit(shape=d["shape"], s=d["s"], n_gauss=d["n_gauss"], seed=d["seed"],
+                            device=device)
+            e.update(grid=w["grid"], params0=w["params0"], lr=w["lr"],
+                     n_gauss=int(w["params0"].shape[0]))
+            del w
+        else:
+            nz, ny, nx = d["shape"]
+            h = float(d["spacing"])
+            e.update(grid=gs.Grid(nx, ny, nz, (h, h, h)))
+        out.append(e)
+    return out

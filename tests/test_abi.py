@@ -1,5 +1,6 @@
 """The C-ABI library builds for sm_103a, loads, and exports every entry point declared in
-include/gs_api.h; host-only entry points validate their arguments (no GPU needed)."""
+include/*.h; host-only entry points validate their arguments (no GPU needed)."""
+import glob
 import ctypes
 import os
 import re
@@ -7,11 +8,11 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "gs_api.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 def declared_functions():
-    src = open(HEADER).read()
+    src = "\n".join(open(h).read() for h in HEADERS)
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(gs_[a-z0-9_]+)\s*\(",
                        src, flags=re.M)

@@ -110,3 +110,33 @@ def test_fit_step_graph_replay_matches_eager():
     torch.cuda.synchronize()
     assert torch.equal(eager.params, graphed.params)
     assert int(graphed.d_step) == 3
+
+
+@pytest.mark.parametrize("deterministic", [1, 0])
+def test_fit_step_overflow_is_a_no_op(deterministic):
+    """A step whose binning overflows the pair capacity leaves params, moments and the step
+    counter unchanged and reports GS_STATUS_CAPACITY; after growing, the fit continues as if
+    the capacity had sufficed."""
+    import torch
+    gs = _gs()
+    w = small_fit()
+    og = w["grid"]
+    g = gs.Grid(og.nx, og.ny, og.nz)
+    cfg = gs.Config(t_act=1, deterministic=deterministic)
+    ref = gs.FitState(to_dev(w["params0"]), to_dev(w["lr"]), g, w["s"], cfg)
+    tiny = gs.FitState(to_dev(w["params0"]), to_dev(w["lr"]), g, w["s"], cfg, capacity=1000)
+    ref.step()
+    tiny.step()
+    tiny.step()
+    torch.cuda.synchronize()
+    rc, bits = tiny.check()
+    assert bits & gs.GS_STATUS_CAPACITY
+    assert int(tiny.d_step) == 0
+    assert torch.equal(tiny.params, to_dev(w["params0"]))
+    assert int(torch.count_nonzero(tiny.m)) == 0 and int(torch.count_nonzero(tiny.v)) == 0
+    assert int(torch.count_nonzero(tiny.grad)) == 0
+    if deterministic:
+        grown = gs.FitState(tiny.params, to_dev(w["lr"]), g, w["s"], cfg, capacity=ref.capacity)
+        grown.step()
+        torch.cuda.synchronize()
+        assert torch.equal(grown.params, ref.params)
