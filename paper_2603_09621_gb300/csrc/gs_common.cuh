@@ -86,7 +86,7 @@ struct Workspace {
     long long* scan_tmp;     // block sums of the multi-level scan
     float* part;             // [capacity, 12] per-pair partial gradients (deterministic mode)
     float* gacc;             // [n_gauss, 12] render-space gradient per Gaussian
-    float2* aip;             // [n_voxels] (dL/dI / max(W, eps), I') for the adjoint
+    float2* aip;             // [n_voxels] (alpha, alpha I'), alpha = dL/dI / max(W, eps)
     float* l1_part;          // [kL1Blocks]
     int64_t scan_tmp_len;
     int32_t n_tiles;

@@ -16,13 +16,15 @@
 // W in registers (deterministic).
 // Adjoint: one thread per (brick, Gaussian) pair evaluates the brick rows the Gaussian
 // reaches (the row shadow, per z-row a quadratic in dy), each row as bx predicated voxel
-// slots, so lanes never diverge inside a row. A block takes 256 consecutive brick-major pairs
+// slots, so lanes never diverge inside a row. A block takes 128 consecutive brick-major pairs
 // (one or two bricks), computes their row masks and counting-sorts them by number of rows in
-// shared memory, so each warp runs pairs of equal length while the block keeps its bricks'
-// locality in L1/L2. The per-voxel factors (dL/dI / max(W, eps), I') are precomputed into
-// one float2 volume. Each pair's partial is summed by one thread in a fixed voxel order (the
-// processing order does not change results) and goes to a per-pair slot (deterministic mode,
-// reduced later in Gaussian-major order) or to one float atomic per value (fast mode).
+// shared memory, so each warp runs pairs of equal length. The per-voxel factors
+// (alpha, alpha I'), alpha = dL/dI / max(W, eps), are precomputed into one float2 volume; a
+// block copies those of its first three bricks into shared memory (zero outside the grid), so
+// rows read them without range tests. Each pair's partial is summed by one thread in a fixed
+// voxel order (the processing order does not change results) and goes to a per-pair slot
+// (deterministic mode, reduced later in Gaussian-major order) or to one float atomic per
+// value (fast mode).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -33,6 +35,8 @@ namespace gs {
 
 constexpr int kFwdChunk = 128;   // Gaussians staged per forward round
 constexpr int kBwdThreads = 128;
+constexpr int kBwdStage = 3;          // bricks of per-voxel factors staged per adjoint block
+constexpr int kMaxBrickVoxels = 512;  // brick volume limit (x * y * z <= 512)
 
 struct RenderGeo {
     int nx, ny, nz;
@@ -200,8 +204,9 @@ __device__ __forceinline__ unsigned long long brick_row_mask(const Rec& R, const
     return mask;
 }
 
-// Per-voxel adjoint factors: dL/dw_i = (v_i - I') alpha with alpha = dL/dI / max(W, eps) and
-// I' = I where W > eps, else 0 (Eq. 5; below the floor I = S / eps, so dI/dw_i = v_i / eps).
+// Per-voxel adjoint factors (alpha, alpha I'): dL/dw_i = v_i alpha - alpha I' with
+// alpha = dL/dI / max(W, eps) and I' = I where W > eps, else 0 (Eq. 5; below the floor
+// I = S / eps, so dI/dw_i = v_i / eps).
 __global__ void __launch_bounds__(256) k_bwd_prep(const float* __restrict__ Iv,
                                                   const float* __restrict__ Wv,
                                                   const float* __restrict__ dIv, int64_t n,
@@ -209,38 +214,133 @@ __global__ void __launch_bounds__(256) k_bwd_prep(const float* __restrict__ Iv,
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += int64_t(gridDim.x) * blockDim.x) {
         const float w = Wv[i], gI = dIv[i];
-        aip[i] = make_float2(gI / (w > eps ? w : eps), (w > eps) ? Iv[i] : 0.0f);
+        const float al = gI / (w > eps ? w : eps);
+        aip[i] = make_float2(al, (w > eps) ? al * Iv[i] : 0.0f);
+    }
+}
+
+// The rows of one (brick, Gaussian) pair: for each row in the mask, bx voxel slots with the
+// factors (alpha, alpha I') read from the block's staged copy (kStaged) or from the volume.
+// Accumulates with h = gamma g (gamma = dL/dw): acc[10] = sum h, acc[9] = sum alpha g and the
+// first and second moments of h about the Gaussian's mean (acc[0..8]).
+template <int BX, bool kStaged>
+__device__ __forceinline__ void adjoint_rows(const Rec& R, unsigned long long m, const RenderGeo& G,
+                                             int x0, int y0, int z0,
+                                             const float2* __restrict__ sfac_b,
+                                             const float2* __restrict__ aip, float (&acc)[11]) {
+    const int x1 = min(x0 + BX, G.nx) - 1;
+    const bool full_row = (x1 == x0 + BX - 1) && ((G.nx & 1) == 0);  // 16-byte aligned rows
+    const float ux0 = (float(x0) - R.mhx) - R.mlx;
+    while (m) {
+        const int r = __ffsll(static_cast<long long>(m)) - 1;
+        m &= m - 1;
+        const int y = y0 + (r & G.bsy_mask), z = z0 + (r >> G.bsy_shift);
+        float dy, dz, S, dxs;
+        row_terms(R, float(y), float(z), dy, dz, S, dxs);
+        // (alpha, alpha I') of the row's voxels; zero outside the grid
+        float2 av[BX];
+        if (kStaged) {
+            const float4* s4 = reinterpret_cast<const float4*>(sfac_b + r * BX);
+#pragma unroll
+            for (int k = 0; k < BX / 2; ++k) {
+                const float4 v = s4[k];
+                av[2 * k] = make_float2(v.x, v.y);
+                av[2 * k + 1] = make_float2(v.z, v.w);
+            }
+        } else {
+            const bool row_in = (y < G.ny) && (z < G.nz);
+            const float2* arow = aip + (int64_t(min(z, G.nz - 1)) * G.ny + min(y, G.ny - 1)) * G.nx + x0;
+            if (full_row && row_in) {
+                const float4* a4 = reinterpret_cast<const float4*>(arow);
+#pragma unroll
+                for (int k = 0; k < BX / 2; ++k) {
+                    const float4 v = a4[k];
+                    av[2 * k] = make_float2(v.x, v.y);
+                    av[2 * k + 1] = make_float2(v.z, v.w);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < BX; ++k)
+                    av[k] = (row_in && x0 + k <= x1) ? arow[k] : make_float2(0.f, 0.f);
+            }
+        }
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+        for (int xb = 0; xb < BX; ++xb) {
+            const float u = ux0 + float(xb);
+            const float t = u - dxs;
+            const float q = fmaf(R.a * t, t, S);
+            const float g = (q <= G.T) ? ex2_approx(-q) : 0.0f;
+            const float h = fmaf(R.v, av[xb].x, -av[xb].y) * g;
+            acc[9] = fmaf(av[xb].x, g, acc[9]);
+            s0 += h;
+            const float tg = h * u;
+            s1 += tg;
+            s2 = fmaf(tg, u, s2);
+        }
+        acc[10] += s0;
+        acc[0] += s1;
+        acc[1] = fmaf(dy, s0, acc[1]);
+        acc[2] = fmaf(dz, s0, acc[2]);
+        acc[3] += s2;
+        acc[6] = fmaf(dy, s1, acc[6]);
+        acc[7] = fmaf(dz, s1, acc[7]);
+        const float ty = dy * s0;
+        acc[4] = fmaf(ty, dy, acc[4]);
+        acc[8] = fmaf(ty, dz, acc[8]);
+        acc[5] = fmaf(dz * s0, dz, acc[5]);
     }
 }
 
 template <int BX, bool kDet>
-__global__ void __launch_bounds__(kBwdThreads, 6) k_render_bwd(
+__global__ void __launch_bounds__(kBwdThreads, 8) k_render_bwd(
     const int32_t* __restrict__ pair_gid, const int32_t* __restrict__ pair_gmj,
     const int32_t* __restrict__ pair_brick, const int64_t* __restrict__ npairs, int64_t capacity,
     const float4* __restrict__ rec4, RenderGeo G, const float2* __restrict__ aip,
     float* __restrict__ part, float* __restrict__ gacc) {
     __shared__ float4 srec[kBwdThreads][REC_F4];
+    __shared__ __align__(16) float2 sfac[kBwdStage][kMaxBrickVoxels];
     __shared__ unsigned long long smask[kBwdThreads];
     __shared__ unsigned short sorder[kBwdThreads];
+    __shared__ unsigned char sstage[kBwdThreads];
     __shared__ int hist[66];
     __shared__ int cursor[66];
+    __shared__ int sbrick[kBwdStage];
+    __shared__ int wcount[kBwdThreads / 32];
     int64_t P = *npairs;
     if (P < 0 || P > capacity) P = 0;
     const int64_t base = int64_t(blockIdx.x) * kBwdThreads;
     if (base >= P) return;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nvalid = static_cast<int>(min(int64_t(kBwdThreads), P - base));
     for (int k = tid; k < 66; k += blockDim.x) {
         hist[k] = 0;
         cursor[k] = 0;
     }
+    // distinct bricks of the block's pairs (brick-major order: a new brick starts a run)
+    int b_t = 0;
+    bool newb = false;
+    if (tid < nvalid) {
+        b_t = pair_brick[base + tid];
+        newb = (tid == 0) || (b_t != pair_brick[base + tid - 1]);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, newb);
+    if (lane == 0) wcount[warp] = __popc(bal);
     __syncthreads();
+    int run_before = 0, n_bricks = 0;
+#pragma unroll
+    for (int w = 0; w < kBwdThreads / 32; ++w) {
+        run_before += (w < warp) ? wcount[w] : 0;
+        n_bricks += wcount[w];
+    }
     // row mask of this thread's pair, staged record, histogram of row counts (most first)
     int bucket = 0;
     if (tid < nvalid) {
+        const int kb = run_before + __popc(bal & ((1u << lane) - 1u)) + (newb ? 1 : 0) - 1;
+        if (newb && kb < kBwdStage) sbrick[kb] = b_t;
+        sstage[tid] = static_cast<unsigned char>(min(kb, kBwdStage));
         const int64_t i = base + tid;
-        const int b = pair_brick[i];
-        const int by = (b / G.nbx) % G.nby, bz = b / (G.nbx * G.nby);
+        const int by = (b_t / G.nbx) % G.nby, bz = b_t / (G.nbx * G.nby);
         const float4* src = rec4 + int64_t(pair_gid[i]) * REC_F4;
 #pragma unroll
         for (int k = 0; k < REC_F4; ++k) srec[tid][k] = src[k];
@@ -258,6 +358,22 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_render_bwd(
             run += c;
         }
     }
+    // per-voxel factors of the first kBwdStage bricks into shared memory, zero outside the
+    // grid, so the row loop needs no range tests
+    const int n_stage = min(n_bricks, kBwdStage);
+    const int bvox = BX * G.bsy * G.bsz;
+    for (int k = 0; k < n_stage; ++k) {
+        const int b = sbrick[k];
+        const int x0 = (b % G.nbx) * BX, y0 = ((b / G.nbx) % G.nby) * G.bsy,
+                  z0 = (b / (G.nbx * G.nby)) * G.bsz;
+        for (int e = tid; e < bvox; e += kBwdThreads) {
+            const int xb = e % BX, r = e / BX;
+            const int x = x0 + xb, y = y0 + (r & G.bsy_mask), z = z0 + (r >> G.bsy_shift);
+            sfac[k][e] = (x < G.nx && y < G.ny && z < G.nz)
+                             ? aip[(int64_t(z) * G.ny + y) * G.nx + x]
+                             : make_float2(0.f, 0.f);
+        }
+    }
     __syncthreads();
     if (tid < nvalid) sorder[hist[bucket] + atomicAdd(&cursor[bucket], 1)] = static_cast<unsigned short>(tid);
     __syncthreads();
@@ -268,65 +384,21 @@ __global__ void __launch_bounds__(kBwdThreads, 6) k_render_bwd(
     const int b = pair_brick[i];
     const int bx = b % G.nbx, by = (b / G.nbx) % G.nby, bz = b / (G.nbx * G.nby);
     const int x0 = bx * BX, y0 = by * G.bsy, z0 = bz * G.bsz;
-    const int x1 = min(x0 + BX, G.nx) - 1;
-    const bool full_row = (x1 == x0 + BX - 1) && ((G.nx & 1) == 0);  // 16-byte aligned rows
+    const int stage = sstage[lt];
     const Rec R = load_rec(srec[lt]);
-    unsigned long long m = smask[lt];
+    const unsigned long long m = smask[lt];
     const bool any = m != 0ull;
-    // Accumulated per pair with h = gamma g (gamma = dL/dw): dr = sum h, dv = r sum alpha g,
-    // and the moments of G = gamma w = r h are r times the moments of h.
-    float m1x = 0.f, m1y = 0.f, m1z = 0.f, m2xx = 0.f, m2yy = 0.f, m2zz = 0.f;
-    float m2xy = 0.f, m2xz = 0.f, m2yz = 0.f, dvp = 0.f, dr = 0.f;
-    const float ux0 = (float(x0) - R.mhx) - R.mlx;
-    while (m) {
-        const int r = __ffsll(static_cast<long long>(m)) - 1;
-        m &= m - 1;
-        const int yr = y0 + (r & G.bsy_mask), zr = z0 + (r >> G.bsy_shift);
-        const bool row_in = (yr < G.ny) && (zr < G.nz);
-        const int y = min(yr, G.ny - 1), z = min(zr, G.nz - 1);
-        float dy, dz, S, dxs;
-        row_terms(R, float(y), float(z), dy, dz, S, dxs);
-        const float2* arow = aip + (int64_t(z) * G.ny + y) * G.nx + x0;
-        float2 av[BX];
-        if (full_row) {
-            const float4* a4 = reinterpret_cast<const float4*>(arow);
+    // acc: m1 (x, y, z), m2 (xx, yy, zz, xy, xz, yz), sum alpha g, sum h
+    float acc[11];
 #pragma unroll
-            for (int k = 0; k < BX / 2; ++k) {
-                const float4 v = a4[k];
-                av[2 * k] = make_float2(v.x, v.y);
-                av[2 * k + 1] = make_float2(v.z, v.w);
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < BX; ++k) av[k] = arow[min(k, x1 - x0)];
-        }
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-#pragma unroll
-        for (int xb = 0; xb < BX; ++xb) {
-            const float u = ux0 + float(xb);
-            const float t = u - dxs;
-            const float q = fmaf(R.a * t, t, S);
-            const bool in = row_in && (x0 + xb <= x1) && (q <= G.T);
-            const float g = in ? ex2_approx(-q) : 0.0f;
-            const float h = (R.v - av[xb].y) * av[xb].x * g;
-            dvp = fmaf(av[xb].x, g, dvp);
-            s0 += h;
-            const float tg = h * u;
-            s1 += tg;
-            s2 = fmaf(tg, u, s2);
-        }
-        dr += s0;
-        m1x += s1;
-        m1y = fmaf(dy, s0, m1y);
-        m1z = fmaf(dz, s0, m1z);
-        m2xx += s2;
-        m2xy = fmaf(dy, s1, m2xy);
-        m2xz = fmaf(dz, s1, m2xz);
-        const float ty = dy * s0;
-        m2yy = fmaf(ty, dy, m2yy);
-        m2yz = fmaf(ty, dz, m2yz);
-        m2zz = fmaf(dz * s0, dz, m2zz);
-    }
+    for (int k = 0; k < 11; ++k) acc[k] = 0.f;
+    if (stage < kBwdStage)
+        adjoint_rows<BX, true>(R, m, G, x0, y0, z0, &sfac[stage][0], aip, acc);
+    else
+        adjoint_rows<BX, false>(R, m, G, x0, y0, z0, nullptr, aip, acc);
+    float m1x = acc[0], m1y = acc[1], m1z = acc[2], m2xx = acc[3], m2yy = acc[4], m2zz = acc[5];
+    float m2xy = acc[6], m2xz = acc[7], m2yz = acc[8];
+    const float dvp = acc[9], dr = acc[10];
     const float rr = R.r;
     const float dv = rr * dvp;
     m1x *= rr; m1y *= rr; m1z *= rr;

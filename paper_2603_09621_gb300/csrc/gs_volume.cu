@@ -125,7 +125,7 @@ gs_status launch_chain_adam(float* params, float* grad, float* m, float* v, cons
 
 // Slice-profile adjoint fused with the adjoint render's per-voxel factors: for each HR voxel
 // dL/dI = dL/dLR[z / s] / s (0 below the last full slab), alpha = dL/dI / max(W, eps) and
-// I' = I where W > eps, else 0.
+// I' = I where W > eps, else 0; stored as (alpha, alpha I').
 __global__ void __launch_bounds__(256) k_profile_adj_prep(const float* __restrict__ dlr,
                                                           const float* __restrict__ Iv,
                                                           const float* __restrict__ Wv, int nz,
@@ -139,7 +139,8 @@ __global__ void __launch_bounds__(256) k_profile_adj_prep(const float* __restric
         const int64_t z = i / plane, r = i - z * plane;
         const float gI = (z < zmax) ? dlr[(z / s) * plane + r] * inv_s : 0.0f;
         const float w = Wv[i];
-        aip[i] = make_float2(gI / (w > eps ? w : eps), (w > eps) ? Iv[i] : 0.0f);
+        const float al = gI / (w > eps ? w : eps);
+        aip[i] = make_float2(al, (w > eps) ? al * Iv[i] : 0.0f);
     }
 }
 
