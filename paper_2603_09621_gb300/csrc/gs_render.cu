@@ -8,12 +8,12 @@
 // in both kernels from the voxel's global index and the Gaussian alone, so forward and
 // adjoint agree on every inclusion decision and no result depends on the brick shape.
 //
-// Forward: the brick is split into 4 x 4 x 4 footprints, one warp each; a lane owns two
-// voxels along x. A warp tests 32 staged Gaussians against its footprint with one ballot
-// (triangle inequality in whitened space: |M (p - mu)| >= |M (c - mu)| - sum_j h_j |m_j|, so a
-// footprint whose centre c is farther than sqrt(T) + 1.5 sum_j |m_j| is missed; a margin
-// absorbs FP32 rounding) and evaluates the hits in ascending Gaussian id, accumulating S and
-// W in registers (deterministic).
+// Forward: the brick is split into 4 x 4 x 4 footprints, one half-warp each; a lane owns one
+// x-row of four voxels. A half-warp tests 16 staged Gaussians against its footprint with one
+// ballot (triangle inequality in whitened space: |M (p - mu)| >= |M (c - mu)| - rho4, with
+// rho4 the whitened radius of the footprint around its centre c, so a footprint whose centre
+// is farther than sqrt(T) + rho4 is missed; a margin absorbs FP32 rounding) and evaluates the
+// hits in ascending Gaussian id, accumulating S and W in registers (deterministic).
 // Adjoint: one thread per (brick, Gaussian) pair evaluates the brick rows the Gaussian
 // reaches (the row shadow, per z-row a quadratic in dy), each row as bx predicated voxel
 // slots, so lanes never diverge inside a row. A block takes 128 consecutive brick-major pairs
@@ -76,11 +76,22 @@ __device__ __forceinline__ void row_terms(const Rec& R, float fy, float fz, floa
     dxs = fmaf(R.c1, dy, R.c2 * dz);
 }
 
-// q at the voxel whose global x index is fx, given the row terms; u = dx is returned too.
-__device__ __forceinline__ float q_at(const Rec& R, float fx, float S, float dxs, float& u) {
-    u = (fx - R.mhx) - R.mlx;
+// x offset of voxel x from the mean, u = ux_base(R, x & ~3) + (x & 3): the same operation
+// sequence in every kernel, so forward and adjoint agree on every inclusion q <= T.
+__device__ __forceinline__ float ux_base(const Rec& R, int x4) {
+    return (float(x4) - R.mhx) - R.mlx;
+}
+
+// q at x offset u, given the row terms.
+__device__ __forceinline__ float q_of_u(const Rec& R, float u, float S, float dxs) {
     const float t = u - dxs;
     return fmaf(R.a * t, t, S);
+}
+
+// q at the point with (fractional) x index fx, given the row terms (footprint culling).
+__device__ __forceinline__ float q_at(const Rec& R, float fx, float S, float dxs, float& u) {
+    u = (fx - R.mhx) - R.mlx;
+    return q_of_u(R, u, S, dxs);
 }
 
 // Footprint cull: may the Gaussian reach a voxel centre within 3/2 of (cx, cy, cz) per axis?
@@ -102,17 +113,23 @@ __global__ void __launch_bounds__(256) k_render_fwd(const int32_t* __restrict__ 
                                                     float* __restrict__ I, float* __restrict__ W,
                                                     unsigned long long* __restrict__ stats) {
     __shared__ float4 srec[kFwdChunk][REC_F4];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int nthreads = blockDim.x;
     const int b = blockIdx.x;
     const int bx = b % G.nbx, by = (b / G.nbx) % G.nby, bz = b / (G.nbx * G.nby);
-    const int wx = warp % G.fx, wy = (warp / G.fx) % G.fy, wz = warp / (G.fx * G.fy);
+    // half-warp per 4^3 footprint; a lane owns one x-row of 4 voxels
+    const int foot = tid >> 4, l16 = lane & 15;
+    const int n_foot = G.fx * G.fy * G.fz;
+    const bool foot_ok = foot < n_foot;
+    const int f = foot_ok ? foot : 0;
+    const int wx = f % G.fx, wy = (f / G.fx) % G.fy, wz = f / (G.fx * G.fy);
     const int ox = bx * G.bsx + wx * 4, oy = by * G.bsy + wy * 4, oz = bz * G.bsz + wz * 4;
-    const int x0 = ox + 2 * (lane & 1), y = oy + ((lane >> 1) & 3), z = oz + (lane >> 3);
-    const float fx0 = float(x0), fx1 = float(x0 + 1), fy = float(y), fz = float(z);
+    const int y = oy + (l16 & 3), z = oz + (l16 >> 2);
+    const float fy = float(y), fz = float(z);
     const float cx = float(ox) + 1.5f, cy = float(oy) + 1.5f, cz = float(oz) + 1.5f;
+    const unsigned half_sel = (lane < 16) ? 0x0000ffffu : 0xffff0000u;
 
-    float S0 = 0.f, W0 = 0.f, S1 = 0.f, W1 = 0.f;
+    float S[4] = {0.f, 0.f, 0.f, 0.f}, Wt[4] = {0.f, 0.f, 0.f, 0.f};
     unsigned long long n_eff = 0, n_eval = 0;
     const int start = brick_off[b], end = brick_off[b + 1];
     for (int c0 = start; c0 < end; c0 += kFwdChunk) {
@@ -123,43 +140,52 @@ __global__ void __launch_bounds__(256) k_render_fwd(const int32_t* __restrict__ 
             srec[k][part] = rec4[int64_t(pair_gid[c0 + k]) * REC_F4 + part];
         }
         __syncthreads();
-        for (int k0 = 0; k0 < cnt; k0 += 32) {
-            const int k = k0 + lane;
-            const bool hit = (k < cnt) && foot_hit(srec[k], cx, cy, cz, G.sqrtTcull);
-            unsigned mask = __ballot_sync(0xffffffffu, hit);
-            while (mask) {
-                const int kk = k0 + __ffs(mask) - 1;
-                mask &= mask - 1;
-                const Rec R = load_rec(srec[kk]);
-                float dy, dz, S, dxs, u0, u1;
-                row_terms(R, fy, fz, dy, dz, S, dxs);
-                const float q0 = q_at(R, fx0, S, dxs, u0);
-                const float q1 = q_at(R, fx1, S, dxs, u1);
-                float g0 = ex2_approx(-q0), g1 = ex2_approx(-q1);
-                g0 = (q0 <= G.T) ? g0 : 0.0f;
-                g1 = (q1 <= G.T) ? g1 : 0.0f;
-                S0 = fmaf(R.vr, g0, S0);
-                W0 = fmaf(R.r, g0, W0);
-                S1 = fmaf(R.vr, g1, S1);
-                W1 = fmaf(R.r, g1, W1);
-                if (kStats) {
-                    const bool in_yz = y < G.ny && z < G.nz;
-                    n_eff += (in_yz && x0 < G.nx && q0 <= G.T) ? 1 : 0;
-                    n_eff += (in_yz && x0 + 1 < G.nx && q1 <= G.T) ? 1 : 0;
-                    n_eval += 2;
+        for (int k0 = 0; k0 < cnt; k0 += 16) {
+            // lane l16 of each half tests Gaussian k0 + l16 against the half's footprint
+            const int k = k0 + l16;
+            const bool hit = foot_ok && (k < cnt) && foot_hit(srec[k], cx, cy, cz, G.sqrtTcull);
+            const unsigned bal = __ballot_sync(0xffffffffu, hit);
+            unsigned mask = (bal & half_sel) >> (lane & 16);
+            // each half takes its hits in ascending Gaussian id (per voxel the order of Eq. 3)
+            while (__any_sync(0xffffffffu, mask != 0u)) {
+                if (mask) {
+                    const int kk = k0 + __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    const Rec R = load_rec(srec[kk]);
+                    float dy, dz, Sr, dxs;
+                    row_terms(R, fy, fz, dy, dz, Sr, dxs);
+                    const float ux = ux_base(R, ox);
+#pragma unroll
+                    for (int xi = 0; xi < 4; ++xi) {
+                        const float q = q_of_u(R, ux + float(xi), Sr, dxs);
+                        float g = ex2_approx(-q);
+                        g = (q <= G.T) ? g : 0.0f;
+                        S[xi] = fmaf(R.vr, g, S[xi]);
+                        Wt[xi] = fmaf(R.r, g, Wt[xi]);
+                        if (kStats) {
+                            n_eff += (y < G.ny && z < G.nz && ox + xi < G.nx && q <= G.T) ? 1 : 0;
+                            n_eval += 1;
+                        }
+                    }
                 }
             }
         }
     }
-    if (y < G.ny && z < G.nz) {
-        const int64_t row = (int64_t(z) * G.ny + y) * G.nx;
-        if (x0 < G.nx) {
-            I[row + x0] = S0 / (W0 > G.eps ? W0 : G.eps);
-            W[row + x0] = W0;
-        }
-        if (x0 + 1 < G.nx) {
-            I[row + x0 + 1] = S1 / (W1 > G.eps ? W1 : G.eps);
-            W[row + x0 + 1] = W1;
+    if (foot_ok && y < G.ny && z < G.nz) {
+        const int64_t row = (int64_t(z) * G.ny + y) * G.nx + ox;
+        float Iv[4];
+#pragma unroll
+        for (int xi = 0; xi < 4; ++xi) Iv[xi] = S[xi] / (Wt[xi] > G.eps ? Wt[xi] : G.eps);
+        if (ox + 3 < G.nx && (G.nx & 3) == 0) {
+            *reinterpret_cast<float4*>(I + row) = make_float4(Iv[0], Iv[1], Iv[2], Iv[3]);
+            *reinterpret_cast<float4*>(W + row) = make_float4(Wt[0], Wt[1], Wt[2], Wt[3]);
+        } else {
+#pragma unroll
+            for (int xi = 0; xi < 4; ++xi)
+                if (ox + xi < G.nx) {
+                    I[row + xi] = Iv[xi];
+                    W[row + xi] = Wt[xi];
+                }
         }
     }
     if (kStats) {
@@ -230,7 +256,9 @@ __device__ __forceinline__ void adjoint_rows(const Rec& R, unsigned long long m,
                                              const float2* __restrict__ aip, float (&acc)[11]) {
     const int x1 = min(x0 + BX, G.nx) - 1;
     const bool full_row = (x1 == x0 + BX - 1) && ((G.nx & 1) == 0);  // 16-byte aligned rows
-    const float ux0 = (float(x0) - R.mhx) - R.mlx;
+    float ux4[BX / 4];
+#pragma unroll
+    for (int j = 0; j < BX / 4; ++j) ux4[j] = ux_base(R, x0 + 4 * j);
     while (m) {
         const int r = __ffsll(static_cast<long long>(m)) - 1;
         m &= m - 1;
@@ -267,9 +295,8 @@ __device__ __forceinline__ void adjoint_rows(const Rec& R, unsigned long long m,
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
 #pragma unroll
         for (int xb = 0; xb < BX; ++xb) {
-            const float u = ux0 + float(xb);
-            const float t = u - dxs;
-            const float q = fmaf(R.a * t, t, S);
+            const float u = ux4[xb >> 2] + float(xb & 3);
+            const float q = q_of_u(R, u, S, dxs);
             const float g = (q <= G.T) ? ex2_approx(-q) : 0.0f;
             const float h = fmaf(R.v, av[xb].x, -av[xb].y) * g;
             acc[9] = fmaf(av[xb].x, g, acc[9]);
@@ -467,7 +494,7 @@ RenderGeo make_geo(const gs_grid* grid, const gs_config* cfg) {
 gs_status render_fwd_impl(const gs_bins* bins, const gs_grid* grid, const gs_config* cfg,
                           float* I, float* W, unsigned long long* stats, cudaStream_t st) {
     RenderGeo G = make_geo(grid, cfg);
-    const int threads = 32 * G.fx * G.fy * G.fz;
+    const int threads = 32 * ((G.fx * G.fy * G.fz + 1) / 2);  // a half-warp per footprint
     const float4* rec4 = reinterpret_cast<const float4*>(bins->rec);
     if (stats)
         k_render_fwd<true><<<bins->n_bricks, threads, 0, st>>>(bins->brick_off, bins->pair_gid, rec4,
