@@ -291,6 +291,79 @@ def downsample_adjoint(dlr, nz: int, s: int) -> np.ndarray:
     return out
 
 
+def resample_map(n_src: int, n_dst: int):
+    """One axis of the trilinear resize that makes the LR inputs (Sec. 4.1: volumes are
+    "downsampled via trilinear interpolation"; the sampling convention is not given).
+
+    Reading: half-pixel centres, i.e. destination sample j sits at the source continuous
+    index c_j = (n_src / n_dst)(j + 1/2) - 1/2, raised to 0 where it is negative; it reads
+    source samples i0 = floor(c_j) and i1 = min(i0 + 1, n_src - 1) with weights 1 - w and
+    w = c_j - i0. The position c_j decides the integers i0, so it is taken in FP32, one
+    rounding per operation, as the CUDA kernels take it; the weights are then FP64.
+    Returns (i0, i1, w) arrays of length n_dst.
+    """
+    scale = np.float32(n_src) / np.float32(n_dst)
+    j = np.arange(n_dst, dtype=np.float32)
+    c = scale * (j + np.float32(0.5)) - np.float32(0.5)
+    c = np.maximum(c, np.float32(0.0))
+    i0 = np.floor(c).astype(np.int64)
+    i1 = np.minimum(i0 + 1, n_src - 1)
+    w = c.astype(np.float64) - i0
+    return i0, i1, w
+
+
+def resample(vol, out_shape) -> np.ndarray:
+    """Trilinear resize of a [z, y, x] volume to ``out_shape``: every output voxel is the sum
+    over the 8 corners of its source cell of w_z w_y w_x times the corner value
+    (``resample_map`` along each axis)."""
+    vol = np.asarray(vol, np.float64)
+    maps = [resample_map(vol.shape[a], out_shape[a]) for a in range(3)]
+    out = np.zeros(tuple(out_shape), np.float64)
+    for cz in (0, 1):
+        for cy in (0, 1):
+            for cx in (0, 1):
+                iz = maps[0][1] if cz else maps[0][0]
+                iy = maps[1][1] if cy else maps[1][0]
+                ix = maps[2][1] if cx else maps[2][0]
+                wz = maps[0][2] if cz else 1.0 - maps[0][2]
+                wy = maps[1][2] if cy else 1.0 - maps[1][2]
+                wx = maps[2][2] if cx else 1.0 - maps[2][2]
+                w = wz[:, None, None] * wy[None, :, None] * wx[None, None, :]
+                out += w * vol[np.ix_(iz, iy, ix)]
+    return out
+
+
+def resample_adjoint(dout, in_shape) -> np.ndarray:
+    """Adjoint (transpose) of ``resample``: each output voxel's value is added back to its 8
+    source corners with the same weights."""
+    dout = np.asarray(dout, np.float64)
+    maps = [resample_map(in_shape[a], dout.shape[a]) for a in range(3)]
+    din = np.zeros(tuple(in_shape), np.float64)
+    for cz in (0, 1):
+        for cy in (0, 1):
+            for cx in (0, 1):
+                iz = maps[0][1] if cz else maps[0][0]
+                iy = maps[1][1] if cy else maps[1][0]
+                ix = maps[2][1] if cx else maps[2][0]
+                wz = maps[0][2] if cz else 1.0 - maps[0][2]
+                wy = maps[1][2] if cy else 1.0 - maps[1][2]
+                wx = maps[2][2] if cx else 1.0 - maps[2][2]
+                w = wz[:, None, None] * wy[None, :, None] * wx[None, None, :]
+                Z, Y, X = np.meshgrid(iz, iy, ix, indexing="ij")
+                np.add.at(din, (Z, Y, X), w * dout)
+    return din
+
+
+def resample_grid(grid_hr: Grid, lr_shape) -> Grid:
+    """The LR grid of a trilinear resize: same field of view and origin as the HR grid,
+    spacing L_a / n_a (destination sample j of ``resample_map`` is the centre of LR voxel j)."""
+    nz, ny, nx = lr_shape
+    n_hr = (grid_hr.nx, grid_hr.ny, grid_hr.nz)
+    n_lr = (nx, ny, nz)
+    h = tuple(grid_hr.h[a] * n_hr[a] / n_lr[a] for a in range(3))
+    return Grid(nx, ny, nz, h, grid_hr.origin)
+
+
 def l1_loss(pred, target):
     """Mean absolute error and its gradient sign(pred - target) / n (sign(0) = 0)."""
     pred = np.asarray(pred, dtype=np.float64)
@@ -381,13 +454,28 @@ def init_lattice(lr_vol, grid_hr: Grid, s: int, n_target: int, t_act: int = 1,
     s_a = l_a / 2 (l_a = L_a / n_a), identity rotation. The LR grid has spacing (h_x, h_y,
     s h_z) and the HR origin. Returns float32 ``[N, 12]`` raw parameters.
     """
+    grid_lr = Grid(grid_hr.nx, grid_hr.ny, grid_hr.nz // s,
+                   (grid_hr.h[0], grid_hr.h[1], grid_hr.h[2] * s), grid_hr.origin)
+    return init_lattice_on(lr_vol, grid_lr, grid_hr, n_target, t_act, t_init)
+
+
+def init_lattice_lr(lr_vol, grid_hr: Grid, n_target: int, t_act: int = 1,
+                    t_init: float = 0.5):
+    """``init_lattice`` for an LR volume made by the trilinear resize: the LR grid is
+    ``resample_grid(grid_hr, lr_vol.shape)``."""
+    grid_lr = resample_grid(grid_hr, np.asarray(lr_vol).shape)
+    return init_lattice_on(lr_vol, grid_lr, grid_hr, n_target, t_act, t_init)
+
+
+def init_lattice_on(lr_vol, grid_lr: Grid, grid_hr: Grid, n_target: int, t_act: int = 1,
+                    t_init: float = 0.5):
+    """The lattice of ``init_lattice`` over the HR field of view, amplitudes sampled from
+    ``lr_vol`` on ``grid_lr``."""
     n, L = lattice_dims(grid_hr, n_target)
     ell = [L[a] / n[a] for a in range(3)]
     xs = [grid_hr.origin[a] + (np.arange(n[a]) + 0.5) * ell[a] for a in range(3)]
     zz, yy, xx = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
     pts = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], axis=1)
-    grid_lr = Grid(grid_hr.nx, grid_hr.ny, grid_hr.nz // s,
-                   (grid_hr.h[0], grid_hr.h[1], grid_hr.h[2] * s), grid_hr.origin)
     A = trilinear(lr_vol, grid_lr, pts)
     N = pts.shape[0]
     out = np.zeros((N, 12), np.float64)
@@ -447,15 +535,23 @@ def ssim3d(x, ref, data_range: float = 1.0, sigma: float = 1.5) -> float:
 # ------------------------------------------------------------------- fitting step
 
 def fit_step(params, lr_target, grid: Grid, s: int, cfg: Config, m, v, step: int,
-             acfg: AdamConfig = AdamConfig()):
+             acfg: AdamConfig = AdamConfig(), lr_model: str = "zbox"):
     """One zero-shot fitting iteration, composed of the pinned pieces above: render
-    (Eq. 3-4), z box slice profile, L1 against the LR scan, adjoint slice profile, adjoint
-    render (Eq. 5-6 and the chain), Adam. Returns dict(loss, grad, params, m, v, I, lr_pred)."""
+    (Eq. 3-4), the LR forward model (``lr_model`` "zbox": z box slice profile of factor s;
+    "trilinear": trilinear resize to lr_target's shape), L1 against the LR scan, the forward
+    model's adjoint, adjoint render (Eq. 5-6 and the chain), Adam.
+    Returns dict(loss, grad, params, m, v, I, lr_pred)."""
     p = np.asarray(params, np.float64)
     r = render(p, grid, cfg)
-    lr_pred = downsample(r["I"], s)
+    if lr_model == "trilinear":
+        lr_pred = resample(r["I"], np.asarray(lr_target).shape)
+    else:
+        lr_pred = downsample(r["I"], s)
     loss, dlr = l1_loss(lr_pred, lr_target)
-    dI = downsample_adjoint(dlr, grid.nz, s)
+    if lr_model == "trilinear":
+        dI = resample_adjoint(dlr, r["I"].shape)
+    else:
+        dI = downsample_adjoint(dlr, grid.nz, s)
     grad = render_grad(p, grid, dI, cfg)
     p2, m2, v2 = adam_step(p, grad, m, v, step, acfg)
     return dict(loss=loss, grad=grad, params=p2, m=m2, v=v2, I=r["I"], lr_pred=lr_pred,

@@ -451,6 +451,75 @@ def test_downsample_adjoint_identity():
         assert np.all(adj[s * (nz // s):] == 0)
 
 
+# ------------------------------------------------------------- trilinear resize (Sec. 4.1)
+
+def test_resample_factor_two_is_block_mean():
+    """Halving every axis puts each LR sample at the centre of a 2 x 2 x 2 block with all
+    weights 1/2: the closed form is the block mean (catches a half-pixel shift or a wrong
+    scale direction)."""
+    import oracle
+    rng = np.random.default_rng(1)
+    v = rng.standard_normal((6, 8, 10))
+    got = oracle.resample(v, (3, 4, 5))
+    ref = v.reshape(3, 2, 4, 2, 5, 2).mean(axis=(1, 3, 5))
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-14)
+
+
+def test_resample_matches_map_coordinates():
+    """Any factor (down, up, mixed) equals scipy.ndimage.map_coordinates(order=1,
+    mode='nearest') at the half-pixel-centre positions c = (n_src/n_dst)(j + 1/2) - 1/2
+    (clamped at 0) computed in FP64 (the oracle takes them in FP32, hence the tolerance)."""
+    import oracle
+    from scipy.ndimage import map_coordinates
+    rng = np.random.default_rng(2)
+    for src, dst in (((24, 31, 20), (10, 13, 9)), ((155, 24, 24), (100, 10, 10)),
+                     ((7, 9, 5), (16, 9, 12))):
+        v = rng.standard_normal(src)
+        got = oracle.resample(v, dst)
+        pos = []
+        for a in range(3):
+            c = (src[a] / dst[a]) * (np.arange(dst[a]) + 0.5) - 0.5
+            pos.append(np.maximum(c, 0.0))
+        Z, Y, X = np.meshgrid(*pos, indexing="ij")
+        ref = map_coordinates(v, [Z.ravel(), Y.ravel(), X.ravel()], order=1,
+                              mode="nearest").reshape(dst)
+        # FP32 positions are off by at most a few ulp of c; the value moves by at most the
+        # largest neighbour difference per unit of c along each of the three axes
+        slope = max(float(np.abs(np.diff(v, axis=a)).max()) for a in range(3))
+        tol = 3 * 4 * 2.0 ** -23 * max(src) * slope
+        np.testing.assert_allclose(got, ref, rtol=0, atol=tol)
+
+
+def test_resample_identity_and_adjoint():
+    """Equal shapes copy exactly; <R x, y> = <x, R^T y> for the resize and its adjoint
+    (catches a transposed weight, a dropped corner or a wrong clamp in the adjoint)."""
+    import oracle
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal((5, 6, 7))
+    np.testing.assert_array_equal(oracle.resample(v, v.shape), v)
+    for src, dst in (((9, 13, 17), (4, 6, 7)), ((20, 20, 20), (8, 11, 20)),
+                     ((5, 6, 4), (9, 13, 8))):
+        x = rng.standard_normal(src)
+        y = rng.standard_normal(dst)
+        lhs = float((oracle.resample(x, dst) * y).sum())
+        rhs = float((x * oracle.resample_adjoint(y, src)).sum())
+        assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+def test_resample_grid_centres():
+    """LR voxel j of ``resample_grid`` has its centre at the HR continuous index c_j of
+    ``resample_map`` (the LR grid covers the HR field of view)."""
+    import oracle
+    g = oracle.Grid(240, 240, 155, (0.9, 0.9, 1.2), (-5.0, 3.0, 1.0))
+    lg = oracle.resample_grid(g, (100, 100, 100))
+    for a, (n_hr, n_lr) in enumerate(((240, 100), (240, 100), (155, 100))):
+        j = np.arange(n_lr)
+        lr_centre = lg.origin[a] + (j + 0.5) * lg.h[a]
+        c = (n_hr / n_lr) * (j + 0.5) - 0.5
+        hr_point = g.origin[a] + (c + 0.5) * g.h[a]
+        np.testing.assert_allclose(lr_centre, hr_point, rtol=1e-13, atol=1e-12)
+
+
 def test_l1_loss_values():
     import oracle
     pred = np.array([0.5, 0.2, 0.3, 0.9])
