@@ -369,10 +369,14 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const int32_t* __re
                                                             int64_t capacity, int shift, int n_tiles,
                                                             int32_t* __restrict__ hist) {
     __shared__ int cnt[kRadix];
-    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) cnt[i] = 0;
-    __syncthreads();
     const int64_t P = valid_pairs(npairs, capacity);
     const int64_t base = int64_t(blockIdx.x) * kSortTile;
+    if (base >= P) {  // a tile past the last pair (the grid is sized by the capacity)
+        for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[int64_t(d) * n_tiles + blockIdx.x] = 0;
+        return;
+    }
+    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
     for (int i = threadIdx.x; i < kSortTile; i += blockDim.x) {
         int64_t idx = base + i;
         if (idx < P) atomicAdd(&cnt[(keys[idx] >> shift) & (kRadix - 1)], 1);
@@ -399,11 +403,12 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     constexpr int kPerWarp = kSortTile / kWarps;
     constexpr int kRounds = kPerWarp / 32;
     __shared__ int wcnt[kWarps][kRadix];
+    const int64_t P = valid_pairs(npairs, capacity);
+    if (int64_t(blockIdx.x) * kSortTile >= P) return;  // past the last pair: nothing to place
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int d = tid; d < kRadix; d += kSortThreads)
         for (int w = 0; w < kWarps; ++w) wcnt[w][d] = 0;
     __syncthreads();
-    const int64_t P = valid_pairs(npairs, capacity);
     const int64_t sub0 = int64_t(blockIdx.x) * kSortTile + int64_t(warp) * kPerWarp;
     const unsigned lt_mask = (1u << lane) - 1u;
     int kr[kRounds], vr[kRounds];
