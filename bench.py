@@ -41,6 +41,9 @@ if ROOT not in sys.path:
 SHAPE = (128, 256, 256)       # (nz, ny, nx)
 S_FACTOR = 4
 N_GAUSS = 500_000
+# arbitrary-shape fit (trilinear LR model): HR 240 x 240 x 155 from a 100^3 LR scan
+SHAPE_TRI = (155, 240, 240)
+LR_TRI = (100, 100, 100)
 FIT_ITERS = 2000
 L2_FLUSH_BYTES = 256 << 20
 SM_COUNT_NOMINAL = 152
@@ -61,8 +64,13 @@ def parse_args():
     ap.add_argument("--fast", action="store_true", help="non-deterministic (atomic) reduction")
     ap.add_argument("--no-graph", action="store_true",
                     help="time eager gs_fit_step calls instead of CUDA-graph replays")
-    ap.add_argument("--workload", choices=["fit", "stress", "serve"], default="fit",
-                    help="fit: the fitting step (default); stress: forward + adjoint render of "
+    ap.add_argument("--workload", choices=["fit", "shape", "fullfit", "stress", "serve"],
+                    default="fit",
+                    help="fit: the fitting step (default); shape: the fitting step of an "
+                         "arbitrary-shape super-resolution (240 x 240 x 155 from 100^3, "
+                         "trilinear LR model); fullfit: complete 2,000-step fits of a "
+                         "256 x 256 x 160 phantom with 1M Gaussians at z factors 2 and 4, with "
+                         "PSNR / SSIM against the clean phantom; stress: forward + adjoint render of "
                          "4M clustered anisotropic Gaussians on 512 x 512 x 256, deterministic "
                          "reduction on and off; serve: a stream of fitting and re-rendering "
                          "requests through the serving runtime")
@@ -292,6 +300,15 @@ def run_reference(args, world, rank):
 
 
 def config_dict(args):
+    if getattr(args, "workload", "fit") == "shape":
+        nz, ny, nx = SHAPE_TRI
+        lz, ly, lx = LR_TRI
+        return {"workload": f"zero-shot fit step {nx}x{ny}x{nz} HR from a {lx}x{ly}x{lz} LR scan "
+                            f"(trilinear LR model), {N_GAUSS} Gaussians, L1, Adam",
+                "grid": [nx, ny, nz], "lr_grid": [lx, ly, lz], "n_gauss": N_GAUSS,
+                "brick": [8, 8, 8], "deterministic": 0 if args.fast else 1,
+                "launch": "eager" if args.no_graph else "cuda graph replay of gs_fit_step",
+                "l2": "flushed between timed steps (256 MB write)"}
     nz, ny, nx = SHAPE
     return {"workload": f"zero-shot fit step {nx}x{ny}x{nz} HR, {N_GAUSS} Gaussians, "
                         f"z box x{S_FACTOR}, L1, Adam",
@@ -310,9 +327,15 @@ def run_ours(args, world, rank, local):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     cfg = gs.Config(t_act=1, deterministic=0 if args.fast else 1)
-    w = workloads.phantom_fit(shape=SHAPE, s=S_FACTOR, n_gauss=N_GAUSS, seed=rank)
+    tri = args.workload == "shape"
+    if tri:
+        w = workloads.phantom_fit_trilinear(shape=SHAPE_TRI, lr_shape=LR_TRI, n_gauss=N_GAUSS,
+                                            seed=rank)
+        st = gs.FitState(w["params0"], w["lr"], w["grid"], 1, cfg, lr_model=gs.GS_LR_TRILINEAR)
+    else:
+        w = workloads.phantom_fit(shape=SHAPE, s=S_FACTOR, n_gauss=N_GAUSS, seed=rank)
+        st = gs.FitState(w["params0"], w["lr"], w["grid"], S_FACTOR, cfg)
     g = w["grid"]
-    st = gs.FitState(w["params0"], w["lr"], g, S_FACTOR, cfg)
     stream = torch.cuda.current_stream()
     events = [torch.cuda.Event(enable_timing=True) for _ in range(gs.GS_FIT_PHASES)]
     for e in events:
@@ -435,7 +458,7 @@ def run_ours(args, world, rank, local):
 
     if rank != 0:
         return
-    nz, ny, nx = SHAPE
+    nz, ny, nx = SHAPE_TRI if tri else SHAPE
     line = {"metric": "gaussian_voxel_pair_evals_per_s", "value": value,
             "unit": "pair-evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -448,7 +471,7 @@ def run_ours(args, world, rank, local):
                       "culling": n_eff / max(n_eval, 1)},
             "phase_ms": per_phase, "wall_s": wall,
             "roofline": roofline, "clocks": clk, "e2e": e2e, "gpu_launches": launches}
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and not tri:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line), flush=True)
 
@@ -508,6 +531,93 @@ def run_stress(args, world, rank, local):
         print(json.dumps({"workload": "stress 512x512x256, 4M clustered anisotropic Gaussians, "
                                       "bin + forward + adjoint render", "steps": args.steps,
                           "warmup": args.warmup, "results": out}), flush=True)
+
+
+# ------------------------------------------------------------------------- quality metrics
+def psnr_t(x, ref, data_range: float = 1.0) -> float:
+    """PSNR over the whole volume (data range 1: Sec. 4.1 normalises volumes to [0, 1])."""
+    import math
+    mse = float(((x.double() - ref.double()) ** 2).mean())
+    return float("inf") if mse == 0 else 10.0 * math.log10(data_range ** 2 / mse)
+
+
+def _blur_sym(v, sigma: float = 1.5, truncate: float = 3.5):
+    """Separable Gaussian blur of a [z, y, x] tensor with symmetric (edge-repeating)
+    padding, the window of scipy.ndimage.gaussian_filter(mode='reflect')."""
+    import torch
+    r = int(truncate * sigma + 0.5)
+    t = torch.arange(-r, r + 1, dtype=torch.float64, device=v.device)
+    k = torch.exp(-0.5 * (t / sigma) ** 2)
+    k = k / k.sum()
+    out = v.double()
+    for axis in range(3):
+        n = out.shape[axis]
+        idx = torch.arange(-r, n + r, device=v.device)
+        idx = torch.where(idx < 0, -idx - 1, idx)
+        idx = torch.where(idx >= n, 2 * n - 1 - idx, idx)
+        padded = out.index_select(axis, idx)
+        moved = padded.movedim(axis, -1)
+        shp = moved.shape
+        flat = moved.reshape(-1, 1, shp[-1])
+        conv = torch.nn.functional.conv1d(flat, k.view(1, 1, -1))
+        out = conv.reshape(shp[:-1] + (n,)).movedim(-1, axis)
+    return out
+
+
+def ssim3d_t(x, ref, data_range: float = 1.0, sigma: float = 1.5) -> float:
+    """Mean 3D SSIM (Wang et al. 2004, cited in Sec. 4.2) with a Gaussian window of std sigma
+    voxels, K1 = 0.01, K2 = 0.03."""
+    c1 = (0.01 * data_range) ** 2
+    c2 = (0.03 * data_range) ** 2
+    x = x.double()
+    y = ref.double()
+    mx, my = _blur_sym(x, sigma), _blur_sym(y, sigma)
+    sxx = _blur_sym(x * x, sigma) - mx * mx
+    syy = _blur_sym(y * y, sigma) - my * my
+    sxy = _blur_sym(x * y, sigma) - mx * my
+    num = (2 * mx * my + c1) * (2 * sxy + c2)
+    den = (mx * mx + my * my + c1) * (sxx + syy + c2)
+    return float((num / den).mean())
+
+
+def run_fullfit(args, world, rank, local):
+    """Complete zero-shot fits (not the headline line): 256 x 256 x 160 phantom, LR by the z
+    box profile at factors 2 and 4, 1M lattice Gaussians, 2,000 Adam steps through the serving
+    runtime (graph-captured chunks of 50 steps; bins grow when the cloud needs it); seconds per
+    scan (admission to completion), and PSNR / SSIM of the fitted render and of the trilinear
+    upsampling of the LR scan against the clean HR phantom."""
+    import torch
+    from paper_2603_09621_gb300 import build as gbuild
+    gbuild.build()
+    from paper_2603_09621_gb300 import gs, serve, workloads
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    shape, n_gauss, iters = (160, 256, 256), 1_000_000, FIT_ITERS
+    cfg = gs.Config(t_act=1, deterministic=0 if args.fast else 1)
+    out = {}
+    for s_fac in (2, 4):
+        w = workloads.phantom_fit(shape=shape, s=s_fac, n_gauss=n_gauss, seed=rank)
+        with serve.Server(16 << 30, max_active=1, chunk_steps=50, cfg=cfg) as sv:
+            rid = sv.submit_fit(w["params0"], w["lr"], w["grid"], s_fac, iters)
+            sv.run(timeout_s=1200)
+            r = sv.result(rid)
+            fitted = sv.output(rid)
+        I = gs.render(fitted, w["grid"], gs.Config(t_act=1))[0]
+        up = gs.gs_resample_fwd(w["lr"], shape)
+        torch.cuda.synchronize()
+        out[f"s{s_fac}"] = {
+            "fit_s_per_scan": r["done_s"] - r["admit_s"], "steps": r["steps_done"],
+            "state": r["state"], "bin_grows": r["grows"], "final_loss": r["loss"],
+            "psnr": psnr_t(I, w["hr"]), "ssim": ssim3d_t(I, w["hr"]),
+            "psnr_trilinear_upsampling": psnr_t(up, w["hr"]),
+            "ssim_trilinear_upsampling": ssim3d_t(up, w["hr"])}
+        del w, I, up, fitted
+        torch.cuda.empty_cache()
+    if rank == 0:
+        nz, ny, nx = shape
+        print(json.dumps({"workload": f"full zero-shot fits: {nx}x{ny}x{nz} phantom, z box LR, "
+                                      f"{n_gauss} Gaussians, {iters} steps, deterministic",
+                          "results": out}), flush=True)
 
 
 def run_serve(args, world, rank, local):
@@ -585,6 +695,8 @@ def main():
         run_stress(args, world, rank, local)
     elif args.workload == "serve":
         run_serve(args, world, rank, local)
+    elif args.workload == "fullfit":
+        run_fullfit(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

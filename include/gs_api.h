@@ -177,6 +177,22 @@ gs_status gs_downsample_fwd(const float* hr, int32_t nz, int32_t ny, int32_t nx,
 gs_status gs_downsample_bwd(const float* dlr, int32_t nz, int32_t ny, int32_t nx, int32_t s,
                             float* dhr, gs_stream stream);
 
+/* Trilinear resize with half-pixel centres (Sec. 4.1 makes the LR inputs by trilinear
+ * downsampling; the convention is this library's reading): along each axis, destination
+ * sample j reads the source at continuous index c_j = (n_src / n_dst)(j + 1/2) - 1/2 (raised
+ * to 0 where negative), i.e. samples floor(c_j) and min(floor(c_j) + 1, n_src - 1) with
+ * linear weights; c_j is formed in FP32, one rounding per operation. Any sizes (down- or
+ * upsampling, per axis). src: device [snz, sny, snx]; dst: device [dnz, dny, dnx].
+ * Every size must be in [1, 2^23). */
+gs_status gs_resample_fwd(const float* src, int32_t snz, int32_t sny, int32_t snx, float* dst,
+                          int32_t dnz, int32_t dny, int32_t dnx, gs_stream stream);
+
+/* Adjoint (transpose) of gs_resample_fwd: dsrc [snz, sny, snx] = R^T ddst [dnz, dny, dnx],
+ * each source voxel gathering the destination samples that read it in a fixed order
+ * (deterministic, no atomics). dsrc is overwritten. */
+gs_status gs_resample_bwd(const float* ddst, int32_t dnz, int32_t dny, int32_t dnx, float* dsrc,
+                          int32_t snz, int32_t sny, int32_t snx, gs_stream stream);
+
 /* Mean absolute error over n values, reduced in a fixed order (deterministic).
  * pred, target: device float [n]; d_loss: device float scalar; dpred: device float [n] or
  * NULL, receives sign(pred - target) / n (sign(0) = 0). ws: workspace. */
@@ -209,6 +225,12 @@ gs_status gs_l1_loss_static(const float* pred, const float* target, int64_t n, f
 gs_status gs_adam_step(float* params, const float* grad, float* m, float* v, int64_t n_gauss,
                        const gs_adam* hp, int32_t* d_step, gs_stream stream);
 
+/* gs_init_lattice for an LR volume made by gs_resample_fwd from the HR grid: lr is device
+ * [lnz, lny, lnx] on the grid with the HR origin and field of view, spacing L_a / ln_a. */
+gs_status gs_init_lattice_lr(const float* lr, int32_t lnz, int32_t lny, int32_t lnx,
+                             const gs_grid* hr_grid, int32_t nlx, int32_t nly, int32_t nlz,
+                             int32_t t_act, float t_init, float* params, gs_stream stream);
+
 /* Initial cloud from the LR volume (Fig. 1 caption: Gaussians are initialised from the
  * coordinates of the LR volume; details are this library's reading): an axis lattice of
  * nl = (nlx, nly, nlz) points with centres origin + (i + 1/2) L / nl, amplitude = trilinear
@@ -219,11 +241,17 @@ gs_status gs_init_lattice(const float* lr, const gs_grid* hr_grid, int32_t s, in
                           int32_t nly, int32_t nlz, int32_t t_act, float t_init, float* params,
                           gs_stream stream);
 
+/* LR forward models of the fitting step: the z box slice profile of factor s
+ * (gs_downsample_fwd), or the trilinear resize to (lr_nz, lr_ny, lr_nx) (gs_resample_fwd). */
+#define GS_LR_ZBOX 0
+#define GS_LR_TRILINEAR 1
+
 /* One zero-shot fitting iteration (all device work, no host synchronisation; the step can
- * be captured in a CUDA graph): bin, forward render, z box slice profile, L1 loss against
- * lr_target, its adjoint, adjoint render, Adam. Every pointer is device memory:
- *   params, grad, m, v [n_gauss, 12]; I, W [nz, ny, nx]; lr_pred [nz / s, ny, nx] (after the
- *   step it holds dL/dLR); lr_target [nz / s, ny, nx]; d_loss float scalar (the loss of this
+ * be captured in a CUDA graph): bin, forward render, LR forward model (lr_model), L1 loss
+ * against lr_target, its adjoint, adjoint render, Adam. Every pointer is device memory:
+ *   params, grad, m, v [n_gauss, 12]; I, W [nz, ny, nx]; lr_pred and lr_target of the LR
+ *   shape: [nz / s, ny, nx] for GS_LR_ZBOX, [lr_nz, lr_ny, lr_nx] for GS_LR_TRILINEAR (after
+ *   the step lr_pred holds dL/dLR); d_loss float scalar (the loss of this
  *   step's forward pass); d_step int32 (Adam step counter); bins bound for n_gauss; ws
  *   workspace. On return grad holds dL/d(params) of this step.
  *   If this step's binning overflows the bins' capacity, the step is a no-op: params, m, v
@@ -257,6 +285,8 @@ typedef struct {
     size_t ws_bytes;
     void* const* phase_events;
     int32_t n_phase_events;
+    int32_t lr_model;                 /* GS_LR_ZBOX (uses s) or GS_LR_TRILINEAR */
+    int32_t lr_nx, lr_ny, lr_nz;      /* LR shape of GS_LR_TRILINEAR, each in [1, 2^23) */
 } gs_fit_state;
 
 gs_status gs_fit_step(gs_fit_state* st, gs_stream stream);

@@ -106,12 +106,15 @@ typedef struct {
  * GS_REQ_PENDING (they are copied into the arena at admission).
  *   kind: GS_REQ_FIT or GS_REQ_RENDER.
  *   grid: fit: the HR grid the cloud is rendered on; render: the output grid.
- *   s: fit: slice factor; lr_target has grid.nz / s slices.
+ *   lr_model: fit: GS_LR_ZBOX (slice factor s; lr_target has grid.nz / s slices) or
+ *           GS_LR_TRILINEAR (lr_target is [lr_nz, lr_ny, lr_nx], the trilinear resize of the
+ *           HR grid's field of view).
+ *   s: fit with GS_LR_ZBOX: slice factor.
  *   iters: fit: number of fitting steps (>= 1).
  *   n_gauss: Gaussians in the cloud (>= 1); for a render of a fit's result, that fit's count.
  *   params: device float [n_gauss, 12]: fit: the initial cloud; render: the cloud to render
  *           (unused when source >= 0).
- *   lr_target: fit: device float [grid.nz / s, ny, nx].
+ *   lr_target: fit: device float of the LR shape.
  *   source: render: id of a fit request of this server whose fitted cloud is rendered (the
  *           render waits for it), or -1.
  *   arrival_s: the request is not admitted before this server-clock time. */
@@ -125,6 +128,8 @@ typedef struct {
     const float* lr_target;
     int64_t source;
     double arrival_s;
+    int32_t lr_model;
+    int32_t lr_nx, lr_ny, lr_nz;
 } gs_request;
 
 /* State of one request.

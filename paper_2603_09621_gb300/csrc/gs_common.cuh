@@ -180,6 +180,11 @@ gs_status launch_param_bwd(const float* params, const float* gacc, int64_t n,
                            cudaStream_t stream);
 
 // L1 loss with optional sign gradient into dpred (gs_volume.cu).
+gs_status resample_fwd_impl(const float* src, int32_t snz, int32_t sny, int32_t snx, float* dst,
+                            int32_t dnz, int32_t dny, int32_t dnx, cudaStream_t st);
+gs_status resample_adj_prep_impl(const float* dlr, int32_t lnz, int32_t lny, int32_t lnx,
+                                 const float* I, const float* W, int32_t nz, int32_t ny, int32_t nx,
+                                 float eps, float2* aip, cudaStream_t st);
 gs_status launch_l1(const float* pred, const float* target, int64_t n, float* d_loss,
                     float* dpred, float* partials, cudaStream_t stream);
 

@@ -410,6 +410,35 @@ extern "C" gs_status gs_adam_step(float* params, const float* grad, float* m, fl
     return last_launch_status();
 }
 
+extern "C" gs_status gs_init_lattice_lr(const float* lr, int32_t lnz, int32_t lny, int32_t lnx,
+                                        const gs_grid* g, int32_t nlx, int32_t nly, int32_t nlz,
+                                        int32_t t_act, float t_init, float* params,
+                                        gs_stream stream) {
+    if (!lr || !g || !params || nlx <= 0 || nly <= 0 || nlz <= 0) return GS_ERR_INVALID_ARG;
+    if (lnx <= 0 || lny <= 0 || lnz <= 0 || g->nx <= 0 || g->ny <= 0 || g->nz <= 0)
+        return GS_ERR_INVALID_ARG;
+    if (t_act && !(t_init > 0.0f && t_init < 1.0f)) return GS_ERR_INVALID_ARG;
+    InitGeo G;
+    G.nx = lnx;
+    G.ny = lny;
+    G.nzl = lnz;
+    const int n[3] = {g->nx, g->ny, g->nz};
+    const int ln[3] = {lnx, lny, lnz};
+    const int nl[3] = {nlx, nly, nlz};
+    for (int a = 0; a < 3; ++a) {
+        G.o[a] = g->origin[a];
+        G.ext[a] = double(n[a]) * double(g->h[a]);
+        G.hl[a] = G.ext[a] / double(ln[a]);
+        G.nl[a] = nl[a];
+        G.log_s[a] = static_cast<float>(log(0.5 * G.ext[a] / double(nl[a])));
+    }
+    G.t_raw = t_act ? static_cast<float>(log(double(t_init) / (1.0 - double(t_init)))) : t_init;
+    const int64_t N = int64_t(nlx) * nly * nlz;
+    k_init_lattice<<<static_cast<unsigned>((N + 255) / 256), 256, 0,
+                     reinterpret_cast<cudaStream_t>(stream)>>>(lr, G, params);
+    return last_launch_status();
+}
+
 extern "C" gs_status gs_init_lattice(const float* lr, const gs_grid* g, int32_t s, int32_t nlx,
                                      int32_t nly, int32_t nlz, int32_t t_act, float t_init,
                                      float* params, gs_stream stream) {

@@ -1,0 +1,309 @@
+// gs_resample.cu -- trilinear resize with half-pixel centres (Sec. 4.1 makes the LR inputs
+// by trilinear downsampling), its adjoint as a deterministic gather, and the adjoint fused
+// with the adjoint render's per-voxel factors for the fitting step.
+//
+// Along one axis, destination sample j sits at the source continuous index
+// c_j = (n_src / n_dst)(j + 1/2) - 1/2 (raised to 0 where negative) and reads source samples
+// i0 = floor(c_j), i1 = min(i0 + 1, n_src - 1) with weights 1 - w, w = c_j - i0. c_j is
+// formed with one rounding per FP32 operation (no contraction), so every kernel, and the
+// oracle, take the same integer decisions.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gs_common.cuh"
+
+namespace gs {
+
+struct ResAxis {
+    float scale;  // n_src / n_dst, FP32 division
+    float inv;    // n_dst / n_src (only bounds the adjoint's search range)
+    int n_src, n_dst;
+};
+
+struct ResGeo {
+    ResAxis a[3];  // x, y, z
+};
+
+__device__ __forceinline__ void res_map(const ResAxis& A, int j, int& i0, int& i1, float& w) {
+    float c = __fsub_rn(__fmul_rn(A.scale, __fadd_rn(float(j), 0.5f)), 0.5f);
+    c = fmaxf(c, 0.0f);
+    const float f = floorf(c);
+    i0 = static_cast<int>(f);
+    i1 = min(i0 + 1, A.n_src - 1);
+    w = __fsub_rn(c, f);  // exact: 0 <= c - f < 1
+}
+
+// Weight with which destination sample j reads source sample i (both corners may coincide
+// at the upper edge).
+__device__ __forceinline__ float res_weight(const ResAxis& A, int j, int i) {
+    int i0, i1;
+    float w;
+    res_map(A, j, i0, i1, w);
+    return (i0 == i ? 1.0f - w : 0.0f) + (i1 == i ? w : 0.0f);
+}
+
+// Destination samples that may read source sample i: c_j in [i - 1, i + 1), widened by one.
+__device__ __forceinline__ void res_range(const ResAxis& A, int i, int& jlo, int& jhi) {
+    jlo = max(0, static_cast<int>(floorf((float(i) - 0.5f) * A.inv - 0.5f)) - 1);
+    jhi = min(A.n_dst - 1, static_cast<int>(ceilf((float(i) + 1.5f) * A.inv - 0.5f)) + 1);
+}
+
+__global__ void __launch_bounds__(256) k_resample_fwd(const float* __restrict__ src, ResGeo G,
+                                                      float* __restrict__ dst) {
+    const ResAxis &AX = G.a[0], &AY = G.a[1], &AZ = G.a[2];
+    const int64_t n = int64_t(AX.n_dst) * AY.n_dst * AZ.n_dst;
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n;
+         t += int64_t(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(t % AX.n_dst);
+        const int y = static_cast<int>((t / AX.n_dst) % AY.n_dst);
+        const int z = static_cast<int>(t / (int64_t(AX.n_dst) * AY.n_dst));
+        int x0, x1, y0, y1, z0, z1;
+        float wx, wy, wz;
+        res_map(AX, x, x0, x1, wx);
+        res_map(AY, y, y0, y1, wy);
+        res_map(AZ, z, z0, z1, wz);
+        const int64_t sx = AX.n_src, sxy = int64_t(AX.n_src) * AY.n_src;
+        const float* p00 = src + z0 * sxy + y0 * sx;
+        const float* p01 = src + z0 * sxy + y1 * sx;
+        const float* p10 = src + z1 * sxy + y0 * sx;
+        const float* p11 = src + z1 * sxy + y1 * sx;
+        const float ux = 1.0f - wx, uy = 1.0f - wy, uz = 1.0f - wz;
+        const float r00 = fmaf(wx, p00[x1], ux * p00[x0]);
+        const float r01 = fmaf(wx, p01[x1], ux * p01[x0]);
+        const float r10 = fmaf(wx, p10[x1], ux * p10[x0]);
+        const float r11 = fmaf(wx, p11[x1], ux * p11[x0]);
+        const float s0 = fmaf(wy, r01, uy * r00);
+        const float s1 = fmaf(wy, r11, uy * r10);
+        dst[t] = fmaf(wz, s1, uz * s0);
+    }
+}
+
+// The destination samples that read source sample i form one run j0, j0 + 1, ... (i0(j) is
+// non-decreasing in j). kResList slots cover it whenever n_dst / n_src <= 3/2 (c_j steps by
+// n_src / n_dst >= 2/3, so at most four c_j fall in [i - 1, i + 1)). Slot k holds the weight
+// of j0 + k (0 past the run); *n is the run length.
+constexpr int kResList = 4;
+__device__ __forceinline__ void res_list(const ResAxis& A, int i, int& j0, int& n,
+                                         float (&w)[kResList]) {
+    int lo, hi;
+    res_range(A, i, lo, hi);
+    int t = lo;
+    for (; t < hi; ++t) {  // skip samples whose upper corner is still below i
+        int a, b;
+        float ww;
+        res_map(A, t, a, b, ww);
+        if (b >= i) break;
+    }
+    j0 = t;
+    n = 0;
+#pragma unroll
+    for (int k = 0; k < kResList; ++k) {
+        const int j = t + k;
+        w[k] = (j < A.n_dst) ? res_weight(A, j, i) : 0.0f;
+        n = (w[k] != 0.0f) ? k + 1 : n;
+    }
+}
+
+__host__ __device__ __forceinline__ bool res_list_ok(const ResGeo& G) {
+    return G.a[0].inv <= 1.5f && G.a[1].inv <= 1.5f && G.a[2].inv <= 1.5f;
+}
+
+// Adjoint value at source voxel (x, y, z): sum over the destination samples that read it, in
+// ascending (z, y, x) order (any ratio).
+__device__ __forceinline__ float res_gather(const float* __restrict__ ddst, const ResGeo& G, int x,
+                                            int y, int z) {
+    const ResAxis &AX = G.a[0], &AY = G.a[1], &AZ = G.a[2];
+    int xlo, xhi, ylo, yhi, zlo, zhi;
+    res_range(AX, x, xlo, xhi);
+    res_range(AY, y, ylo, yhi);
+    res_range(AZ, z, zlo, zhi);
+    float acc = 0.0f;
+    for (int jz = zlo; jz <= zhi; ++jz) {
+        const float wz = res_weight(AZ, jz, z);
+        if (wz == 0.0f) continue;
+        for (int jy = ylo; jy <= yhi; ++jy) {
+            const float wy = res_weight(AY, jy, y);
+            if (wy == 0.0f) continue;
+            const float wzy = wz * wy;
+            const float* row = ddst + (int64_t(jz) * AY.n_dst + jy) * AX.n_dst;
+            for (int jx = xlo; jx <= xhi; ++jx) {
+                const float wx = res_weight(AX, jx, x);
+                if (wx != 0.0f) acc = fmaf(wzy * wx, row[jx], acc);
+            }
+        }
+    }
+    return acc;
+}
+
+__global__ void __launch_bounds__(256) k_resample_bwd(const float* __restrict__ ddst, ResGeo G,
+                                                      float* __restrict__ dsrc) {
+    const ResAxis &AX = G.a[0], &AY = G.a[1], &AZ = G.a[2];
+    const int64_t n = int64_t(AX.n_src) * AY.n_src * AZ.n_src;
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n;
+         t += int64_t(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(t % AX.n_src);
+        const int y = static_cast<int>((t / AX.n_src) % AY.n_src);
+        const int z = static_cast<int>(t / (int64_t(AX.n_src) * AY.n_src));
+        dsrc[t] = res_gather(ddst, G, x, y, z);
+    }
+}
+
+// Row-chunk form of the list gather (n_dst / n_src <= 3/2 on every axis and at most kResTab
+// source columns): a block first tabulates the x runs of all source columns in shared
+// memory; a thread then takes kResChunk consecutive voxels of one row, builds its y and z
+// runs once and gathers each voxel in ascending (z, y, x) order.
+constexpr int kResTab = 1024;
+constexpr int kResChunk = 8;
+
+struct ResRun {
+    int j0, n;
+    float w[kResList];
+};
+
+template <bool kPrep>
+__global__ void __launch_bounds__(256, 3) k_resample_adj_rows(const float* __restrict__ ddst, ResGeo G,
+                                                           const float* __restrict__ Iv,
+                                                           const float* __restrict__ Wv, float eps,
+                                                           float* __restrict__ dsrc,
+                                                           float2* __restrict__ aip) {
+    __shared__ ResRun xt[kResTab];
+    const ResAxis &AX = G.a[0], &AY = G.a[1], &AZ = G.a[2];
+    for (int i = threadIdx.x; i < AX.n_src; i += blockDim.x) {
+        ResRun rr;
+        res_list(AX, i, rr.j0, rr.n, rr.w);
+        xt[i] = rr;
+    }
+    __syncthreads();
+    const int nxc = (AX.n_src + kResChunk - 1) / kResChunk;
+    const int64_t n = int64_t(nxc) * AY.n_src * AZ.n_src;
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n;
+         t += int64_t(gridDim.x) * blockDim.x) {
+        const int xc = static_cast<int>(t % nxc);
+        const int y = static_cast<int>((t / nxc) % AY.n_src);
+        const int z = static_cast<int>(t / (int64_t(nxc) * AY.n_src));
+        int jy, jz, ny, nz;
+        float wy[kResList], wz[kResList];
+        res_list(AY, y, jy, ny, wy);
+        res_list(AZ, z, jz, nz, wz);
+        const int64_t row0 = (int64_t(z) * AY.n_src + y) * AX.n_src;
+        const int x0 = xc * kResChunk;
+        const int x1 = min(x0 + kResChunk, AX.n_src);
+        for (int x = x0; x < x1; ++x) {
+            const ResRun& rx = xt[x];
+            float acc = 0.0f;
+#pragma unroll
+            for (int a = 0; a < kResList; ++a) {
+                if (a >= nz) break;
+#pragma unroll
+                for (int b = 0; b < kResList; ++b) {
+                    if (b >= ny) break;
+                    const float wzy = wz[a] * wy[b];
+                    const float* row =
+                        ddst + (int64_t(jz + a) * AY.n_dst + (jy + b)) * AX.n_dst + rx.j0;
+#pragma unroll
+                    for (int c = 0; c < kResList; ++c) {
+                        if (c >= rx.n) break;
+                        if (rx.w[c] != 0.0f) acc = fmaf(wzy * rx.w[c], row[c], acc);
+                    }
+                }
+            }
+            if (kPrep) {
+                const float w = Wv[row0 + x];
+                const float al = acc / (w > eps ? w : eps);
+                aip[row0 + x] = make_float2(al, (w > eps) ? al * Iv[row0 + x] : 0.0f);
+            } else {
+                dsrc[row0 + x] = acc;
+            }
+        }
+    }
+}
+
+// Fitting step, any ratio: dL/dI at each HR voxel is the resize adjoint of dL/dLR; stored
+// directly as the adjoint render's factors (alpha, alpha I'), alpha = dL/dI / max(W, eps),
+// I' = I where W > eps, else 0.
+__global__ void __launch_bounds__(256) k_resample_adj_prep(const float* __restrict__ dlr, ResGeo G,
+                                                           const float* __restrict__ Iv,
+                                                           const float* __restrict__ Wv, float eps,
+                                                           float2* __restrict__ aip) {
+    const ResAxis &AX = G.a[0], &AY = G.a[1], &AZ = G.a[2];
+    const int64_t n = int64_t(AX.n_src) * AY.n_src * AZ.n_src;
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n;
+         t += int64_t(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(t % AX.n_src);
+        const int y = static_cast<int>((t / AX.n_src) % AY.n_src);
+        const int z = static_cast<int>(t / (int64_t(AX.n_src) * AY.n_src));
+        const float gI = res_gather(dlr, G, x, y, z);
+        const float w = Wv[t];
+        const float al = gI / (w > eps ? w : eps);
+        aip[t] = make_float2(al, (w > eps) ? al * Iv[t] : 0.0f);
+    }
+}
+
+static bool dims_ok(int32_t nz, int32_t ny, int32_t nx) {
+    return nz > 0 && ny > 0 && nx > 0 && nx < (1 << 23) && ny < (1 << 23) && nz < (1 << 23);
+}
+
+static ResGeo make_res(int32_t snz, int32_t sny, int32_t snx, int32_t dnz, int32_t dny, int32_t dnx) {
+    ResGeo G;
+    const int32_t s[3] = {snx, sny, snz}, d[3] = {dnx, dny, dnz};
+    for (int a = 0; a < 3; ++a) {
+        G.a[a].n_src = s[a];
+        G.a[a].n_dst = d[a];
+        G.a[a].scale = float(s[a]) / float(d[a]);
+        G.a[a].inv = float(d[a]) / float(s[a]);
+    }
+    return G;
+}
+
+static unsigned res_blocks(int64_t n) {
+    const int64_t b = (n + 255) / 256;
+    return static_cast<unsigned>(b < 152 * 64 ? b : 152 * 64);
+}
+
+gs_status resample_fwd_impl(const float* src, int32_t snz, int32_t sny, int32_t snx, float* dst,
+                            int32_t dnz, int32_t dny, int32_t dnx, cudaStream_t st) {
+    const ResGeo G = make_res(snz, sny, snx, dnz, dny, dnx);
+    k_resample_fwd<<<res_blocks(int64_t(dnz) * dny * dnx), 256, 0, st>>>(src, G, dst);
+    return last_launch_status();
+}
+
+gs_status resample_adj_prep_impl(const float* dlr, int32_t lnz, int32_t lny, int32_t lnx,
+                                 const float* I, const float* W, int32_t nz, int32_t ny, int32_t nx,
+                                 float eps, float2* aip, cudaStream_t st) {
+    const ResGeo G = make_res(nz, ny, nx, lnz, lny, lnx);
+    if (res_list_ok(G) && nx <= kResTab) {
+        const int64_t rows = int64_t((nx + kResChunk - 1) / kResChunk) * ny * nz;
+        k_resample_adj_rows<true><<<res_blocks(rows), 256, 0, st>>>(dlr, G, I, W, eps, nullptr, aip);
+    } else {
+        k_resample_adj_prep<<<res_blocks(int64_t(nz) * ny * nx), 256, 0, st>>>(dlr, G, I, W, eps, aip);
+    }
+    return last_launch_status();
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" gs_status gs_resample_fwd(const float* src, int32_t snz, int32_t sny, int32_t snx,
+                                     float* dst, int32_t dnz, int32_t dny, int32_t dnx,
+                                     gs_stream stream) {
+    if (!src || !dst || !dims_ok(snz, sny, snx) || !dims_ok(dnz, dny, dnx)) return GS_ERR_INVALID_ARG;
+    return resample_fwd_impl(src, snz, sny, snx, dst, dnz, dny, dnx,
+                             reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" gs_status gs_resample_bwd(const float* ddst, int32_t dnz, int32_t dny, int32_t dnx,
+                                     float* dsrc, int32_t snz, int32_t sny, int32_t snx,
+                                     gs_stream stream) {
+    if (!ddst || !dsrc || !dims_ok(snz, sny, snx) || !dims_ok(dnz, dny, dnx)) return GS_ERR_INVALID_ARG;
+    const ResGeo G = make_res(snz, sny, snx, dnz, dny, dnx);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (res_list_ok(G) && snx <= kResTab) {
+        const int64_t rows = int64_t((snx + kResChunk - 1) / kResChunk) * sny * snz;
+        k_resample_adj_rows<false><<<res_blocks(rows), 256, 0, st>>>(ddst, G, nullptr, nullptr, 0.f,
+                                                                     dsrc, nullptr);
+    } else {
+        k_resample_bwd<<<res_blocks(int64_t(snz) * sny * snx), 256, 0, st>>>(ddst, G, dsrc);
+    }
+    return last_launch_status();
+}

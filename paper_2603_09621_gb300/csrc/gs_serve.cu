@@ -212,10 +212,20 @@ size_t bins_block_bytes(const gs_server_config& c, int64_t n, int64_t cap, const
 
 bool request_ok(const gs_request& r) {
     if (!grid_ok(r.grid) || r.n_gauss < 1 || !std::isfinite(r.arrival_s)) return false;
-    if (r.kind == GS_REQ_FIT)
-        return r.s >= 1 && r.grid.nz / r.s >= 1 && r.iters >= 1 && r.params && r.lr_target;
+    if (r.kind == GS_REQ_FIT) {
+        if (r.iters < 1 || !r.params || !r.lr_target) return false;
+        if (r.lr_model == GS_LR_TRILINEAR)
+            return r.lr_nx >= 1 && r.lr_ny >= 1 && r.lr_nz >= 1;
+        return r.lr_model == GS_LR_ZBOX && r.s >= 1 && r.grid.nz / r.s >= 1;
+    }
     if (r.kind == GS_REQ_RENDER) return r.source >= 0 || r.params;
     return false;
+}
+
+// Voxels of a fit request's LR scan.
+size_t lr_voxels(const gs_request& r) {
+    if (r.lr_model == GS_LR_TRILINEAR) return size_t(r.lr_nz) * r.lr_ny * r.lr_nx;
+    return size_t(r.grid.nz / r.s) * r.grid.ny * r.grid.nx;
 }
 
 // Block sizes of a request at capacity `cap`; false if the request is invalid.
@@ -226,7 +236,7 @@ bool sizes_of(const gs_server_config& c, const gs_request& r, int64_t cap, Sizes
     s->bins = bins_block_bytes(c, r.n_gauss, cap, r.grid);
     if (!s->bins) return false;
     if (r.kind == GS_REQ_FIT) {
-        const size_t lbytes = size_t(r.grid.nz / r.s) * r.grid.ny * r.grid.nx * sizeof(float);
+        const size_t lbytes = lr_voxels(r) * sizeof(float);
         s->persist = round_up(pbytes);
         s->state = 3 * round_up(pbytes) + 2 * round_up(vbytes) + 2 * round_up(lbytes) + 2 * kAlign;
     } else {
@@ -369,9 +379,13 @@ struct gs_server {
         Carver c(j.state_blk);
         bool ok = true;
         if (j.req.kind == GS_REQ_FIT) {
-            const size_t lbytes = size_t(g.nz / j.req.s) * g.ny * g.nx * sizeof(float);
+            const size_t lbytes = lr_voxels(j.req) * sizeof(float);
             gs_fit_state& f = j.fs;
             f = gs_fit_state{};
+            f.lr_model = j.req.lr_model;
+            f.lr_nx = j.req.lr_nx;
+            f.lr_ny = j.req.lr_ny;
+            f.lr_nz = j.req.lr_nz;
             f.grid = g;
             f.cfg = cfg.cfg;
             f.adam = cfg.adam;

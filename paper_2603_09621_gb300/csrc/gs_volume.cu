@@ -178,7 +178,17 @@ extern "C" gs_status gs_fit_step(gs_fit_state* st, gs_stream stream) {
     if (!st) return GS_ERR_INVALID_ARG;
     gs_status s = validate_grid_cfg(&st->grid, &st->cfg);
     if (s != GS_OK) return s;
-    if (st->n_gauss <= 0 || st->s <= 0 || st->grid.nz / st->s <= 0) return GS_ERR_INVALID_ARG;
+    if (st->n_gauss <= 0) return GS_ERR_INVALID_ARG;
+    const bool trilinear = st->lr_model == GS_LR_TRILINEAR;
+    if (trilinear) {
+        const int32_t lim = 1 << 23;
+        if (st->lr_nx <= 0 || st->lr_ny <= 0 || st->lr_nz <= 0 || st->lr_nx >= lim ||
+            st->lr_ny >= lim || st->lr_nz >= lim || st->grid.nx >= lim || st->grid.ny >= lim ||
+            st->grid.nz >= lim)
+            return GS_ERR_INVALID_ARG;
+    } else if (st->lr_model != GS_LR_ZBOX || st->s <= 0 || st->grid.nz / st->s <= 0) {
+        return GS_ERR_INVALID_ARG;
+    }
     if (!st->params || !st->grad || !st->m || !st->v || !st->d_step || !st->I || !st->W ||
         !st->lr_pred || !st->lr_target || !st->d_loss)
         return GS_ERR_INVALID_ARG;
@@ -209,13 +219,21 @@ extern "C" gs_status gs_fit_step(gs_fit_state* st, gs_stream stream) {
     s = render_fwd_impl(&st->bins, &g, &st->cfg, st->I, st->W, nullptr, cs);
     if (s != GS_OK) return s;
     if (!mark(2)) return GS_ERR_CUDA;
-    s = downsample_fwd_impl(st->I, g.nz, g.ny, g.nx, st->s, st->lr_pred, cs);
+    if (trilinear)
+        s = resample_fwd_impl(st->I, g.nz, g.ny, g.nx, st->lr_pred, st->lr_nz, st->lr_ny, st->lr_nx, cs);
+    else
+        s = downsample_fwd_impl(st->I, g.nz, g.ny, g.nx, st->s, st->lr_pred, cs);
     if (s != GS_OK) return s;
-    const int64_t n_lr = int64_t(g.nz / st->s) * g.ny * g.nx;
+    const int64_t n_lr = trilinear ? int64_t(st->lr_nz) * st->lr_ny * st->lr_nx
+                                   : int64_t(g.nz / st->s) * g.ny * g.nx;
     // L1 loss; its gradient overwrites lr_pred in place.
     s = launch_l1(st->lr_pred, st->lr_target, n_lr, st->d_loss, st->lr_pred, w.l1_part, cs);
     if (s != GS_OK) return s;
-    {
+    if (trilinear) {
+        s = resample_adj_prep_impl(st->lr_pred, st->lr_nz, st->lr_ny, st->lr_nx, st->I, st->W, g.nz,
+                                   g.ny, g.nx, st->cfg.eps, w.aip, cs);
+        if (s != GS_OK) return s;
+    } else {
         const int64_t nv = int64_t(g.nz) * g.ny * g.nx;
         k_profile_adj_prep<<<grid_for(nv), 256, 0, cs>>>(st->lr_pred, st->I, st->W, g.nz, g.ny, g.nx,
                                                          st->s, 1.0f / float(st->s), st->cfg.eps,

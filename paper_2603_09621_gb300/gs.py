@@ -59,7 +59,11 @@ class gs_fit_state(ctypes.Structure):
                 ("I", ctypes.c_void_p), ("W", ctypes.c_void_p), ("lr_pred", ctypes.c_void_p), ("lr_target", ctypes.c_void_p),
                 ("d_loss", ctypes.c_void_p), ("ws", ctypes.c_void_p),
                 ("ws_bytes", ctypes.c_size_t), ("phase_events", ctypes.c_void_p),
-                ("n_phase_events", ctypes.c_int32)]
+                ("n_phase_events", ctypes.c_int32), ("lr_model", ctypes.c_int32),
+                ("lr_nx", ctypes.c_int32), ("lr_ny", ctypes.c_int32), ("lr_nz", ctypes.c_int32)]
+
+
+GS_LR_ZBOX, GS_LR_TRILINEAR = 0, 1
 
 
 GS_FIT_PHASES = 7
@@ -77,7 +81,9 @@ class gs_request(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("grid", gs_grid), ("s", ctypes.c_int32),
                 ("iters", ctypes.c_int32), ("n_gauss", ctypes.c_int64),
                 ("params", ctypes.c_void_p), ("lr_target", ctypes.c_void_p),
-                ("source", ctypes.c_int64), ("arrival_s", ctypes.c_double)]
+                ("source", ctypes.c_int64), ("arrival_s", ctypes.c_double),
+                ("lr_model", ctypes.c_int32), ("lr_nx", ctypes.c_int32),
+                ("lr_ny", ctypes.c_int32), ("lr_nz", ctypes.c_int32)]
 
 
 class gs_result(ctypes.Structure):
@@ -124,6 +130,10 @@ SIGNATURES = {
     "gs_l1_loss_static": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P]),
     "gs_adam_step": (ctypes.c_int, [_P, _P, _P, _P, _I64, _P, _P, _P]),
     "gs_init_lattice": (ctypes.c_int, [_P, _P, _I32, _I32, _I32, _I32, _I32, _F, _P, _P]),
+    "gs_init_lattice_lr": (ctypes.c_int, [_P, _I32, _I32, _I32, _P, _I32, _I32, _I32, _I32, _F,
+                                          _P, _P]),
+    "gs_resample_fwd": (ctypes.c_int, [_P, _I32, _I32, _I32, _P, _I32, _I32, _I32, _P]),
+    "gs_resample_bwd": (ctypes.c_int, [_P, _I32, _I32, _I32, _P, _I32, _I32, _I32, _P]),
     "gs_fit_step": (ctypes.c_int, [_P, _P]),
     "gs_status_read": (ctypes.c_int, [_P, _P, _P]),
     "gs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -370,6 +380,26 @@ def gs_downsample_bwd(dlr: torch.Tensor, nz: int, s: int, dhr=None, stream=None)
     return dhr
 
 
+def gs_resample_fwd(src: torch.Tensor, out_shape, dst=None, stream=None):
+    """Trilinear resize (half-pixel centres) of a [z, y, x] volume to out_shape."""
+    snz, sny, snx = src.shape
+    dnz, dny, dnx = out_shape
+    dst = torch.empty(tuple(out_shape), dtype=torch.float32, device=src.device) if dst is None else dst
+    _check(load().gs_resample_fwd(_ptr(src), snz, sny, snx, _ptr(dst), dnz, dny, dnx,
+                                  _stream(stream)), "gs_resample_fwd")
+    return dst
+
+
+def gs_resample_bwd(ddst: torch.Tensor, src_shape, dsrc=None, stream=None):
+    """Adjoint of gs_resample_fwd: R^T ddst on the source shape."""
+    dnz, dny, dnx = ddst.shape
+    snz, sny, snx = src_shape
+    dsrc = torch.empty(tuple(src_shape), dtype=torch.float32, device=ddst.device) if dsrc is None else dsrc
+    _check(load().gs_resample_bwd(_ptr(ddst), dnz, dny, dnx, _ptr(dsrc), snz, sny, snx,
+                                  _stream(stream)), "gs_resample_bwd")
+    return dsrc
+
+
 def gs_l1_loss(pred, target, ws: Workspace, d_loss=None, dpred=None, stream=None):
     d_loss = torch.empty((), dtype=torch.float32, device=pred.device) if d_loss is None else d_loss
     _check(load().gs_l1_loss(_ptr(pred), _ptr(target), pred.numel(), _ptr(d_loss), _ptr(dpred),
@@ -401,6 +431,19 @@ def gs_init_lattice(lr, grid: Grid, s: int, nl, t_act: int = 1, t_init: float = 
     g = grid.c()
     _check(load().gs_init_lattice(_ptr(lr), ctypes.byref(g), s, nl[0], nl[1], nl[2], t_act,
                                   t_init, _ptr(out), _stream(stream)), "gs_init_lattice")
+    return out
+
+
+def gs_init_lattice_lr(lr, grid: Grid, nl, t_act: int = 1, t_init: float = 0.5, out=None,
+                       stream=None):
+    """Lattice init from an LR volume made by gs_resample_fwd on ``grid``'s field of view."""
+    lnz, lny, lnx = lr.shape
+    n = nl[0] * nl[1] * nl[2]
+    out = torch.empty((n, 12), dtype=torch.float32, device=lr.device) if out is None else out
+    g = grid.c()
+    _check(load().gs_init_lattice_lr(_ptr(lr), lnz, lny, lnx, ctypes.byref(g), nl[0], nl[1],
+                                     nl[2], t_act, t_init, _ptr(out), _stream(stream)),
+           "gs_init_lattice_lr")
     return out
 
 
@@ -457,7 +500,10 @@ class FitState:
     volumes, workspace) driving gs_fit_step."""
 
     def __init__(self, params0: torch.Tensor, lr_target: torch.Tensor, grid: Grid, s: int,
-                 cfg: Config = Config(t_act=1), adam: Adam = Adam(), capacity: int | None = None):
+                 cfg: Config = Config(t_act=1), adam: Adam = Adam(), capacity: int | None = None,
+                 lr_model: int = GS_LR_ZBOX):
+        """lr_model GS_LR_ZBOX: lr_target is [nz // s, ny, nx]; GS_LR_TRILINEAR: lr_target has
+        any shape and s is unused."""
         dev = params0.device
         n = params0.shape[0]
         self.grid, self.cfg, self.adam, self.s = grid, cfg, adam, s
@@ -489,6 +535,9 @@ class FitState:
         st.I, st.W = self.I.data_ptr(), self.W.data_ptr()
         st.lr_pred, st.lr_target = self.lr_pred.data_ptr(), self.lr_target.data_ptr()
         st.d_loss, st.ws, st.ws_bytes = self.d_loss.data_ptr(), self.ws.buf.data_ptr(), self.ws.nbytes
+        st.lr_model = lr_model
+        if lr_model == GS_LR_TRILINEAR:
+            st.lr_nz, st.lr_ny, st.lr_nx = self.lr_target.shape
         self.c = st
 
     def set_phase_events(self, events):

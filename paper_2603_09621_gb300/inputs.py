@@ -94,12 +94,13 @@ def _random_rotations(rng, n):
 
 
 def phantom_draws(seed: int, shape_zyx, n_ell: int = 12, s: int = 4,
-                  semi_axes=(10.0, 80.0), noise_sigma: float = 0.02) -> dict:
+                  semi_axes=(10.0, 80.0), noise_sigma: float = 0.02, lr_shape=None) -> dict:
     """Ellipsoid tissue phantom draws.
 
     Returns dict(label [nz, ny, nx] uint8 (0 background, e + 1 for ellipsoid e; later
-    ellipsoids overwrite earlier ones), pd, t1, t2 [n_ell], n1, n2 [nz // s, ny, nx]
-    (independent N(0, noise_sigma^2) draws for the real and imaginary noise channels).
+    ellipsoids overwrite earlier ones), pd, t1, t2 [n_ell], n1, n2 of shape ``lr_shape``
+    (default [nz // s, ny, nx]: independent N(0, noise_sigma^2) draws for the real and
+    imaginary noise channels of the LR scan).
     Semi-axes are drawn uniformly in ``semi_axes`` voxels, capped at 45 % of the volume's
     extent along the ellipsoid's longest box axis so that every ellipsoid stays visible.
     """
@@ -134,9 +135,9 @@ def phantom_draws(seed: int, shape_zyx, n_ell: int = 12, s: int = 4,
         inside = (u * u + v * v + w * w) <= 1.0
         sub = label[z0:z1, y0:y1, x0:x1]
         sub[inside] = e + 1
-    nl = nz // s
-    n1 = rng.standard_normal(size=(nl, ny, nx)).astype(np.float32) * np.float32(noise_sigma)
-    n2 = rng.standard_normal(size=(nl, ny, nx)).astype(np.float32) * np.float32(noise_sigma)
+    lshape = tuple(lr_shape) if lr_shape is not None else (nz // s, ny, nx)
+    n1 = rng.standard_normal(size=lshape).astype(np.float32) * np.float32(noise_sigma)
+    n2 = rng.standard_normal(size=lshape).astype(np.float32) * np.float32(noise_sigma)
     return dict(label=label, pd=pd, t1=t1, t2=t2, n1=n1, n2=n2, s=s)
 
 

@@ -38,12 +38,17 @@ def server_config(budget_bytes: int, max_active: int = 4, chunk_steps: int = 25,
 
 
 def fit_request(params0: torch.Tensor, lr_target: torch.Tensor, grid: Grid, s: int, iters: int,
-                arrival_s: float = 0.0) -> gs.gs_request:
+                arrival_s: float = 0.0, lr_model: int = gs.GS_LR_ZBOX) -> gs.gs_request:
+    """lr_model GS_LR_ZBOX: lr_target is [nz // s, ny, nx]; GS_LR_TRILINEAR: any LR shape (s
+    unused)."""
     r = gs.gs_request()
     r.kind, r.grid, r.s, r.iters = gs.GS_REQ_FIT, grid.c(), s, iters
     r.n_gauss = params0.shape[0]
     r.params, r.lr_target = params0.data_ptr(), lr_target.data_ptr()
     r.source, r.arrival_s = -1, arrival_s
+    r.lr_model = lr_model
+    if lr_model == gs.GS_LR_TRILINEAR:
+        r.lr_nz, r.lr_ny, r.lr_nx = lr_target.shape
     return r
 
 
@@ -99,9 +104,9 @@ class Server:
         return rid.value
 
     def submit_fit(self, params0, lr_target, grid: Grid, s: int, iters: int,
-                   arrival_s: float = 0.0) -> int:
+                   arrival_s: float = 0.0, lr_model: int = gs.GS_LR_ZBOX) -> int:
         params0, lr_target = params0.contiguous(), lr_target.contiguous()
-        req = fit_request(params0, lr_target, grid, s, iters, arrival_s)
+        req = fit_request(params0, lr_target, grid, s, iters, arrival_s, lr_model)
         return self._submit(req, (params0, lr_target), (params0.shape[0], 12))
 
     def submit_render(self, grid: Grid, source: int | None = None, params=None,

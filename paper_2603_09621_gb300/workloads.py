@@ -61,6 +61,32 @@ def phantom_fit(shape=(128, 256, 256), s=4, n_gauss=500_000, seed=0, n_ell=12,
     return dict(grid=grid, hr=hr, lr=lr, params0=params0, s=s, nl=nl)
 
 
+def phantom_fit_trilinear(shape=(155, 240, 240), lr_shape=(100, 100, 100), n_gauss=500_000,
+                          seed=0, n_ell=12, semi=(10.0, 80.0), device="cuda"):
+    """Fitting workload with the trilinear LR model (Sec. 4.1-4.2: LR by trilinear
+    downsampling, super-resolution to an arbitrary target shape): HR phantom, noisy LR scan of
+    ``lr_shape`` by gs_resample_fwd, lattice init from it. Returns dict(grid, hr, lr,
+    params0, nl)."""
+    nz, ny, nx = shape
+    ph = inputs.phantom_draws(seed, shape, n_ell=n_ell, semi_axes=semi, lr_shape=lr_shape)
+    t1 = torch.as_tensor(ph["t1"], dtype=torch.float32, device=device)
+    t2 = torch.as_tensor(ph["t2"], dtype=torch.float32, device=device)
+    tissue = torch.as_tensor(ph["pd"], dtype=torch.float32, device=device) * gs.gs_signal_proxy(
+        t1, t2, TR, TE)
+    table = torch.cat([torch.zeros(1, device=device), tissue])
+    label = torch.as_tensor(ph["label"], device=device).long()
+    vmax = table[torch.unique(label)].max()
+    hr = (table[label] / torch.where(vmax > 0, vmax, torch.ones_like(vmax))).contiguous()
+    lr_clean = gs.gs_resample_fwd(hr, lr_shape)
+    n1 = torch.as_tensor(ph["n1"], device=device)
+    n2 = torch.as_tensor(ph["n2"], device=device)
+    lr = torch.sqrt((lr_clean + n1) ** 2 + n2 ** 2).contiguous()
+    grid = gs.Grid(nx, ny, nz)
+    nl = lattice_dims(grid, n_gauss)
+    params0 = gs.gs_init_lattice_lr(lr, grid, nl, t_act=1, t_init=0.5)
+    return dict(grid=grid, hr=hr, lr=lr, params0=params0, nl=nl)
+
+
 def serving_workload(draws: list, device="cuda") -> list:
     """Device inputs of a serving request stream (``inputs.serving_draws``): each fit gets its
     own phantom scan (seeded by its draw), noisy LR target and lattice-initialised cloud; each

@@ -53,3 +53,18 @@ def rel_l2(a, b) -> float:
 def to_dev(x, device="cuda"):
     import torch
     return torch.as_tensor(np.ascontiguousarray(x)).to(device)
+
+
+@functools.lru_cache(maxsize=None)
+def phantom_fit_trilinear(shape=(40, 48, 56), lr_shape=(17, 20, 23), n_gauss=6000, seed=2,
+                          n_ell=5, semi=(5.0, 16.0)):
+    """Fitting workload with the trilinear LR model: ellipsoid phantom, LR by the oracle's
+    trilinear resize to lr_shape with Rician noise, lattice init from it."""
+    import oracle
+    nz, ny, nx = shape
+    ph = inputs.phantom_draws(seed, shape, n_ell=n_ell, semi_axes=semi, lr_shape=lr_shape)
+    hr = oracle.phantom_from_draws(ph, TR, TE)
+    lr = oracle.rician(oracle.resample(hr, lr_shape), ph["n1"], ph["n2"]).astype(np.float32)
+    grid = oracle.Grid(nx, ny, nz)
+    params0 = oracle.init_lattice_lr(lr, grid, n_gauss, t_act=1)
+    return dict(grid=grid, hr=hr, lr=lr, params0=params0)
