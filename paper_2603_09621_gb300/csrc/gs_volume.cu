@@ -82,6 +82,66 @@ static unsigned grid_for(int64_t n) {
     return static_cast<unsigned>(b < 65536 ? b : 65536);
 }
 
+// The slice profile and its adjoint-factor kernel over a 2D grid (blockIdx.y = LR or HR
+// slice) with four voxels per thread, for planes of a multiple of 4 voxels and at most 65,535 slices: no index division
+// per voxel, 16-byte accesses. Same arithmetic, same results.
+__global__ void __launch_bounds__(256) k_downsample_fwd4(const float4* __restrict__ hr, int plane4,
+                                                         int s, float inv_s,
+                                                         float4* __restrict__ lr) {
+    const int k = blockIdx.y;
+    const float4* src = hr + int64_t(k) * s * plane4;
+    float4* dst = lr + int64_t(k) * plane4;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < plane4; r += gridDim.x * blockDim.x) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int j = 0; j < s; ++j) {
+            const float4 v = src[int64_t(j) * plane4 + r];
+            acc.x += v.x;
+            acc.y += v.y;
+            acc.z += v.z;
+            acc.w += v.w;
+        }
+        dst[r] = make_float4(acc.x * inv_s, acc.y * inv_s, acc.z * inv_s, acc.w * inv_s);
+    }
+}
+
+__device__ __forceinline__ float2 adj_factor(float gI, float w, float iv, float eps) {
+    const float al = gI / (w > eps ? w : eps);
+    return make_float2(al, (w > eps) ? al * iv : 0.0f);
+}
+
+__global__ void __launch_bounds__(256) k_profile_adj_prep4(const float4* __restrict__ dlr,
+                                                           const float4* __restrict__ Iv,
+                                                           const float4* __restrict__ Wv,
+                                                           int plane4, int zmax, int s, float inv_s,
+                                                           float eps, float4* __restrict__ aip) {
+    const int z = blockIdx.y;
+    const bool in = z < zmax;
+    const int64_t base = int64_t(z) * plane4;
+    const float4* g4 = dlr + int64_t(in ? z / s : 0) * plane4;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < plane4; r += gridDim.x * blockDim.x) {
+        float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (in) {
+            const float4 d = g4[r];
+            g = make_float4(d.x * inv_s, d.y * inv_s, d.z * inv_s, d.w * inv_s);
+        }
+        const float4 w = Wv[base + r], iv = Iv[base + r];
+        const float2 a0 = adj_factor(g.x, w.x, iv.x, eps), a1 = adj_factor(g.y, w.y, iv.y, eps);
+        const float2 a2 = adj_factor(g.z, w.z, iv.z, eps), a3 = adj_factor(g.w, w.w, iv.w, eps);
+        aip[2 * (base + r)] = make_float4(a0.x, a0.y, a1.x, a1.y);
+        aip[2 * (base + r) + 1] = make_float4(a2.x, a2.y, a3.x, a3.y);
+    }
+}
+
+static dim3 grid2d(int plane4, int slices) {
+    const int bx = (plane4 + 255) / 256;
+    return dim3(static_cast<unsigned>(bx < 64 ? bx : 64), static_cast<unsigned>(slices));
+}
+
+static bool vec_ok(const void* a, const void* b, int64_t plane, int slices) {
+    return plane % 4 == 0 && slices <= 65535 && reinterpret_cast<uintptr_t>(a) % 16 == 0 &&
+           reinterpret_cast<uintptr_t>(b) % 16 == 0;
+}
+
 gs_status launch_l1(const float* pred, const float* target, int64_t n, float* d_loss, float* dpred,
                     float* partials, cudaStream_t st) {
     const float inv_n = n > 0 ? 1.0f / float(n) : 0.0f;
@@ -97,7 +157,14 @@ gs_status downsample_fwd_impl(const float* hr, int nz, int ny, int nx, int s, fl
     const int nzl = nz / s;
     const int64_t n = int64_t(nzl) * ny * nx;
     if (n == 0) return GS_OK;
-    k_downsample_fwd<<<grid_for(n), 256, 0, st>>>(hr, ny, nx, nzl, s, 1.0f / float(s), lr);
+    const int64_t plane = int64_t(ny) * nx;
+    if (vec_ok(hr, lr, plane, nzl) && plane / 4 <= (int64_t(1) << 30)) {
+        const int plane4 = static_cast<int>(plane / 4);
+        k_downsample_fwd4<<<grid2d(plane4, nzl), 256, 0, st>>>(
+            reinterpret_cast<const float4*>(hr), plane4, s, 1.0f / float(s), reinterpret_cast<float4*>(lr));
+    } else {
+        k_downsample_fwd<<<grid_for(n), 256, 0, st>>>(hr, ny, nx, nzl, s, 1.0f / float(s), lr);
+    }
     return last_launch_status();
 }
 
@@ -235,9 +302,19 @@ extern "C" gs_status gs_fit_step(gs_fit_state* st, gs_stream stream) {
         if (s != GS_OK) return s;
     } else {
         const int64_t nv = int64_t(g.nz) * g.ny * g.nx;
-        k_profile_adj_prep<<<grid_for(nv), 256, 0, cs>>>(st->lr_pred, st->I, st->W, g.nz, g.ny, g.nx,
-                                                         st->s, 1.0f / float(st->s), st->cfg.eps,
-                                                         w.aip);
+        const int64_t plane = int64_t(g.ny) * g.nx;
+        if (vec_ok(st->lr_pred, st->I, plane, g.nz) && vec_ok(st->W, w.aip, plane, g.nz) &&
+            plane / 4 <= (int64_t(1) << 30)) {
+            const int plane4 = static_cast<int>(plane / 4);
+            k_profile_adj_prep4<<<grid2d(plane4, g.nz), 256, 0, cs>>>(
+                reinterpret_cast<const float4*>(st->lr_pred), reinterpret_cast<const float4*>(st->I),
+                reinterpret_cast<const float4*>(st->W), plane4, st->s * (g.nz / st->s), st->s,
+                1.0f / float(st->s), st->cfg.eps, reinterpret_cast<float4*>(w.aip));
+        } else {
+            k_profile_adj_prep<<<grid_for(nv), 256, 0, cs>>>(st->lr_pred, st->I, st->W, g.nz, g.ny,
+                                                             g.nx, st->s, 1.0f / float(st->s),
+                                                             st->cfg.eps, w.aip);
+        }
         s = last_launch_status();
         if (s != GS_OK) return s;
     }
