@@ -62,13 +62,14 @@ def phantom_fit(shape=(128, 256, 256), s=4, n_gauss=500_000, seed=0, n_ell=12,
 
 
 def phantom_fit_trilinear(shape=(155, 240, 240), lr_shape=(100, 100, 100), n_gauss=500_000,
-                          seed=0, n_ell=12, semi=(10.0, 80.0), device="cuda"):
+                          seed=0, n_ell=12, semi=(10.0, 80.0), noise_sigma=0.02, device="cuda"):
     """Fitting workload with the trilinear LR model (Sec. 4.1-4.2: LR by trilinear
     downsampling, super-resolution to an arbitrary target shape): HR phantom, noisy LR scan of
     ``lr_shape`` by gs_resample_fwd, lattice init from it. Returns dict(grid, hr, lr,
     params0, nl)."""
     nz, ny, nx = shape
-    ph = inputs.phantom_draws(seed, shape, n_ell=n_ell, semi_axes=semi, lr_shape=lr_shape)
+    ph = inputs.phantom_draws(seed, shape, n_ell=n_ell, semi_axes=semi, lr_shape=lr_shape,
+                              noise_sigma=noise_sigma)
     t1 = torch.as_tensor(ph["t1"], dtype=torch.float32, device=device)
     t2 = torch.as_tensor(ph["t2"], dtype=torch.float32, device=device)
     tissue = torch.as_tensor(ph["pd"], dtype=torch.float32, device=device) * gs.gs_signal_proxy(
