@@ -62,6 +62,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--fast", action="store_true", help="non-deterministic (atomic) reduction")
+    ap.add_argument("--brick", default="8,8,8",
+                    help="brick shape x,y,z of the fitting step (Sec. 3.3 uses 8,8,4)")
     ap.add_argument("--no-graph", action="store_true",
                     help="time eager gs_fit_step calls instead of CUDA-graph replays")
     ap.add_argument("--workload", choices=["fit", "shape", "fullfit", "stress", "serve"],
@@ -299,6 +301,10 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def brick_of(args):
+    return tuple(int(v) for v in getattr(args, "brick", "8,8,8").split(","))
+
+
 def config_dict(args):
     if getattr(args, "workload", "fit") == "shape":
         nz, ny, nx = SHAPE_TRI
@@ -306,14 +312,14 @@ def config_dict(args):
         return {"workload": f"zero-shot fit step {nx}x{ny}x{nz} HR from a {lx}x{ly}x{lz} LR scan "
                             f"(trilinear LR model), {N_GAUSS} Gaussians, L1, Adam",
                 "grid": [nx, ny, nz], "lr_grid": [lx, ly, lz], "n_gauss": N_GAUSS,
-                "brick": [8, 8, 8], "deterministic": 0 if args.fast else 1,
+                "brick": list(brick_of(args)), "deterministic": 0 if args.fast else 1,
                 "launch": "eager" if args.no_graph else "cuda graph replay of gs_fit_step",
                 "l2": "flushed between timed steps (256 MB write)"}
     nz, ny, nx = SHAPE
     return {"workload": f"zero-shot fit step {nx}x{ny}x{nz} HR, {N_GAUSS} Gaussians, "
                         f"z box x{S_FACTOR}, L1, Adam",
             "grid": [nx, ny, nz], "n_gauss": N_GAUSS, "slice_factor": S_FACTOR,
-            "brick": [8, 8, 8], "deterministic": 0 if args.fast else 1,
+            "brick": list(brick_of(args)), "deterministic": 0 if args.fast else 1,
             "launch": "eager" if args.no_graph else "cuda graph replay of gs_fit_step",
             "l2": "flushed between timed steps (256 MB write)"}
 
@@ -326,7 +332,7 @@ def run_ours(args, world, rank, local):
     from paper_2603_09621_gb300 import gs, workloads
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    cfg = gs.Config(t_act=1, deterministic=0 if args.fast else 1)
+    cfg = gs.Config(t_act=1, deterministic=0 if args.fast else 1, brick=brick_of(args))
     tri = args.workload == "shape"
     if tri:
         w = workloads.phantom_fit_trilinear(shape=SHAPE_TRI, lr_shape=LR_TRI, n_gauss=N_GAUSS,

@@ -388,11 +388,12 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const int32_t* __re
 
 // Stable scatter of one tile of kSortTile keys. Warp w owns the contiguous sub-tile
 // [w * 512, (w + 1) * 512) and visits it in 16 rounds of 32 consecutive keys (kept in
-// registers). Pass 1 counts each warp's digits; one block-wide prefix over the warps (plus
-// the tile's global offset) gives every warp its starting slot per digit; pass 2 places each
-// key at that slot + its rank among equal digits in lower lanes (warp match masks), then
-// advances the warp's counter. Order is preserved: warps in tile order, rounds in order,
-// lanes in order.
+// registers). Pass 1 counts each warp's digits. A block-wide prefix then gives, per digit,
+// the tile-local start of its run and each warp's start inside it. Pass 2 places every key in
+// shared memory at its warp's start + its rank among equal digits in lower lanes (warp match
+// masks), so the tile sits in shared memory sorted by digit, ties in tile order. The tile is
+// then written out in that order: digit d's run goes to [hist_off[d][tile], ...), so
+// consecutive threads store consecutive addresses.
 template <bool kFirst>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in,
@@ -402,14 +403,21 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     constexpr int kWarps = kSortThreads / 32;
     constexpr int kPerWarp = kSortTile / kWarps;
     constexpr int kRounds = kPerWarp / 32;
+    static_assert(kSortThreads == kRadix, "one thread per digit in the block-wide prefix");
     __shared__ int wcnt[kWarps][kRadix];
+    __shared__ int dstart[kRadix];   // tile-local start of each digit's run
+    __shared__ int gstart[kRadix];   // global start of each digit's run for this tile
+    __shared__ int wsum[kWarps];
+    __shared__ int skey[kSortTile];
+    __shared__ int sval[kSortTile];
     const int64_t P = valid_pairs(npairs, capacity);
-    if (int64_t(blockIdx.x) * kSortTile >= P) return;  // past the last pair: nothing to place
+    const int64_t tile0 = int64_t(blockIdx.x) * kSortTile;
+    if (tile0 >= P) return;  // past the last pair: nothing to place
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int d = tid; d < kRadix; d += kSortThreads)
         for (int w = 0; w < kWarps; ++w) wcnt[w][d] = 0;
     __syncthreads();
-    const int64_t sub0 = int64_t(blockIdx.x) * kSortTile + int64_t(warp) * kPerWarp;
+    const int64_t sub0 = tile0 + int64_t(warp) * kPerWarp;
     const unsigned lt_mask = (1u << lane) - 1u;
     int kr[kRounds], vr[kRounds];
 #pragma unroll
@@ -425,30 +433,54 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
         __syncwarp();
     }
     __syncthreads();
-    for (int d = tid; d < kRadix; d += kSortThreads) {
-        int run = hist_off[int64_t(d) * n_tiles + blockIdx.x];
-        for (int w = 0; w < kWarps; ++w) {
-            const int c = wcnt[w][d];
-            wcnt[w][d] = run;
-            run += c;
-        }
+    // thread d: warps' starts inside digit d's run, and the run's length
+    const int d = tid;
+    int run = 0;
+    for (int w = 0; w < kWarps; ++w) {
+        const int c = wcnt[w][d];
+        wcnt[w][d] = run;
+        run += c;
     }
+    // exclusive prefix of the run lengths over digits (block scan, digit order)
+    int incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    const int start = before + incl - run;
+    dstart[d] = start;
+    gstart[d] = hist_off[int64_t(d) * n_tiles + blockIdx.x];
+    for (int w = 0; w < kWarps; ++w) wcnt[w][d] += start;
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
         const int64_t idx = sub0 + r * 32 + lane;
         const bool valid = idx < P;
-        const int d = (kr[r] >> shift) & (kRadix - 1);
-        const unsigned tag = valid ? static_cast<unsigned>(d) : static_cast<unsigned>(kRadix + lane);
+        const int dk = (kr[r] >> shift) & (kRadix - 1);
+        const unsigned tag = valid ? static_cast<unsigned>(dk) : static_cast<unsigned>(kRadix + lane);
         const unsigned peers = __match_any_sync(0xffffffffu, tag);
         if (valid) {
-            const int pos = wcnt[warp][d] + __popc(peers & lt_mask);
-            keys_out[pos] = kr[r];
-            vals_out[pos] = vr[r];
+            const int lp = wcnt[warp][dk] + __popc(peers & lt_mask);
+            skey[lp] = kr[r];
+            sval[lp] = vr[r];
         }
         __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] += __popc(peers);
+        if (valid && lane == __ffs(peers) - 1) wcnt[warp][dk] += __popc(peers);
         __syncwarp();
+    }
+    __syncthreads();
+    const int n_here = static_cast<int>(min(int64_t(kSortTile), P - tile0));
+    for (int j = tid; j < n_here; j += kSortThreads) {
+        const int key = skey[j];
+        const int dk = (key >> shift) & (kRadix - 1);
+        const int pos = gstart[dk] + (j - dstart[dk]);
+        keys_out[pos] = key;
+        vals_out[pos] = sval[j];
     }
 }
 
