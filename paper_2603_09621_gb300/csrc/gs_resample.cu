@@ -79,12 +79,11 @@ __global__ void __launch_bounds__(256) k_resample_fwd(const float* __restrict__ 
 }
 
 // The destination samples that read source sample i form one run j0, j0 + 1, ... (i0(j) is
-// non-decreasing in j). kResList slots cover it whenever n_dst / n_src <= 3/2 (c_j steps by
-// n_src / n_dst >= 2/3, so at most four c_j fall in [i - 1, i + 1)). Slot k holds the weight
-// of j0 + k (0 past the run); *n is the run length.
+// non-decreasing in j). K slots cover it under the bounds of res_list_ok / res_two_taps.
+// Slot k holds the weight of j0 + k (0 past the run); *n is the run length.
 constexpr int kResList = 4;
-__device__ __forceinline__ void res_list(const ResAxis& A, int i, int& j0, int& n,
-                                         float (&w)[kResList]) {
+template <int K = kResList>
+__device__ __forceinline__ void res_list(const ResAxis& A, int i, int& j0, int& n, float (&w)[K]) {
     int lo, hi;
     res_range(A, i, lo, hi);
     int t = lo;
@@ -97,15 +96,32 @@ __device__ __forceinline__ void res_list(const ResAxis& A, int i, int& j0, int& 
     j0 = t;
     n = 0;
 #pragma unroll
-    for (int k = 0; k < kResList; ++k) {
+    for (int k = 0; k < K; ++k) {
         const int j = t + k;
         w[k] = (j < A.n_dst) ? res_weight(A, j, i) : 0.0f;
         n = (w[k] != 0.0f) ? k + 1 : n;
     }
 }
 
-__host__ __device__ __forceinline__ bool res_list_ok(const ResGeo& G) {
-    return G.a[0].inv <= 1.5f && G.a[1].inv <= 1.5f && G.a[2].inv <= 1.5f;
+// Run lengths with FP32 positions: c_j is within c 2^-23 of its exact value, so for source
+// sizes up to 2^16 consecutive positions are spaced by the scale +- 2^-6.
+//   kResList slots: scale >= 2/3 on every axis keeps the spacing above 0.65, so at most
+//   four positions fall in one window [i - 1, i + 1).
+//   2 slots: an exact copy (scale 1: c_j = j) or scale >= 1.05 (spacing above 1.03).
+constexpr int kResMaxSrc = 1 << 16;
+static bool res_list_ok(const ResGeo& G) {
+    for (int a = 0; a < 3; ++a)
+        if (!(G.a[a].inv <= 1.5f) || G.a[a].n_src > kResMaxSrc) return false;
+    return true;
+}
+
+static bool res_two_taps(const ResGeo& G) {
+    for (int a = 0; a < 3; ++a) {
+        const ResAxis& A = G.a[a];
+        if (A.n_src > kResMaxSrc) return false;
+        if (A.n_dst != A.n_src && !(A.scale >= 1.05f)) return false;
+    }
+    return true;
 }
 
 // Adjoint value at source voxel (x, y, z): sum over the destination samples that read it, in
@@ -148,62 +164,66 @@ __global__ void __launch_bounds__(256) k_resample_bwd(const float* __restrict__ 
     }
 }
 
-// Row-chunk form of the list gather (n_dst / n_src <= 3/2 on every axis and at most kResTab
-// source columns): a block first tabulates the x runs of all source columns in shared
-// memory; a thread then takes kResChunk consecutive voxels of one row, builds its y and z
-// runs once and gathers each voxel in ascending (z, y, x) order.
-constexpr int kResTab = 1024;
-constexpr int kResChunk = 8;
+// Table form of the adjoint gather (under res_list_ok / res_two_taps, with at most
+// kResTabMax source samples over the three axes): each block tabulates the runs of every
+// source x, y and z in shared memory once, then sweeps source rows (z, y) with one thread
+// per voxel; a voxel reads its three runs from the tables and gathers in ascending (z, y, x)
+// order.
+constexpr int kResTabMax = 2048;
 
+template <int K>
 struct ResRun {
     int j0, n;
-    float w[kResList];
+    float w[K];
 };
 
-template <bool kPrep>
-__global__ void __launch_bounds__(256, 3) k_resample_adj_rows(const float* __restrict__ ddst, ResGeo G,
-                                                           const float* __restrict__ Iv,
-                                                           const float* __restrict__ Wv, float eps,
-                                                           float* __restrict__ dsrc,
-                                                           float2* __restrict__ aip) {
-    __shared__ ResRun xt[kResTab];
+template <bool kPrep, int K>
+__global__ void __launch_bounds__(256) k_resample_adj_tab(const float* __restrict__ ddst, ResGeo G,
+                                                          const float* __restrict__ Iv,
+                                                          const float* __restrict__ Wv, float eps,
+                                                          float* __restrict__ dsrc,
+                                                          float2* __restrict__ aip) {
+    extern __shared__ __align__(16) unsigned char res_smem[];
+    ResRun<K>* tab = reinterpret_cast<ResRun<K>*>(res_smem);
     const ResAxis &AX = G.a[0], &AY = G.a[1], &AZ = G.a[2];
-    for (int i = threadIdx.x; i < AX.n_src; i += blockDim.x) {
-        ResRun rr;
-        res_list(AX, i, rr.j0, rr.n, rr.w);
-        xt[i] = rr;
+    const int nx = AX.n_src, ny = AY.n_src, nz = AZ.n_src;
+    ResRun<K>* xt = tab;
+    ResRun<K>* yt = tab + nx;
+    ResRun<K>* zt = tab + nx + ny;
+    for (int e = threadIdx.x; e < nx + ny + nz; e += blockDim.x) {
+        const int ax = e < nx ? 0 : (e < nx + ny ? 1 : 2);
+        const int i = e - (ax > 0 ? nx : 0) - (ax > 1 ? ny : 0);
+        ResAxis A;
+        A.scale = ax == 0 ? AX.scale : (ax == 1 ? AY.scale : AZ.scale);
+        A.inv = ax == 0 ? AX.inv : (ax == 1 ? AY.inv : AZ.inv);
+        A.n_src = ax == 0 ? AX.n_src : (ax == 1 ? AY.n_src : AZ.n_src);
+        A.n_dst = ax == 0 ? AX.n_dst : (ax == 1 ? AY.n_dst : AZ.n_dst);
+        ResRun<K> rr;
+        res_list<K>(A, i, rr.j0, rr.n, rr.w);
+        tab[e] = rr;
     }
     __syncthreads();
-    const int nxc = (AX.n_src + kResChunk - 1) / kResChunk;
-    const int64_t n = int64_t(nxc) * AY.n_src * AZ.n_src;
-    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n;
-         t += int64_t(gridDim.x) * blockDim.x) {
-        const int xc = static_cast<int>(t % nxc);
-        const int y = static_cast<int>((t / nxc) % AY.n_src);
-        const int z = static_cast<int>(t / (int64_t(nxc) * AY.n_src));
-        int jy, jz, ny, nz;
-        float wy[kResList], wz[kResList];
-        res_list(AY, y, jy, ny, wy);
-        res_list(AZ, z, jz, nz, wz);
-        const int64_t row0 = (int64_t(z) * AY.n_src + y) * AX.n_src;
-        const int x0 = xc * kResChunk;
-        const int x1 = min(x0 + kResChunk, AX.n_src);
-        for (int x = x0; x < x1; ++x) {
-            const ResRun& rx = xt[x];
+    const int64_t rows = int64_t(nz) * ny;
+    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int z = static_cast<int>(row / ny), y = static_cast<int>(row - int64_t(z) * ny);
+        const ResRun<K> rz = zt[z], ry = yt[y];
+        const int64_t row0 = row * nx;
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+            const ResRun<K> rx = xt[x];
             float acc = 0.0f;
 #pragma unroll
-            for (int a = 0; a < kResList; ++a) {
-                if (a >= nz) break;
+            for (int a = 0; a < K; ++a) {
+                if (a >= rz.n) break;
 #pragma unroll
-                for (int b = 0; b < kResList; ++b) {
-                    if (b >= ny) break;
-                    const float wzy = wz[a] * wy[b];
-                    const float* row =
-                        ddst + (int64_t(jz + a) * AY.n_dst + (jy + b)) * AX.n_dst + rx.j0;
+                for (int b = 0; b < K; ++b) {
+                    if (b >= ry.n) break;
+                    const float wzy = rz.w[a] * ry.w[b];
+                    const float* src =
+                        ddst + (int64_t(rz.j0 + a) * AY.n_dst + (ry.j0 + b)) * AX.n_dst + rx.j0;
 #pragma unroll
-                    for (int c = 0; c < kResList; ++c) {
+                    for (int c = 0; c < K; ++c) {
                         if (c >= rx.n) break;
-                        if (rx.w[c] != 0.0f) acc = fmaf(wzy * rx.w[c], row[c], acc);
+                        if (rx.w[c] != 0.0f) acc = fmaf(wzy * rx.w[c], src[c], acc);
                     }
                 }
             }
@@ -267,16 +287,28 @@ gs_status resample_fwd_impl(const float* src, int32_t snz, int32_t sny, int32_t 
     return last_launch_status();
 }
 
+template <bool kPrep>
+static bool launch_adj_tab(const float* dd, const ResGeo& G, const float* I, const float* W,
+                           float eps, float* dsrc, float2* aip, cudaStream_t st) {
+    const int n_tab = G.a[0].n_src + G.a[1].n_src + G.a[2].n_src;
+    if (!res_list_ok(G) || n_tab > kResTabMax) return false;
+    const int64_t rows = int64_t(G.a[2].n_src) * G.a[1].n_src;
+    const unsigned nb = static_cast<unsigned>(rows < 152 * 8 ? rows : 152 * 8);
+    if (res_two_taps(G))
+        k_resample_adj_tab<kPrep, 2><<<nb, 256, sizeof(ResRun<2>) * n_tab, st>>>(dd, G, I, W, eps,
+                                                                                dsrc, aip);
+    else
+        k_resample_adj_tab<kPrep, kResList><<<nb, 256, sizeof(ResRun<kResList>) * n_tab, st>>>(
+            dd, G, I, W, eps, dsrc, aip);
+    return true;
+}
+
 gs_status resample_adj_prep_impl(const float* dlr, int32_t lnz, int32_t lny, int32_t lnx,
                                  const float* I, const float* W, int32_t nz, int32_t ny, int32_t nx,
                                  float eps, float2* aip, cudaStream_t st) {
     const ResGeo G = make_res(nz, ny, nx, lnz, lny, lnx);
-    if (res_list_ok(G) && nx <= kResTab) {
-        const int64_t rows = int64_t((nx + kResChunk - 1) / kResChunk) * ny * nz;
-        k_resample_adj_rows<true><<<res_blocks(rows), 256, 0, st>>>(dlr, G, I, W, eps, nullptr, aip);
-    } else {
+    if (!launch_adj_tab<true>(dlr, G, I, W, eps, nullptr, aip, st))
         k_resample_adj_prep<<<res_blocks(int64_t(nz) * ny * nx), 256, 0, st>>>(dlr, G, I, W, eps, aip);
-    }
     return last_launch_status();
 }
 
@@ -298,12 +330,7 @@ extern "C" gs_status gs_resample_bwd(const float* ddst, int32_t dnz, int32_t dny
     if (!ddst || !dsrc || !dims_ok(snz, sny, snx) || !dims_ok(dnz, dny, dnx)) return GS_ERR_INVALID_ARG;
     const ResGeo G = make_res(snz, sny, snx, dnz, dny, dnx);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (res_list_ok(G) && snx <= kResTab) {
-        const int64_t rows = int64_t((snx + kResChunk - 1) / kResChunk) * sny * snz;
-        k_resample_adj_rows<false><<<res_blocks(rows), 256, 0, st>>>(ddst, G, nullptr, nullptr, 0.f,
-                                                                     dsrc, nullptr);
-    } else {
+    if (!launch_adj_tab<false>(ddst, G, nullptr, nullptr, 0.f, dsrc, nullptr, st))
         k_resample_bwd<<<res_blocks(int64_t(snz) * sny * snx), 256, 0, st>>>(ddst, G, dsrc);
-    }
     return last_launch_status();
 }

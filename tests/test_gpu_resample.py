@@ -12,6 +12,8 @@ SHAPES = [((21, 29, 37), (9, 13, 16)),      # ragged downsampling, every axis
           ((32, 48, 64), (16, 24, 32)),     # factor 2 (block means)
           ((7, 9, 11), (16, 13, 20)),       # upsampling
           ((40, 30, 50), (40, 12, 77)),     # mixed: identity, down, up
+          ((20, 24, 30), (26, 30, 40)),     # mild upsampling (four-slot adjoint runs)
+          ((20, 64, 100), (19, 62, 96)),    # near-identity downsampling (four-slot runs)
           ((1, 5, 6), (3, 1, 2))]           # degenerate single-slice axes
 
 
