@@ -107,7 +107,7 @@ __device__ __forceinline__ bool foot_hit(const float4* s, float cx, float cy, fl
 // ------------------------------------------------------------------------ forward
 
 template <bool kStats>
-__global__ void __launch_bounds__(256) k_render_fwd(const int32_t* __restrict__ brick_off,
+__global__ void __launch_bounds__(128, 14) k_render_fwd(const int32_t* __restrict__ brick_off,
                                                     const int32_t* __restrict__ pair_gid,
                                                     const float4* __restrict__ rec4, RenderGeo G,
                                                     float* __restrict__ I, float* __restrict__ W,

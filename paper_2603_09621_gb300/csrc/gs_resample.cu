@@ -287,6 +287,109 @@ gs_status resample_fwd_impl(const float* src, int32_t snz, int32_t sny, int32_t 
     return last_launch_status();
 }
 
+// Separable form of the adjoint for one source plane z and a tile of kPlaneRows source rows:
+// first U[y][jx] = sum over the z and y runs of w_z w_y dL/dLR[jz][jy][jx] for every LR column
+// jx (shared memory), then each voxel sums its x run over U[y]. Fixed order: z, then y
+// (inside U), then x.
+template <bool kPrep, int K, int kPlaneRows>
+__global__ void __launch_bounds__(256) k_resample_adj_plane(const float* __restrict__ ddst, ResGeo G,
+                                                            const float* __restrict__ Iv,
+                                                            const float* __restrict__ Wv, float eps,
+                                                            float* __restrict__ dsrc,
+                                                            float2* __restrict__ aip) {
+    extern __shared__ __align__(16) unsigned char res_smem[];
+    const ResAxis &AX = G.a[0], &AY = G.a[1], &AZ = G.a[2];
+    const int nx = AX.n_src, ny = AY.n_src;
+    const int lnx = AX.n_dst, lny = AY.n_dst;
+    ResRun<K>* xt = reinterpret_cast<ResRun<K>*>(res_smem);
+    ResRun<K>* yt = xt + nx;                                // kPlaneRows entries
+    float* U = reinterpret_cast<float*>(yt + kPlaneRows);  // [kPlaneRows][lnx]
+    __shared__ ResRun<K> zr;
+    const int z = blockIdx.x;
+    const int y0 = blockIdx.y * kPlaneRows;
+    const int rows = min(kPlaneRows, ny - y0);
+    for (int e = threadIdx.x; e < nx + rows + 1; e += blockDim.x) {
+        ResRun<K> rr;
+        if (e < nx) {
+            res_list<K>(AX, e, rr.j0, rr.n, rr.w);
+            xt[e] = rr;
+        } else if (e < nx + rows) {
+            res_list<K>(AY, y0 + (e - nx), rr.j0, rr.n, rr.w);
+            yt[e - nx] = rr;
+        } else {
+            res_list<K>(AZ, z, rr.j0, rr.n, rr.w);
+            zr = rr;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * lnx; e += blockDim.x) {
+        const int r = e / lnx, jx = e - r * lnx;
+        const ResRun<K>& ry = yt[r];
+        float acc = 0.0f;
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+            if (a >= zr.n) break;
+#pragma unroll
+            for (int b = 0; b < K; ++b) {
+                if (b >= ry.n) break;
+                acc = fmaf(zr.w[a] * ry.w[b], ddst[(int64_t(zr.j0 + a) * lny + (ry.j0 + b)) * lnx + jx], acc);
+            }
+        }
+        U[e] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * nx; e += blockDim.x) {
+        const int r = e / nx, x = e - r * nx;
+        const ResRun<K>& rx = xt[x];
+        const float* u = U + r * lnx + rx.j0;
+        float acc = 0.0f;
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+            if (c >= rx.n) break;
+            acc = fmaf(rx.w[c], u[c], acc);
+        }
+        const int64_t v = (int64_t(z) * ny + (y0 + r)) * nx + x;
+        if (kPrep) {
+            const float w = Wv[v];
+            const float al = acc / (w > eps ? w : eps);
+            aip[v] = make_float2(al, (w > eps) ? al * Iv[v] : 0.0f);
+        } else {
+            dsrc[v] = acc;
+        }
+    }
+}
+
+constexpr int kPlaneSmem = 48 * 1024;
+
+template <bool kPrep, int K>
+static bool launch_adj_plane_k(const float* dd, const ResGeo& G, const float* I, const float* W,
+                               float eps, float* dsrc, float2* aip, cudaStream_t st) {
+    const int nx = G.a[0].n_src, ny = G.a[1].n_src, nz = G.a[2].n_src, lnx = G.a[0].n_dst;
+    const size_t base = sizeof(ResRun<K>) * size_t(nx);
+    if (nz > 65535) return false;
+    if (base + (sizeof(ResRun<K>) + sizeof(float) * lnx) * 32 <= size_t(kPlaneSmem)) {
+        const size_t smem = base + (sizeof(ResRun<K>) + sizeof(float) * lnx) * 32;
+        k_resample_adj_plane<kPrep, K, 32><<<dim3(nz, (ny + 31) / 32), 256, smem, st>>>(dd, G, I, W, eps,
+                                                                                       dsrc, aip);
+        return true;
+    }
+    if (base + (sizeof(ResRun<K>) + sizeof(float) * lnx) * 8 <= size_t(kPlaneSmem)) {
+        const size_t smem = base + (sizeof(ResRun<K>) + sizeof(float) * lnx) * 8;
+        k_resample_adj_plane<kPrep, K, 8><<<dim3(nz, (ny + 7) / 8), 256, smem, st>>>(dd, G, I, W, eps,
+                                                                                   dsrc, aip);
+        return true;
+    }
+    return false;
+}
+
+template <bool kPrep>
+static bool launch_adj_plane(const float* dd, const ResGeo& G, const float* I, const float* W,
+                             float eps, float* dsrc, float2* aip, cudaStream_t st) {
+    if (!res_list_ok(G)) return false;
+    if (res_two_taps(G)) return launch_adj_plane_k<kPrep, 2>(dd, G, I, W, eps, dsrc, aip, st);
+    return launch_adj_plane_k<kPrep, kResList>(dd, G, I, W, eps, dsrc, aip, st);
+}
+
 template <bool kPrep>
 static bool launch_adj_tab(const float* dd, const ResGeo& G, const float* I, const float* W,
                            float eps, float* dsrc, float2* aip, cudaStream_t st) {
@@ -307,7 +410,8 @@ gs_status resample_adj_prep_impl(const float* dlr, int32_t lnz, int32_t lny, int
                                  const float* I, const float* W, int32_t nz, int32_t ny, int32_t nx,
                                  float eps, float2* aip, cudaStream_t st) {
     const ResGeo G = make_res(nz, ny, nx, lnz, lny, lnx);
-    if (!launch_adj_tab<true>(dlr, G, I, W, eps, nullptr, aip, st))
+    if (!launch_adj_plane<true>(dlr, G, I, W, eps, nullptr, aip, st) &&
+        !launch_adj_tab<true>(dlr, G, I, W, eps, nullptr, aip, st))
         k_resample_adj_prep<<<res_blocks(int64_t(nz) * ny * nx), 256, 0, st>>>(dlr, G, I, W, eps, aip);
     return last_launch_status();
 }
@@ -330,7 +434,8 @@ extern "C" gs_status gs_resample_bwd(const float* ddst, int32_t dnz, int32_t dny
     if (!ddst || !dsrc || !dims_ok(snz, sny, snx) || !dims_ok(dnz, dny, dnx)) return GS_ERR_INVALID_ARG;
     const ResGeo G = make_res(snz, sny, snx, dnz, dny, dnx);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (!launch_adj_tab<false>(ddst, G, nullptr, nullptr, 0.f, dsrc, nullptr, st))
+    if (!launch_adj_plane<false>(ddst, G, nullptr, nullptr, 0.f, dsrc, nullptr, st) &&
+        !launch_adj_tab<false>(ddst, G, nullptr, nullptr, 0.f, dsrc, nullptr, st))
         k_resample_bwd<<<res_blocks(int64_t(snz) * sny * snx), 256, 0, st>>>(ddst, G, dsrc);
     return last_launch_status();
 }
