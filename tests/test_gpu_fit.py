@@ -140,3 +140,50 @@ def test_fit_step_overflow_is_a_no_op(deterministic):
         grown.step()
         torch.cuda.synchronize()
         assert torch.equal(grown.params, ref.params)
+
+
+@pytest.mark.parametrize("lr_model", ["zbox", "trilinear"])
+def test_fit_step_full_size_equals_composed_entry_points(lr_model):
+    """At full size, in the bench's configuration (graph-capturable fused step, 8^3 bricks,
+    deterministic), one gs_fit_step equals the composition of the public entry points that
+    the parity tests check against the oracle: render, LR forward model, L1, its adjoint,
+    adjoint render, Adam. Loss, gradient and updated parameters must agree bit for bit."""
+    import torch
+    from paper_2603_09621_gb300 import workloads
+    gs = _gs()
+    cfg = gs.Config(t_act=1)
+    if lr_model == "zbox":
+        w = workloads.phantom_fit()
+        st = gs.FitState(w["params0"], w["lr"], w["grid"], w["s"], cfg)
+    else:
+        w = workloads.phantom_fit_trilinear()
+        st = gs.FitState(w["params0"], w["lr"], w["grid"], 1, cfg, lr_model=gs.GS_LR_TRILINEAR)
+    g = w["grid"]
+    st.step()
+    torch.cuda.synchronize()
+    assert st.check()[0] == 0
+    # composed: every step through its own entry point
+    p0 = w["params0"]
+    I, W, bins, ws = gs.render(p0, g, cfg)
+    if lr_model == "zbox":
+        pred = gs.gs_downsample_fwd(I, w["s"])
+    else:
+        pred = gs.gs_resample_fwd(I, tuple(w["lr"].shape))
+    dpred = torch.empty_like(pred)
+    loss = gs.gs_l1_loss(pred, w["lr"], ws, dpred=dpred)
+    if lr_model == "zbox":
+        dI = gs.gs_downsample_bwd(dpred, g.nz, w["s"])
+    else:
+        dI = gs.gs_resample_bwd(dpred, tuple(I.shape))
+    grad = gs.gs_render_bwd(p0, bins, g, cfg, I, W, dI, ws)
+    params = p0.clone()
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    d_step = torch.zeros((), dtype=torch.int32, device=params.device)
+    gs.gs_adam_step(params, grad, m, v, gs.Adam(), d_step)
+    torch.cuda.synchronize()
+    assert torch.equal(st.d_loss, loss)
+    assert torch.equal(st.grad.view(torch.int32), grad.view(torch.int32))
+    assert torch.equal(st.params.view(torch.int32), params.view(torch.int32))
+    assert torch.equal(st.m.view(torch.int32), m.view(torch.int32))
+    assert int(st.d_step) == int(d_step) == 1
