@@ -66,6 +66,20 @@ __device__ __forceinline__ Rec load_rec(const float4* s) {
     return R;
 }
 
+// The adjoint's copy of a record: quads 0, 1, 2 and 4 (it never reads quad 3, the footprint
+// radius). Slots keep the full 80-byte stride: a 64-byte stride puts the pairs' quads into
+// two bank groups and the shared-memory loads conflict.
+__device__ __forceinline__ Rec load_rec_bwd(const float4* s) {
+    const float4 a = s[0], b = s[1], c = s[2], e = s[4];
+    Rec R;
+    R.mhx = a.x; R.mhy = a.y; R.mhz = a.z; R.mlx = a.w;
+    R.mly = b.x; R.mlz = b.y; R.pyy = b.z; R.p2yz = b.w;
+    R.pzz = c.x; R.c1 = c.y; R.c2 = c.z; R.a = c.w;
+    R.inva = 0.f; R.rho4 = 0.f;
+    R.vr = e.x; R.r = e.y; R.v = e.z;
+    return R;
+}
+
 // Row quantities of the Gaussian for the row through voxel centres (., y, z): the row shadow
 // S and the position dx* of the row minimum. One operation sequence for both kernels.
 __device__ __forceinline__ void row_terms(const Rec& R, float fy, float fz, float& dy, float& dz,
@@ -369,20 +383,36 @@ __global__ void __launch_bounds__(kBwdThreads, 8) k_render_bwd(
         const int64_t i = base + tid;
         const int by = (b_t / G.nbx) % G.nby, bz = b_t / (G.nbx * G.nby);
         const float4* src = rec4 + int64_t(pair_gid[i]) * REC_F4;
-#pragma unroll
-        for (int k = 0; k < REC_F4; ++k) srec[tid][k] = src[k];
-        const unsigned long long m = brick_row_mask(load_rec(srec[tid]), G, by * G.bsy, bz * G.bsz);
+        srec[tid][0] = src[0];
+        srec[tid][1] = src[1];
+        srec[tid][2] = src[2];
+        srec[tid][4] = src[4];
+        const unsigned long long m = brick_row_mask(load_rec_bwd(srec[tid]), G, by * G.bsy, bz * G.bsz);
         smask[tid] = m;
         bucket = 64 - __popcll(static_cast<long long>(m));
         atomicAdd(&hist[bucket], 1);
     }
     __syncthreads();
-    if (tid == 0) {
-        int run = 0;
-        for (int k = 0; k <= 64; ++k) {
-            const int c = hist[k];
-            hist[k] = run;
-            run += c;
+    if (warp == 0) {  // exclusive prefix of the 65 bucket counts: lane l owns buckets 3l..3l+2
+        int c[3], t = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int bk = 3 * lane + k;
+            c[k] = bk <= 64 ? hist[bk] : 0;
+            t += c[k];
+        }
+        int incl = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        int run = incl - t;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int bk = 3 * lane + k;
+            if (bk <= 64) hist[bk] = run;
+            run += c[k];
         }
     }
     // per-voxel factors of the first kBwdStage bricks into shared memory, zero outside the
@@ -412,7 +442,7 @@ __global__ void __launch_bounds__(kBwdThreads, 8) k_render_bwd(
     const int bx = b % G.nbx, by = (b / G.nbx) % G.nby, bz = b / (G.nbx * G.nby);
     const int x0 = bx * BX, y0 = by * G.bsy, z0 = bz * G.bsz;
     const int stage = sstage[lt];
-    const Rec R = load_rec(srec[lt]);
+    const Rec R = load_rec_bwd(srec[lt]);
     const unsigned long long m = smask[lt];
     const bool any = m != 0ull;
     // acc: m1 (x, y, z), m2 (xx, yy, zz, xy, xz, yz), sum alpha g, sum h
