@@ -602,3 +602,94 @@ def test_psnr_ssim_basic():
     y = x + rng.normal(0, 0.1, x.shape)
     assert oracle.ssim3d(x, y) == pytest.approx(oracle.ssim3d(y, x), rel=1e-12)
     assert oracle.ssim3d(x, y) < 0.99
+
+
+# ----------------------------------------------------------- composed pieces: closed forms
+
+def test_rician_closed_forms():
+    """Magnitude of LR + n1 + i n2: |LR| without noise, sqrt(n1^2 + n2^2) on a zero signal,
+    and the 3-4-5 triangle (catches a dropped channel or a missing square root)."""
+    import oracle
+    x = np.array([0.3, -0.7, 0.0])
+    np.testing.assert_array_equal(oracle.rician(x, 0.0, 0.0), np.abs(x))
+    assert oracle.rician(np.array([0.0]), 0.6, 0.8)[0] == pytest.approx(1.0, rel=1e-15)
+    assert oracle.rician(np.array([1.0]), 2.0, 4.0)[0] == pytest.approx(5.0, rel=1e-15)
+
+
+@pytest.mark.parametrize("trilinear_grid", [False, True])
+def test_init_lattice_closed_form(trilinear_grid):
+    """Lattice init on a constant LR volume gives every Gaussian that amplitude; on a volume
+    linear in the LR continuous index it gives the linear function at each centre's LR
+    index (interior centres). Centres sit at cell centres of the field of view, log-scales
+    are log(l / 2), rotations identity, t = logit(t_init). Catches a half-cell shift, a wrong
+    LR spacing or a swapped axis."""
+    import oracle
+    g = oracle.Grid(24, 20, 16, (1.0, 1.5, 2.0), (-3.0, 2.0, 5.0))
+    if trilinear_grid:
+        lr_shape = (7, 9, 10)
+        lg = oracle.resample_grid(g, lr_shape)
+        init = lambda v: oracle.init_lattice_lr(v, g, 480, t_act=1, t_init=0.3)
+    else:
+        s = 2
+        lr_shape = (g.nz // s, g.ny, g.nx)
+        lg = oracle.Grid(g.nx, g.ny, g.nz // s, (g.h[0], g.h[1], g.h[2] * s), g.origin)
+        init = lambda v: oracle.init_lattice(v, g, s, 480, t_act=1, t_init=0.3)
+    n, L = oracle.lattice_dims(g, 480)
+    p = init(np.full(lr_shape, 0.625))
+    np.testing.assert_allclose(p[:, 10], 0.625, rtol=1e-6)
+    ell = [L[a] / n[a] for a in range(3)]
+    ix = np.arange(p.shape[0])
+    idx = [ix % n[0], (ix // n[0]) % n[1], ix // (n[0] * n[1])]
+    for a in range(3):
+        np.testing.assert_allclose(p[:, a], g.origin[a] + (idx[a] + 0.5) * ell[a], rtol=1e-6,
+                                   atol=1e-5)
+        np.testing.assert_allclose(p[:, 3 + a], np.log(ell[a] / 2.0), rtol=1e-6)
+    np.testing.assert_allclose(p[:, 6:10], np.tile([1.0, 0.0, 0.0, 0.0], (p.shape[0], 1)))
+    np.testing.assert_allclose(p[:, 11], np.log(0.3 / 0.7), rtol=1e-6)
+    # linear LR volume: value = 1 + 0.1 i + 0.2 j + 0.3 k at LR index (i, j, k) = (x, y, z)
+    K, J, I = np.meshgrid(np.arange(lr_shape[0]), np.arange(lr_shape[1]), np.arange(lr_shape[2]),
+                          indexing="ij")
+    p = init(1.0 + 0.1 * I + 0.2 * J + 0.3 * K)
+    u = [(p[:, a].astype(np.float64) - lg.origin[a]) / lg.h[a] - 0.5 for a in range(3)]
+    nl = (lr_shape[2], lr_shape[1], lr_shape[0])
+    inner = np.all([(u[a] >= 0) & (u[a] <= nl[a] - 1) for a in range(3)], axis=0)
+    assert inner.sum() > 50
+    ref = 1.0 + 0.1 * u[0] + 0.2 * u[1] + 0.3 * u[2]
+    np.testing.assert_allclose(p[inner, 10], ref[inner], rtol=1e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("lr_model", ["zbox", "trilinear"])
+def test_fit_step_gradient_finite_differences(lr_model):
+    """The composed fitting step's gradient is dL/d(raw params) of the L1 loss through the
+    render and the LR forward model: central differences of that loss (FP64, wide
+    truncation so the render is smooth, a target kept clear of ties) match it. Catches a
+    wrong sign or 1/n in the L1 gradient, or a forward model and adjoint that disagree."""
+    import oracle
+    cfg = oracle.Config(trunc_sigma=10.0, t_act=1)
+    g = oracle.Grid(8, 7, 6, (1.0, 1.2, 0.9), (0.2, 0.1, -0.3))
+    d = inputs.gaussian_cloud(31, 4, (6, 7, 8), scale_range=(0.9, 1.8))
+    t = np.random.default_rng(2).normal(0, 1, 4)
+    p = inputs.assemble_params(d["mu"], d["log_s"], d["q"], d["pd"], t).astype(np.float64)
+    r = oracle.render(p, g, cfg)["I"]
+    if lr_model == "zbox":
+        pred = oracle.downsample(r, 2)
+        fwd = lambda I: oracle.downsample(I, 2)
+    else:
+        pred = oracle.resample(r, (4, 5, 5))
+        fwd = lambda I: oracle.resample(I, (4, 5, 5))
+    rng = np.random.default_rng(5)
+    target = pred + rng.choice([-1.0, 1.0], pred.shape) * rng.uniform(0.05, 0.1, pred.shape)
+    n = p.shape[0]
+    out = oracle.fit_step(p, target, g, 2, cfg, np.zeros((n, 12)), np.zeros((n, 12)), 1,
+                          lr_model=lr_model)
+    loss = lambda q: float(np.abs(fwd(oracle.render(q, g, cfg)["I"]) - target).mean())
+    assert out["loss"] == pytest.approx(loss(p), rel=1e-12)
+    num = np.zeros_like(out["grad"])
+    hstep = 1e-6
+    for i in range(n):
+        for k in range(12):
+            pp, pm = p.copy(), p.copy()
+            pp[i, k] += hstep
+            pm[i, k] -= hstep
+            num[i, k] = (loss(pp) - loss(pm)) / (2 * hstep)
+    np.testing.assert_allclose(out["grad"], num, rtol=1e-5, atol=1e-6 * np.abs(num).max())
