@@ -356,13 +356,16 @@ def run_ours(args, world, rank, local):
         raise RuntimeError(f"fit step status {gs.STATUS.get(rc, rc)} bits {bits}")
 
     # effective / evaluated pairs of the current cloud (outside the timed region)
-    stats = torch.zeros(2, dtype=torch.int64, device=dev)
-    gs.gs_bin_bricks(st.params, g, cfg, st.bins, st.ws)
-    I_tmp, W_tmp = gs.gs_render_fwd(st.bins, g, cfg, stats=stats)
-    torch.cuda.synchronize()
-    n_eff, n_eval = [int(x) for x in stats.cpu()]
-    n_pairs = st.bins.npairs()
-    del I_tmp, W_tmp
+    def pair_stats():
+        stats = torch.zeros(2, dtype=torch.int64, device=dev)
+        gs.gs_bin_bricks(st.params, g, cfg, st.bins, st.ws)
+        I_tmp, W_tmp = gs.gs_render_fwd(st.bins, g, cfg, stats=stats)
+        torch.cuda.synchronize()
+        e, v = [int(x) for x in stats.cpu()]
+        del I_tmp, W_tmp
+        return e, v, st.bins.npairs()
+
+    n_eff, n_eval, n_pairs = pair_stats()
 
     gpu_id = None
     try:
@@ -416,8 +419,13 @@ def run_ours(args, world, rank, local):
     if rc != 0:
         raise RuntimeError(f"fit step status {gs.STATUS.get(rc, rc)} bits {bits}")
 
+    # The fit moves the cloud during the timed steps (the Gaussians grow, so later steps have
+    # more pairs): count the effective pairs again after the last timed step and credit each
+    # step with the mean of the two counts.
+    n_eff_end, n_eval_end, n_pairs_end = pair_stats()
+    n_eff_step = 0.5 * (n_eff + n_eff_end)
     t_dev = sum(step_ms) / 1000.0
-    value, t_max, _ = replica_throughput(float(n_eff) * args.steps, t_dev, world)
+    value, t_max, _ = replica_throughput(n_eff_step * args.steps, t_dev, world)
     ms_step = 1000.0 * t_max / args.steps
 
     # roofline of the dominant render kernel (effective pairs per launch / mean duration)
@@ -429,7 +437,7 @@ def run_ours(args, world, rank, local):
     f_mhz = float(peaks.get("sm_max_mhz", FALLBACK_SM_MHZ))
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_gpairs = n_sm * EX2_PER_CLK_SM * f_mhz * 1e6 / 1e9
-    achieved = n_eff / t_k / 1e9
+    achieved = n_eff_step / t_k / 1e9
     roofline = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak_gpairs,
                 "unit": "Gpair/s", "frac": achieved / peak_gpairs,
                 "traffic": traffic_for(kern),
@@ -440,6 +448,9 @@ def run_ours(args, world, rank, local):
     h_params = w["params0"].cpu().pin_memory()
     h_lr = w["lr"].cpu().pin_memory()
     h_loss = torch.empty((), dtype=torch.float32).pin_memory()
+    # every end-to-end step renders the uploaded initial cloud: count its pairs
+    st.params.copy_(h_params)
+    n_eff_e2e = pair_stats()[0]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_ms = []
     for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
@@ -455,7 +466,7 @@ def run_ours(args, world, rank, local):
             e2e_ms.append(e0.elapsed_time(e1))
     e2e = None
     if e2e_ms:
-        e2e_value, t_e2e, _ = replica_throughput(float(n_eff) * len(e2e_ms),
+        e2e_value, t_e2e, _ = replica_throughput(float(n_eff_e2e) * len(e2e_ms),
                                                  sum(e2e_ms) / 1000.0, world)
         e2e = {"value": e2e_value,
                "unit": "pair-evals/s",
@@ -473,8 +484,11 @@ def run_ours(args, world, rank, local):
             "config": config_dict(args),
             "fit_s_per_scan": FIT_ITERS * ms_step / 1000.0,
             "voxels_per_s": world * nx * ny * nz * args.steps / t_max,
-            "pairs": {"effective": n_eff, "evaluated": n_eval, "brick_pairs": n_pairs,
-                      "culling": n_eff / max(n_eval, 1)},
+            "pairs": {"effective": n_eff_step, "effective_first": n_eff,
+                      "effective_last": n_eff_end, "evaluated": 0.5 * (n_eval + n_eval_end),
+                      "brick_pairs": 0.5 * (n_pairs + n_pairs_end),
+                      "culling": n_eff_step / max(0.5 * (n_eval + n_eval_end), 1),
+                      "counted": "mean of the first and last timed step"},
             "phase_ms": per_phase, "wall_s": wall,
             "roofline": roofline, "clocks": clk, "e2e": e2e, "gpu_launches": launches}
     if world == 1 and not args.no_cpu_baseline and not tri:
