@@ -6,7 +6,8 @@
 //                  bit-exact against the oracle's binning specification), render record.
 //   scan           exclusive scan of per-Gaussian pair counts -> gm_off, total -> d_npairs.
 //   k_capacity     flags GS_STATUS_CAPACITY when the total exceeds the bins' capacity.
-//   k_emit         Gaussian-major pair emission (brick key, owner).
+//   k_emit         Gaussian-major pair emission (brick key, owner), staged per block in shared
+//                  memory so the stores are coalesced.
 //   radix passes   stable LSD radix sort of the brick keys, 8 bits per pass: per-tile digit
 //                  histograms, a digit-major scan, and a stable scatter whose in-tile ranks
 //                  come from warp match masks. Stability keeps ascending Gaussian ids inside
@@ -96,12 +97,20 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const Tin* __restr
     if (threadIdx.x == 0) sums[blockIdx.x] = tot;
 }
 
-// Exclusive scan of each block, offset by the scanned block sums (nullptr: single block).
-template <typename Tin, typename Tout>
+// Exclusive scan of each block, offset by the block sums before it (nullptr: single block).
+// kRaw: offs holds the raw block sums and each block adds up those before its own (few
+// blocks); otherwise offs is already scanned.
+template <typename Tin, typename Tout, bool kRaw>
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(const Tin* __restrict__ in, Tout* out,
                                                             int64_t n, const long long* __restrict__ offs,
                                                             long long* total) {
     __shared__ long long sm[32];
+    long long boff = 0;
+    if (kRaw) {
+        long long o = 0;
+        for (int k = threadIdx.x; k < static_cast<int>(blockIdx.x); k += kScanThreads) o += offs[k];
+        block_exclusive_scan(o, sm, &boff);
+    }
     const int64_t base = int64_t(blockIdx.x) * kScanTile + int64_t(threadIdx.x) * kScanItems;
     long long vals[kScanItems];
     long long s = 0;
@@ -112,7 +121,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const Tin* __restric
     }
     long long tot;
     long long run = block_exclusive_scan(s, sm, &tot);
-    if (offs) run += offs[blockIdx.x];
+    if (kRaw) run += boff;
+    else if (offs) run += offs[blockIdx.x];
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         if (base + i < n) out[base + i] = static_cast<Tout>(run);
@@ -126,7 +136,7 @@ static gs_status scan_rec(const Tin* in, Tout* out, int64_t n, long long* total,
                           int64_t tmp_len, cudaStream_t st) {
     if (n <= 0) return GS_OK;
     if (n <= kScanTile) {
-        k_scan_down<Tin, Tout><<<1, kScanThreads, 0, st>>>(in, out, n, nullptr, total);
+        k_scan_down<Tin, Tout, false><<<1, kScanThreads, 0, st>>>(in, out, n, nullptr, total);
         return last_launch_status();
     }
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
@@ -135,10 +145,16 @@ static gs_status scan_rec(const Tin* in, Tout* out, int64_t n, long long* total,
     k_scan_reduce<Tin><<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, n, sums);
     gs_status s = last_launch_status();
     if (s != GS_OK) return s;
+    if (nb <= kScanTile) {  // few blocks: each adds up the raw sums before its own
+        k_scan_down<Tin, Tout, true><<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, out, n, sums,
+                                                                                     total);
+        return last_launch_status();
+    }
     // Scan the block sums in place (64-bit), recursively.
     s = scan_rec<long long, long long>(sums, sums, nb, nullptr, tmp + nb + 1, tmp_len - nb - 1, st);
     if (s != GS_OK) return s;
-    k_scan_down<Tin, Tout><<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, out, n, sums, total);
+    k_scan_down<Tin, Tout, false><<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, out, n, sums,
+                                                                                  total);
     return last_launch_status();
 }
 
@@ -314,7 +330,7 @@ __global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ pa
     }
     r4[0] = make_float4(mh[0], mh[1], mh[2], ml[0]);
     r4[1] = make_float4(ml[1], ml[2], Pyy, P2yz);
-    r4[2] = make_float4(Pzz, -d1, -d2, am0);
+    r4[2] = make_float4(Pzz, -d1, -d2, nrm[0]);
     // radius of a 4^3 footprint in whitened units: |M d|^2 <= sum_jk |m_j . m_k| (3/2)^2
     float gsum = 0.0f;
 #pragma unroll
@@ -323,7 +339,7 @@ __global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ pa
         for (int k = 0; k < 3; ++k)
             gsum += fabsf(col[j][0] * col[k][0] + col[j][1] * col[k][1] + col[j][2] * col[k][2]);
     const float rho4 = 1.5f * sqrtf(gsum);
-    r4[3] = make_float4(inv_a, rho4, nrm[1], nrm[2]);
+    r4[3] = make_float4(am0, rho4, nrm[1], nrm[2]);
     r4[4] = make_float4(v * r, r, v, 0.0f);
 }
 
@@ -341,25 +357,50 @@ __device__ __forceinline__ int64_t valid_pairs(const int64_t* npairs, int64_t ca
     return (P > capacity || P < 0) ? 0 : P;
 }
 
-__global__ void __launch_bounds__(256) k_emit(const int32_t* __restrict__ brange,
-                                              const int32_t* __restrict__ gm_off, int64_t N, int nbx,
-                                              int nby, const int64_t* __restrict__ npairs,
-                                              int64_t capacity, int32_t* __restrict__ keys,
-                                              int32_t* __restrict__ gm_gid) {
-    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (g >= N) return;
+// One block per 256 consecutive Gaussians, whose pairs fill the contiguous Gaussian-major
+// range [gm_off[g0], gm_off[g0 + 256]). When that range fits kEmitStage entries, each thread
+// writes its pairs into shared memory and the block then stores the range with consecutive
+// threads on consecutive addresses; otherwise threads write their pairs straight to global
+// memory. Both paths write the same values.
+constexpr int kEmitThreads = 256;
+constexpr int kEmitStage = 4096;
+
+__global__ void __launch_bounds__(kEmitThreads) k_emit(const int32_t* __restrict__ brange,
+                                                       const int32_t* __restrict__ gm_off, int64_t N,
+                                                       int nbx, int nby,
+                                                       const int64_t* __restrict__ npairs,
+                                                       int64_t capacity, int32_t* __restrict__ keys,
+                                                       int32_t* __restrict__ gm_gid) {
+    __shared__ int32_t skey[kEmitStage];
+    __shared__ int32_t sgid[kEmitStage];
     if (valid_pairs(npairs, capacity) == 0) return;
-    const int32_t* br = brange + g * 8;
-    if (br[B_CNT] == 0) return;
-    int j = gm_off[g];
-    for (int bz = br[B_LOZ]; bz <= br[B_HIZ]; ++bz)
-        for (int by = br[B_LOY]; by <= br[B_HIY]; ++by)
-            for (int bx = br[B_LOX]; bx <= br[B_HIX]; ++bx) {
-                int b = (bz * nby + by) * nbx + bx;
-                keys[j] = b;
-                gm_gid[j] = static_cast<int32_t>(g);
-                ++j;
-            }
+    const int64_t g0 = int64_t(blockIdx.x) * kEmitThreads;
+    const int64_t g = g0 + threadIdx.x;
+    const int64_t gl = min(g0 + kEmitThreads, N);
+    const int base = gm_off[g0];
+    const int total = gm_off[gl] - base;
+    const bool staged = total <= kEmitStage;
+    int32_t* kdst = staged ? skey : keys + base;
+    int32_t* gdst = staged ? sgid : gm_gid + base;
+    if (g < N) {
+        const int32_t* br = brange + g * 8;
+        if (br[B_CNT] != 0) {
+            int j = gm_off[g] - base;
+            for (int bz = br[B_LOZ]; bz <= br[B_HIZ]; ++bz)
+                for (int by = br[B_LOY]; by <= br[B_HIY]; ++by)
+                    for (int bx = br[B_LOX]; bx <= br[B_HIX]; ++bx) {
+                        kdst[j] = (bz * nby + by) * nbx + bx;
+                        gdst[j] = static_cast<int32_t>(g);
+                        ++j;
+                    }
+        }
+    }
+    if (!staged) return;  // uniform across the block
+    __syncthreads();
+    for (int i = threadIdx.x; i < total; i += kEmitThreads) {
+        keys[base + i] = skey[i];
+        gm_gid[base + i] = sgid[i];
+    }
 }
 
 // ============================================================================ radix sort
@@ -675,7 +716,7 @@ gs_status bin_bricks_impl(const float* params, const gs_grid* grid, const gs_con
     gs_status s = last_launch_status();
     if (s != GS_OK) return s;
     if (N > 0) {
-        k_emit<<<static_cast<unsigned>((N + 255) / 256), 256, 0, st>>>(
+        k_emit<<<static_cast<unsigned>((N + kEmitThreads - 1) / kEmitThreads), kEmitThreads, 0, st>>>(
             bins->brange, bins->gm_off, N, b.nbx, b.nby, bins->d_npairs, cap, ws.keys0, ws.gm_gid);
         s = last_launch_status();
         if (s != GS_OK) return s;

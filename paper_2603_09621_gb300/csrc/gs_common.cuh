@@ -17,12 +17,13 @@ namespace gs {
 // at large coordinates.
 // The exponent q = (log2 e / 2) d^T Sigma'^{-1} d (Sigma' the covariance in voxel units, the
 // Gaussian kernel is 2^-q) is stored by completing the square along x:
-//     q(dx, dy, dz) = S(dy, dz) + a (dx - dx*(dy, dz))^2,
+//     q(dx, dy, dz) = S(dy, dz) + (sa (dx - dx*(dy, dz)))^2,
 //     S(dy, dz) = Pyy dy^2 + P2yz dy dz + Pzz dz^2   (the minimum of q along the x-row),
 //     dx*(dy, dz) = c1 dy + c2 dz                      (where that minimum is reached).
 // With M = sqrt(log2 e / 2) diag(1/s) R^T H (columns m0, m1, m2, the whitened steps of one
-// voxel along x, y, z): a = |m0|^2, c_j = -(m_j . m0) / a, and S is the Gram form of m1, m2
-// with their components along m0 removed. Every term of this form has the size of q itself
+// voxel along x, y, z): sa = |m0| (the whitened length of one voxel step along x),
+// c_j = -(m_j . m0) / |m0|^2, and S is the Gram form of m1, m2 with their components along m0
+// removed. Every term of this form has the size of q itself
 // for voxels inside the ellipsoid, so FP32 keeps its accuracy for strongly anisotropic
 // Gaussians, and the value at a voxel depends only on the voxel and the Gaussian.
 // rho4 bounds |M (p - c)| over a 4 x 4 x 4 voxel footprint around its centre c:
@@ -32,7 +33,7 @@ enum RecField : int {
     R_MLX = 3, R_MLY = 4, R_MLZ = 5,        // mu' tail
     R_PYY = 6, R_P2YZ = 7, R_PZZ = 8,       // row shadow S
     R_C1 = 9, R_C2 = 10,                    // dx* = c1 dy + c2 dz
-    R_A = 11, R_INVA = 12,                  // a = |m0|^2 and 1 / a
+    R_SA = 11, R_A = 12,                    // sa = |m0| and a = |m0|^2
     R_RHO4 = 13,                            // footprint radius (see above)
     R_N1 = 14, R_N2 = 15,                   // |m1|, |m2| (unused by the kernels)
     R_VR = 16,                              // v * r
@@ -222,6 +223,13 @@ __device__ __forceinline__ float exp_cw(float x) {
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Approximate square root (sqrt.approx, flush-to-zero); for bounds that carry a margin.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 

@@ -2,7 +2,7 @@
 // (Sec. 3.3: "each handled by one CUDA thread block"; the brick's Gaussians are staged into
 // shared memory and no depth order is needed).
 //
-// Exponent of a pair (voxel p, Gaussian i) in voxel units: q = S(dy, dz) + a (dx - dx*)^2
+// Exponent of a pair (voxel p, Gaussian i) in voxel units: q = S(dy, dz) + (sa (dx - dx*))^2
 // (record layout in gs_common.cuh), the Gaussian kernel is 2^-q and the pair contributes
 // only where q <= T = (log2 e / 2) trunc_sigma^2. q is computed by the same operation sequence
 // in both kernels from the voxel's global index and the Gaussian alone, so forward and
@@ -52,7 +52,7 @@ struct RenderGeo {
 
 struct Rec {
     float mhx, mhy, mhz, mlx, mly, mlz;
-    float pyy, p2yz, pzz, c1, c2, a, inva, rho4, vr, r, v;
+    float pyy, p2yz, pzz, c1, c2, sa, rho4, vr, r, v;
 };
 
 __device__ __forceinline__ Rec load_rec(const float4* s) {
@@ -60,8 +60,8 @@ __device__ __forceinline__ Rec load_rec(const float4* s) {
     Rec R;
     R.mhx = a.x; R.mhy = a.y; R.mhz = a.z; R.mlx = a.w;
     R.mly = b.x; R.mlz = b.y; R.pyy = b.z; R.p2yz = b.w;
-    R.pzz = c.x; R.c1 = c.y; R.c2 = c.z; R.a = c.w;
-    R.inva = d.x; R.rho4 = d.y;
+    R.pzz = c.x; R.c1 = c.y; R.c2 = c.z; R.sa = c.w;
+    R.rho4 = d.y;
     R.vr = e.x; R.r = e.y; R.v = e.z;
     return R;
 }
@@ -74,8 +74,8 @@ __device__ __forceinline__ Rec load_rec_bwd(const float4* s) {
     Rec R;
     R.mhx = a.x; R.mhy = a.y; R.mhz = a.z; R.mlx = a.w;
     R.mly = b.x; R.mlz = b.y; R.pyy = b.z; R.p2yz = b.w;
-    R.pzz = c.x; R.c1 = c.y; R.c2 = c.z; R.a = c.w;
-    R.inva = 0.f; R.rho4 = 0.f;
+    R.pzz = c.x; R.c1 = c.y; R.c2 = c.z; R.sa = c.w;
+    R.rho4 = 0.f;
     R.vr = e.x; R.r = e.y; R.v = e.z;
     return R;
 }
@@ -86,35 +86,41 @@ __device__ __forceinline__ void row_terms(const Rec& R, float fy, float fz, floa
                                           float& S, float& dxs) {
     dy = (fy - R.mhy) - R.mly;
     dz = (fz - R.mhz) - R.mlz;
-    S = fmaf(R.pyy * dy, dy, fmaf(R.p2yz * dy, dz, R.pzz * dz * dz));
+    S = fmaf(dy, fmaf(R.pyy, dy, R.p2yz * dz), R.pzz * dz * dz);
     dxs = fmaf(R.c1, dy, R.c2 * dz);
 }
 
-// x offset of voxel x from the mean, u = ux_base(R, x & ~3) + (x & 3): the same operation
-// sequence in every kernel, so forward and adjoint agree on every inclusion q <= T.
+// x offset of voxel x from the mean, u = ux_base(R, x & ~3) + (x & 3).
 __device__ __forceinline__ float ux_base(const Rec& R, int x4) {
     return (float(x4) - R.mhx) - R.mlx;
 }
 
-// q at x offset u, given the row terms.
-__device__ __forceinline__ float q_of_u(const Rec& R, float u, float S, float dxs) {
-    const float t = u - dxs;
-    return fmaf(R.a * t, t, S);
+// Scaled x offset of voxel x = x4 + k (x4 = x & ~3) from the row minimum, tq = sa (u - dx*),
+// taken as tq = fma(k, sa, tq0) from the group's tq0 = sa (ux_base(R, x4) - dx*); then
+// q = fma(tq, tq, S). Every kernel uses this operation sequence, so forward and adjoint agree
+// on every inclusion q <= T.
+__device__ __forceinline__ float tq_base(const Rec& R, int x4, float dxs) {
+    return R.sa * (ux_base(R, x4) - dxs);
+}
+
+__device__ __forceinline__ float q_of_k(const Rec& R, float tq0, int k, float S) {
+    const float tq = (k == 0) ? tq0 : fmaf(float(k), R.sa, tq0);
+    return fmaf(tq, tq, S);
 }
 
 // q at the point with (fractional) x index fx, given the row terms (footprint culling).
-__device__ __forceinline__ float q_at(const Rec& R, float fx, float S, float dxs, float& u) {
-    u = (fx - R.mhx) - R.mlx;
-    return q_of_u(R, u, S, dxs);
+__device__ __forceinline__ float q_at(const Rec& R, float fx, float S, float dxs) {
+    const float tq = R.sa * (((fx - R.mhx) - R.mlx) - dxs);
+    return fmaf(tq, tq, S);
 }
 
 // Footprint cull: may the Gaussian reach a voxel centre within 3/2 of (cx, cy, cz) per axis?
 __device__ __forceinline__ bool foot_hit(const float4* s, float cx, float cy, float cz,
                                          float sqrtTcull) {
     const Rec R = load_rec(s);
-    float dy, dz, S, dxs, u;
+    float dy, dz, S, dxs;
     row_terms(R, cy, cz, dy, dz, S, dxs);
-    const float qc = q_at(R, cx, S, dxs, u);
+    const float qc = q_at(R, cx, S, dxs);
     return sqrtf(fmaxf(qc, 0.0f)) - R.rho4 <= sqrtTcull;
 }
 
@@ -160,22 +166,24 @@ __global__ void __launch_bounds__(128, 14) k_render_fwd(const int32_t* __restric
             const bool hit = foot_ok && (k < cnt) && foot_hit(srec[k], cx, cy, cz, G.sqrtTcull);
             const unsigned bal = __ballot_sync(0xffffffffu, hit);
             unsigned mask = (bal & half_sel) >> (lane & 16);
-            // each half takes its hits in ascending Gaussian id (per voxel the order of Eq. 3)
-            while (__any_sync(0xffffffffu, mask != 0u)) {
-                if (mask) {
+            // each half takes its hits in ascending Gaussian id (per voxel the order of Eq. 3);
+            // the halves run their own trip counts and meet again at the next ballot
+            while (mask) {
+                {
                     const int kk = k0 + __ffs(mask) - 1;
                     mask &= mask - 1;
                     const Rec R = load_rec(srec[kk]);
                     float dy, dz, Sr, dxs;
                     row_terms(R, fy, fz, dy, dz, Sr, dxs);
-                    const float ux = ux_base(R, ox);
+                    const float tq0 = tq_base(R, ox, dxs);
 #pragma unroll
                     for (int xi = 0; xi < 4; ++xi) {
-                        const float q = q_of_u(R, ux + float(xi), Sr, dxs);
-                        float g = ex2_approx(-q);
-                        g = (q <= G.T) ? g : 0.0f;
-                        S[xi] = fmaf(R.vr, g, S[xi]);
-                        Wt[xi] = fmaf(R.r, g, Wt[xi]);
+                        const float q = q_of_k(R, tq0, xi, Sr);
+                        if (q <= G.T) {
+                            const float g = ex2_approx(-q);
+                            S[xi] = fmaf(R.vr, g, S[xi]);
+                            Wt[xi] = fmaf(R.r, g, Wt[xi]);
+                        }
                         if (kStats) {
                             n_eff += (y < G.ny && z < G.nz && ox + xi < G.nx && q <= G.T) ? 1 : 0;
                             n_eval += 1;
@@ -218,24 +226,26 @@ __global__ void __launch_bounds__(128, 14) k_render_fwd(const int32_t* __restric
 // ------------------------------------------------------------------------ adjoint
 
 // Rows of the brick (index rz * bsy + ry) that the Gaussian may reach: per z-row the row
-// shadow S(dy, dz) <= Tcull is a quadratic in dy, solved for its y-interval (padded).
+// shadow S(dy, dz) <= Tcull holds on the y-interval yc(dz) +- hw(dz), with
+// yc = mu_y - (P2yz / 2 Pyy) dz and hw^2 = Tcull / Pyy - c3 dz^2,
+// c3 = (Pzz - P2yz^2 / 4 Pyy) / Pyy (the interval is padded; Tcull carries a 1 % margin).
 __device__ __forceinline__ unsigned long long brick_row_mask(const Rec& R, const RenderGeo& G,
                                                              int y0, int z0) {
     unsigned long long mask = 0;
     const float mu_y = R.mhy + R.mly;
-    const float inv2a = 0.5f / R.pyy;
+    const float ipyy = __fdividef(1.0f, R.pyy);
+    const float k1 = -0.5f * (R.p2yz * ipyy);
+    const float c3 = (R.pzz - 0.25f * R.p2yz * (R.p2yz * ipyy)) * ipyy;
+    const float h0 = G.Tcull * ipyy;
+    const float pad = 1e-3f + 1e-5f * fabsf(mu_y);
     for (int rz = 0; rz < G.bsz; ++rz) {
         const float dz = (float(z0 + rz) - R.mhz) - R.mlz;
-        const float bq = R.p2yz * dz;
-        const float cq = R.pzz * dz * dz - G.Tcull;
-        const float disc = bq * bq - 4.0f * R.pyy * cq;
-        if (!(disc >= 0.0f)) continue;
-        const float sq = sqrtf(disc);
-        const float ylo = mu_y + (-bq - sq) * inv2a;
-        const float yhi = mu_y + (-bq + sq) * inv2a;
-        const float pad = 1e-3f + 1e-5f * fabsf(mu_y);
-        int ia = static_cast<int>(ceilf(fmaxf(ylo - pad, float(y0) - 1.0f))) - y0;
-        int ib = static_cast<int>(floorf(fminf(yhi + pad, float(y0 + G.bsy)))) - y0;
+        const float hw2 = fmaf(-c3 * dz, dz, h0);
+        if (!(hw2 >= 0.0f)) continue;
+        const float hw = sqrt_approx(hw2) + pad;
+        const float yc = fmaf(k1, dz, mu_y);
+        int ia = static_cast<int>(ceilf(fmaxf(yc - hw, float(y0) - 1.0f))) - y0;
+        int ib = static_cast<int>(floorf(fminf(yc + hw, float(y0 + G.bsy)))) - y0;
         ia = max(ia, 0);
         ib = min(ib, G.bsy - 1);
         if (ia > ib) continue;
@@ -279,6 +289,9 @@ __device__ __forceinline__ void adjoint_rows(const Rec& R, unsigned long long m,
         const int y = y0 + (r & G.bsy_mask), z = z0 + (r >> G.bsy_shift);
         float dy, dz, S, dxs;
         row_terms(R, float(y), float(z), dy, dz, S, dxs);
+        float tq4[BX / 4];
+#pragma unroll
+        for (int j = 0; j < BX / 4; ++j) tq4[j] = tq_base(R, x0 + 4 * j, dxs);
         // (alpha, alpha I') of the row's voxels; zero outside the grid
         float2 av[BX];
         if (kStaged) {
@@ -310,7 +323,7 @@ __device__ __forceinline__ void adjoint_rows(const Rec& R, unsigned long long m,
 #pragma unroll
         for (int xb = 0; xb < BX; ++xb) {
             const float u = ux4[xb >> 2] + float(xb & 3);
-            const float q = q_of_u(R, u, S, dxs);
+            const float q = q_of_k(R, tq4[xb >> 2], xb & 3, S);
             const float g = (q <= G.T) ? ex2_approx(-q) : 0.0f;
             const float h = fmaf(R.v, av[xb].x, -av[xb].y) * g;
             acc[9] = fmaf(av[xb].x, g, acc[9]);
