@@ -4,8 +4,9 @@
 // Pipeline of gs_bin_bricks (all asynchronous on one stream):
 //   k_preprocess   one thread per Gaussian: validity, FP32 brick range (fixed operation order,
 //                  bit-exact against the oracle's binning specification), render record.
-//   scan           exclusive scan of per-Gaussian pair counts -> gm_off, total -> d_npairs.
-//   k_capacity     flags GS_STATUS_CAPACITY when the total exceeds the bins' capacity.
+//   scan           exclusive scan of per-Gaussian pair counts -> gm_off; its last thread stores
+//                  the total as d_npairs and flags GS_STATUS_CAPACITY when it exceeds the
+//                  bins' capacity.
 //   k_emit         Gaussian-major pair emission (brick key, owner), staged per block in shared
 //                  memory so the stores are coalesced.
 //   radix passes   stable LSD radix sort of the brick keys, 8 bits per pass: per-tile digit
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const Tin* __restr
 template <typename Tin, typename Tout, bool kRaw>
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(const Tin* __restrict__ in, Tout* out,
                                                             int64_t n, const long long* __restrict__ offs,
-                                                            long long* total) {
+                                                            long long* total, CapCheck cc) {
     __shared__ long long sm[32];
     long long boff = 0;
     if (kRaw) {
@@ -128,15 +129,21 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const Tin* __restric
         if (base + i < n) out[base + i] = static_cast<Tout>(run);
         run += vals[i];
     }
-    if (total && blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) *total = run;
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) {
+        if (total) *total = run;
+        if (cc.npairs) {
+            *cc.npairs = run;
+            if (run > cc.capacity) atomicOr(cc.status, GS_STATUS_CAPACITY);
+        }
+    }
 }
 
 template <typename Tin, typename Tout>
 static gs_status scan_rec(const Tin* in, Tout* out, int64_t n, long long* total, long long* tmp,
-                          int64_t tmp_len, cudaStream_t st) {
+                          int64_t tmp_len, cudaStream_t st, CapCheck cc) {
     if (n <= 0) return GS_OK;
     if (n <= kScanTile) {
-        k_scan_down<Tin, Tout, false><<<1, kScanThreads, 0, st>>>(in, out, n, nullptr, total);
+        k_scan_down<Tin, Tout, false><<<1, kScanThreads, 0, st>>>(in, out, n, nullptr, total, cc);
         return last_launch_status();
     }
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
@@ -147,20 +154,21 @@ static gs_status scan_rec(const Tin* in, Tout* out, int64_t n, long long* total,
     if (s != GS_OK) return s;
     if (nb <= kScanTile) {  // few blocks: each adds up the raw sums before its own
         k_scan_down<Tin, Tout, true><<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, out, n, sums,
-                                                                                     total);
+                                                                                     total, cc);
         return last_launch_status();
     }
     // Scan the block sums in place (64-bit), recursively.
-    s = scan_rec<long long, long long>(sums, sums, nb, nullptr, tmp + nb + 1, tmp_len - nb - 1, st);
+    s = scan_rec<long long, long long>(sums, sums, nb, nullptr, tmp + nb + 1, tmp_len - nb - 1, st,
+                                       CapCheck{});
     if (s != GS_OK) return s;
     k_scan_down<Tin, Tout, false><<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, out, n, sums,
-                                                                                  total);
+                                                                                  total, cc);
     return last_launch_status();
 }
 
 gs_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, long long* total,
-                             long long* tmp, int64_t tmp_len, cudaStream_t stream) {
-    return scan_rec<int32_t, int32_t>(in, out, n, total, tmp, tmp_len, stream);
+                             long long* tmp, int64_t tmp_len, cudaStream_t stream, CapCheck cc) {
+    return scan_rec<int32_t, int32_t>(in, out, n, total, tmp, tmp_len, stream, cc);
 }
 
 // ============================================================================ preprocess
@@ -182,6 +190,7 @@ __global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ pa
                                                     int32_t* __restrict__ gm_cnt,
                                                     int32_t* __restrict__ status) {
     const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g == 0) gm_cnt[N] = 0;  // sentinel: gm_off has N + 1 entries
     if (g >= N) return;
     const float4* p4 = reinterpret_cast<const float4*>(params + g * 12);
     float4 a0 = p4[0], a1 = p4[1], a2 = p4[2];
@@ -703,18 +712,20 @@ gs_status bin_bricks_impl(const float* params, const gs_grid* grid, const gs_con
                                          bins->d_status);
         gs_status s = last_launch_status();
         if (s != GS_OK) return s;
-        // gm_off = exclusive scan of counts (N + 1 entries; gm_cnt[N] = 0 sentinel).
-        if (cudaMemsetAsync(ws.gm_cnt + N, 0, sizeof(int32_t), st) != cudaSuccess) return GS_ERR_CUDA;
+        // gm_off = exclusive scan of counts (N + 1 entries; gm_cnt[N] = 0 sentinel); the scan's
+        // last thread also stores the total as d_npairs and flags an overflow of the capacity.
+        const CapCheck cc{cap, bins->d_npairs, bins->d_status};
         s = exclusive_scan_i32(ws.gm_cnt, bins->gm_off, N + 1, total, ws.scan_tmp,
-                               ws.scan_tmp_len - 1, st);
+                               ws.scan_tmp_len - 1, st, cc);
         if (s != GS_OK) return s;
     } else {
         if (cudaMemsetAsync(total, 0, sizeof(long long), st) != cudaSuccess) return GS_ERR_CUDA;
         if (cudaMemsetAsync(bins->gm_off, 0, sizeof(int32_t), st) != cudaSuccess) return GS_ERR_CUDA;
+        k_capacity<<<1, 1, 0, st>>>(total, cap, bins->d_npairs, bins->d_status);
+        const gs_status s = last_launch_status();
+        if (s != GS_OK) return s;
     }
-    k_capacity<<<1, 1, 0, st>>>(total, cap, bins->d_npairs, bins->d_status);
-    gs_status s = last_launch_status();
-    if (s != GS_OK) return s;
+    gs_status s = GS_OK;
     if (N > 0) {
         k_emit<<<static_cast<unsigned>((N + kEmitThreads - 1) / kEmitThreads), kEmitThreads, 0, st>>>(
             bins->brange, bins->gm_off, N, b.nbx, b.nby, bins->d_npairs, cap, ws.keys0, ws.gm_gid);

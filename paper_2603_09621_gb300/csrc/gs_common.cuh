@@ -170,10 +170,19 @@ inline gs_status last_launch_status() {
     return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
+// Optional check of a scan's grand total against a pair capacity: with npairs set, the total
+// is stored there and GS_STATUS_CAPACITY is or-ed into *status when it exceeds capacity.
+struct CapCheck {
+    int64_t capacity = 0;
+    int64_t* npairs = nullptr;
+    int32_t* status = nullptr;
+};
+
 // Device-wide exclusive scan of int32 values (n <= kMaxCapacity + 1); 64-bit accumulation.
 // out may alias in. If total != nullptr, the grand total is written there (device int64).
 gs_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, long long* total,
-                             long long* tmp, int64_t tmp_len, cudaStream_t stream);
+                             long long* tmp, int64_t tmp_len, cudaStream_t stream,
+                             CapCheck cc = CapCheck{});
 
 // Parameter chain + render-space gradient -> raw-parameter gradient (gs_param.cu).
 gs_status launch_param_bwd(const float* params, const float* gacc, int64_t n,

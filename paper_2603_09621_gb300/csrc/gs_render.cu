@@ -115,13 +115,14 @@ __device__ __forceinline__ float q_at(const Rec& R, float fx, float S, float dxs
 }
 
 // Footprint cull: may the Gaussian reach a voxel centre within 3/2 of (cx, cy, cz) per axis?
+// (An approximate square root suffices: Tcull carries a 1 % margin over T.)
 __device__ __forceinline__ bool foot_hit(const float4* s, float cx, float cy, float cz,
                                          float sqrtTcull) {
     const Rec R = load_rec(s);
     float dy, dz, S, dxs;
     row_terms(R, cy, cz, dy, dz, S, dxs);
     const float qc = q_at(R, cx, S, dxs);
-    return sqrtf(fmaxf(qc, 0.0f)) - R.rho4 <= sqrtTcull;
+    return sqrt_approx(fmaxf(qc, 0.0f)) - R.rho4 <= sqrtTcull;
 }
 
 // ------------------------------------------------------------------------ forward
@@ -436,6 +437,17 @@ __global__ void __launch_bounds__(kBwdThreads, 8) k_render_bwd(
         const int b = sbrick[k];
         const int x0 = (b % G.nbx) * BX, y0 = ((b / G.nbx) % G.nby) * G.bsy,
                   z0 = (b / (G.nbx * G.nby)) * G.bsz;
+        if (x0 + BX <= G.nx && y0 + G.bsy <= G.ny && z0 + G.bsz <= G.nz && (G.nx & 1) == 0) {
+            // brick inside the grid, rows 16-byte aligned: one float4 (two voxels) per load
+            constexpr int kPerRow = BX / 2;
+            float4* dst = reinterpret_cast<float4*>(&sfac[k][0]);
+            for (int e = tid; e < bvox / 2; e += kBwdThreads) {
+                const int r = e / kPerRow, c = e - r * kPerRow;
+                const int y = y0 + (r & G.bsy_mask), z = z0 + (r >> G.bsy_shift);
+                dst[e] = *reinterpret_cast<const float4*>(aip + (int64_t(z) * G.ny + y) * G.nx + x0 + 2 * c);
+            }
+            continue;
+        }
         for (int e = tid; e < bvox; e += kBwdThreads) {
             const int xb = e % BX, r = e / BX;
             const int x = x0 + xb, y = y0 + (r & G.bsy_mask), z = z0 + (r >> G.bsy_shift);
