@@ -177,11 +177,17 @@ struct GridF {
     int n[3];
     float h[3];
     float o[3];
-    double hd[3];
-    double od[3];
+    float ih[3];  // 1 / h
     int b[3];
     int nb[3];
 };
+
+// Error-free sum (Knuth): s + e == a + b exactly, s = fl(a + b).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
 
 __global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ params, int64_t N, GridF G,
                                                     float trunc_sigma, int signal_mode, int a_act,
@@ -320,12 +326,21 @@ __global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ pa
     const float Pyy = n1[0] * n1[0] + n1[1] * n1[1] + n1[2] * n1[2];
     const float Pzz = n2[0] * n2[0] + n2[1] * n2[1] + n2[2] * n2[2];
     const float P2yz = 2.0f * (n1[0] * n2[0] + n1[1] * n2[1] + n1[2] * n2[2]);
+    // Mean in voxel-index space m = (mu - o) / h - 1/2 as a float head + tail, in double-float
+    // arithmetic (Knuth's error-free two-sum; the quotient's remainder from one FMA), so that
+    // m = mh + ml to about 2^-46 relative and d = (i - mh) - ml keeps one rounding at any
+    // coordinate. (FP64 runs at 1/64 of the FP32 rate here.)
     float mh[3], ml[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        double m = (static_cast<double>(p[k]) - G.od[k]) / G.hd[k] - 0.5;
-        mh[k] = static_cast<float>(m);
-        ml[k] = static_cast<float>(m - static_cast<double>(mh[k]));
+        float dh, dl;
+        two_sum(p[k], -G.o[k], dh, dl);           // mu - o exactly
+        const float qh = __fdiv_rn(dh, G.h[k]);   // correctly rounded: the remainder is exact
+        const float rem = fmaf(-qh, G.h[k], dh);
+        const float ql = __fmul_rn(__fadd_rn(rem, dl), G.ih[k]);
+        float sh, sl;
+        two_sum(qh, -0.5f, sh, sl);
+        two_sum(sh, __fadd_rn(sl, ql), mh[k], ml[k]);
     }
     float A = a_act ? sigmoidf_(p[10]) : p[10];
     float T = t_act ? sigmoidf_(p[11]) : p[11];
@@ -697,8 +712,7 @@ gs_status bin_bricks_impl(const float* params, const gs_grid* grid, const gs_con
     for (int k = 0; k < 3; ++k) {
         G.h[k] = grid->h[k];
         G.o[k] = grid->origin[k];
-        G.hd[k] = grid->h[k];
-        G.od[k] = grid->origin[k];
+        G.ih[k] = 1.0f / grid->h[k];
     }
     G.b[0] = b.bx; G.b[1] = b.by; G.b[2] = b.bz;
     G.nb[0] = b.nbx; G.nb[1] = b.nby; G.nb[2] = b.nbz;

@@ -13,8 +13,8 @@ namespace gs {
 // Per-Gaussian record (20 floats = 5 float4, 80 bytes) written by the preprocess kernel and
 // staged into shared memory by the render kernels. Coordinates are voxel-index space: voxel
 // (i, j, k) sits at (i, j, k). The mean mu' = (mu - o) / h - 1/2 is a float head plus a
-// float tail computed in FP64, so d = (i - head) - tail is accurate to one rounding of d even
-// at large coordinates.
+// float tail (double-float arithmetic), so d = (i - head) - tail is accurate to one rounding
+// of d even at large coordinates.
 // The exponent q = (log2 e / 2) d^T Sigma'^{-1} d (Sigma' the covariance in voxel units, the
 // Gaussian kernel is 2^-q) is stored by completing the square along x:
 //     q(dx, dy, dz) = S(dy, dz) + (sa (dx - dx*(dy, dz)))^2,
