@@ -419,9 +419,9 @@ def run_ours(args, world, rank, local):
     if rc != 0:
         raise RuntimeError(f"fit step status {gs.STATUS.get(rc, rc)} bits {bits}")
 
-    # The fit moves the cloud during the timed steps (the Gaussians grow, so later steps have
-    # more pairs): count the effective pairs again after the last timed step and credit each
-    # step with the mean of the two counts.
+    # The fit moves the cloud during the timed steps (its effective pairs change as the
+    # Gaussians shrink and grow): count the effective pairs again after the last timed step
+    # and credit each step with the mean of the two counts.
     n_eff_end, n_eval_end, n_pairs_end = pair_stats()
     n_eff_step = 0.5 * (n_eff + n_eff_end)
     t_dev = sum(step_ms) / 1000.0

@@ -87,6 +87,7 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* smem, T* total) {
 template <typename Tin>
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const Tin* __restrict__ in, int64_t n,
                                                               long long* __restrict__ sums) {
+    pdl_enter();
     __shared__ long long sm[32];
     const int64_t base = int64_t(blockIdx.x) * kScanTile + int64_t(threadIdx.x) * kScanItems;
     long long s = 0;
@@ -105,6 +106,7 @@ template <typename Tin, typename Tout, bool kRaw>
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(const Tin* __restrict__ in, Tout* out,
                                                             int64_t n, const long long* __restrict__ offs,
                                                             long long* total, CapCheck cc) {
+    pdl_enter();
     __shared__ long long sm[32];
     long long boff = 0;
     if (kRaw) {
@@ -143,26 +145,28 @@ static gs_status scan_rec(const Tin* in, Tout* out, int64_t n, long long* total,
                           int64_t tmp_len, cudaStream_t st, CapCheck cc) {
     if (n <= 0) return GS_OK;
     if (n <= kScanTile) {
-        k_scan_down<Tin, Tout, false><<<1, kScanThreads, 0, st>>>(in, out, n, nullptr, total, cc);
+        launch_k(k_scan_down<Tin, Tout, false>, dim3(1), dim3(kScanThreads), 0, st, in, out, n,
+            nullptr, total, cc);
         return last_launch_status();
     }
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
     if (nb + 1 > tmp_len) return GS_ERR_WORKSPACE;
     long long* sums = tmp;
-    k_scan_reduce<Tin><<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, n, sums);
+    launch_k(k_scan_reduce<Tin>, dim3(static_cast<unsigned>(nb)), dim3(kScanThreads), 0, st, in, n,
+        sums);
     gs_status s = last_launch_status();
     if (s != GS_OK) return s;
     if (nb <= kScanTile) {  // few blocks: each adds up the raw sums before its own
-        k_scan_down<Tin, Tout, true><<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, out, n, sums,
-                                                                                     total, cc);
+        launch_k(k_scan_down<Tin, Tout, true>, dim3(static_cast<unsigned>(nb)), dim3(kScanThreads),
+            0, st, in, out, n, sums, total, cc);
         return last_launch_status();
     }
     // Scan the block sums in place (64-bit), recursively.
     s = scan_rec<long long, long long>(sums, sums, nb, nullptr, tmp + nb + 1, tmp_len - nb - 1, st,
                                        CapCheck{});
     if (s != GS_OK) return s;
-    k_scan_down<Tin, Tout, false><<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, out, n, sums,
-                                                                                  total, cc);
+    launch_k(k_scan_down<Tin, Tout, false>, dim3(static_cast<unsigned>(nb)), dim3(kScanThreads), 0,
+        st, in, out, n, sums, total, cc);
     return last_launch_status();
 }
 
@@ -195,6 +199,7 @@ __global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ pa
                                                     int32_t* __restrict__ brange,
                                                     int32_t* __restrict__ gm_cnt,
                                                     int32_t* __restrict__ status) {
+    pdl_enter();
     const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g == 0) gm_cnt[N] = 0;  // sentinel: gm_off has N + 1 entries
     if (g >= N) return;
@@ -371,6 +376,7 @@ __global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ pa
 
 __global__ void k_capacity(const long long* __restrict__ total, int64_t capacity,
                            int64_t* __restrict__ npairs, int32_t* __restrict__ status) {
+    pdl_enter();
     long long t = *total;
     *npairs = t;
     if (t > capacity) atomicOr(status, GS_STATUS_CAPACITY);
@@ -395,6 +401,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const int32_t* __restrict
                                                        const int64_t* __restrict__ npairs,
                                                        int64_t capacity, int32_t* __restrict__ keys,
                                                        int32_t* __restrict__ gm_gid) {
+    pdl_enter();
     __shared__ int32_t skey[kEmitStage];
     __shared__ int32_t sgid[kEmitStage];
     if (valid_pairs(npairs, capacity) == 0) return;
@@ -433,6 +440,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const int32_t* __re
                                                             const int64_t* __restrict__ npairs,
                                                             int64_t capacity, int shift, int n_tiles,
                                                             int32_t* __restrict__ hist) {
+    pdl_enter();
     __shared__ int cnt[kRadix];
     const int64_t P = valid_pairs(npairs, capacity);
     const int64_t base = int64_t(blockIdx.x) * kSortTile;
@@ -465,6 +473,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out,
     const int32_t* __restrict__ hist_off, const int64_t* __restrict__ npairs, int64_t capacity,
     int shift, int n_tiles) {
+    pdl_enter();
     constexpr int kWarps = kSortThreads / 32;
     constexpr int kPerWarp = kSortTile / kWarps;
     constexpr int kRounds = kPerWarp / 32;
@@ -560,6 +569,7 @@ __global__ void __launch_bounds__(256) k_finalize(const int32_t* __restrict__ ke
                                                   int32_t* __restrict__ pair_gid,
                                                   int32_t* __restrict__ pair_brick,
                                                   int32_t* __restrict__ brick_off) {
+    pdl_enter();
     const int64_t P = valid_pairs(npairs, capacity);
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i <= P;
          i += int64_t(gridDim.x) * blockDim.x) {
@@ -721,9 +731,9 @@ gs_status bin_bricks_impl(const float* params, const gs_grid* grid, const gs_con
     long long* total = ws.scan_tmp + ws.scan_tmp_len - 1;
     if (N > 0) {
         const unsigned gb = static_cast<unsigned>((N + 255) / 256);
-        k_preprocess<<<gb, 256, 0, st>>>(params, N, G, cfg->trunc_sigma, cfg->signal_mode,
-                                         cfg->a_act, cfg->t_act, bins->rec, bins->brange, ws.gm_cnt,
-                                         bins->d_status);
+        launch_k(k_preprocess, dim3(gb), dim3(256), 0, st, params, N, G, cfg->trunc_sigma,
+            cfg->signal_mode, cfg->a_act, cfg->t_act, bins->rec, bins->brange, ws.gm_cnt,
+            bins->d_status);
         gs_status s = last_launch_status();
         if (s != GS_OK) return s;
         // gm_off = exclusive scan of counts (N + 1 entries; gm_cnt[N] = 0 sentinel); the scan's
@@ -735,14 +745,15 @@ gs_status bin_bricks_impl(const float* params, const gs_grid* grid, const gs_con
     } else {
         if (cudaMemsetAsync(total, 0, sizeof(long long), st) != cudaSuccess) return GS_ERR_CUDA;
         if (cudaMemsetAsync(bins->gm_off, 0, sizeof(int32_t), st) != cudaSuccess) return GS_ERR_CUDA;
-        k_capacity<<<1, 1, 0, st>>>(total, cap, bins->d_npairs, bins->d_status);
+        launch_k(k_capacity, dim3(1), dim3(1), 0, st, total, cap, bins->d_npairs, bins->d_status);
         const gs_status s = last_launch_status();
         if (s != GS_OK) return s;
     }
     gs_status s = GS_OK;
     if (N > 0) {
-        k_emit<<<static_cast<unsigned>((N + kEmitThreads - 1) / kEmitThreads), kEmitThreads, 0, st>>>(
-            bins->brange, bins->gm_off, N, b.nbx, b.nby, bins->d_npairs, cap, ws.keys0, ws.gm_gid);
+        launch_k(k_emit, dim3(static_cast<unsigned>((N + kEmitThreads - 1) / kEmitThreads)),
+            dim3(kEmitThreads), 0, st, bins->brange, bins->gm_off, N, b.nbx, b.nby, bins->d_npairs,
+            cap, ws.keys0, ws.gm_gid);
         s = last_launch_status();
         if (s != GS_OK) return s;
     }
@@ -763,25 +774,25 @@ gs_status bin_bricks_impl(const float* params, const gs_grid* grid, const gs_con
     const int64_t hist_len = int64_t(kRadix) * nt;
     for (int pass = 0; pass < passes; ++pass) {
         const int shift = pass * kRadixBits;
-        k_radix_hist<<<nt, kSortThreads, 0, st>>>(kin, bins->d_npairs, cap, shift, nt, ws.hist);
+        launch_k(k_radix_hist, dim3(nt), dim3(kSortThreads), 0, st, kin, bins->d_npairs, cap, shift,
+            nt, ws.hist);
         s = last_launch_status();
         if (s != GS_OK) return s;
         s = exclusive_scan_i32(ws.hist, ws.hist, hist_len, nullptr, ws.scan_tmp, ws.scan_tmp_len - 1, st);
         if (s != GS_OK) return s;
         if (pass == 0)
-            k_radix_scatter<true><<<nt, kSortThreads, 0, st>>>(kin, vin, kout, vout, ws.hist,
-                                                              bins->d_npairs, cap, shift, nt);
+            launch_k(k_radix_scatter<true>, dim3(nt), dim3(kSortThreads), 0, st, kin, vin, kout,
+                vout, ws.hist, bins->d_npairs, cap, shift, nt);
         else
-            k_radix_scatter<false><<<nt, kSortThreads, 0, st>>>(kin, vin, kout, vout, ws.hist,
-                                                               bins->d_npairs, cap, shift, nt);
+            launch_k(k_radix_scatter<false>, dim3(nt), dim3(kSortThreads), 0, st, kin, vin, kout,
+                vout, ws.hist, bins->d_npairs, cap, shift, nt);
         s = last_launch_status();
         if (s != GS_OK) return s;
         int32_t* t = kin; kin = kout; kout = t;
         t = vin; vin = vout; vout = t;
     }
-    k_finalize<<<1184, 256, 0, st>>>(kin, vin, ws.gm_gid, bins->d_npairs, cap, bins->n_bricks,
-                                     bins->pair_gmj, bins->pair_gid, bins->pair_brick,
-                                     bins->brick_off);
+    launch_k(k_finalize, dim3(1184), dim3(256), 0, st, kin, vin, ws.gm_gid, bins->d_npairs, cap,
+        bins->n_bricks, bins->pair_gmj, bins->pair_gid, bins->pair_brick, bins->brick_off);
     return last_launch_status();
 }
 

@@ -163,6 +163,29 @@ gs_status validate_grid_cfg(const gs_grid* g, const gs_config* c);
 // Launch counter (every kernel launch site is followed by last_launch_status()).
 void note_launch();
 
+// ------------------------------------------------------------------ launch chaining
+// Programmatic dependent launch (sm_90 and later): every kernel is launched with programmatic
+// stream serialisation, so its launch overlaps the end of its predecessor on the stream, and
+// its first statement (pdl_enter) waits until the predecessor has completed and its memory is
+// visible; nothing is read or written before the wait. Kernels do not trigger their
+// successors early (the trigger is implicit as their blocks exit): an early trigger measured
+// slower in graph replays of the fitting step.
+template <typename... P, typename... A>
+inline void launch_k(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     A&&... args) {
+    cudaLaunchConfig_t c = {};
+    c.gridDim = grid;
+    c.blockDim = block;
+    c.dynamicSmemBytes = smem;
+    c.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    c.attrs = at;
+    c.numAttrs = 1;
+    (void)cudaLaunchKernelEx(&c, k, static_cast<A&&>(args)...);  // errors: cudaGetLastError
+}
+
 // Launch error check -> gs_status; counts the launch it follows.
 inline gs_status last_launch_status() {
     note_launch();
@@ -226,6 +249,12 @@ __device__ __forceinline__ float exp_cw(float x) {
     int k = static_cast<int>(kf);
     float two_k = __int_as_float((k + 127) << 23);
     return __fmul_rn(p, two_k);
+}
+
+// First statement of every kernel: wait for the preceding kernel on the stream (see
+// launch_k; a no-op for a launch without a programmatic dependency).
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // 2^x on the special-function unit (ex2.approx, flush-to-zero).

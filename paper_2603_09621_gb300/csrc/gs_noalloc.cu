@@ -38,6 +38,7 @@ float* g_scratch_ptr[kMaxDevices] = {};
 __global__ void __launch_bounds__(kStaticThreads) k_l1_static_partial(
     const float* __restrict__ pred, const float* __restrict__ target, int64_t n, float inv_n,
     float* __restrict__ dpred, float* __restrict__ partials) {
+    pdl_enter();
     __shared__ float sm[kStaticThreads];
     const int64_t base = int64_t(blockIdx.x) * kStaticChunk;
     float acc = 0.f;
@@ -62,6 +63,7 @@ __global__ void __launch_bounds__(kStaticThreads) k_l1_static_partial(
 __global__ void __launch_bounds__(1024) k_l1_static_final(const float* __restrict__ partials,
                                                           int nblocks, float inv_n,
                                                           float* __restrict__ loss) {
+    pdl_enter();
     __shared__ float sm[1024];
     float acc = 0.f;
     for (int i = threadIdx.x; i < nblocks; i += 1024) acc += partials[i];
@@ -102,9 +104,10 @@ extern "C" gs_status gs_l1_loss_static(const float* pred, const float* target, i
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int nblocks = static_cast<int>((n + kStaticChunk - 1) / kStaticChunk);
     const float inv_n = 1.0f / float(n);
-    k_l1_static_partial<<<nblocks, kStaticThreads, 0, st>>>(pred, target, n, inv_n, dpred, scratch);
+    launch_k(k_l1_static_partial, dim3(nblocks), dim3(kStaticThreads), 0, st, pred, target, n,
+        inv_n, dpred, scratch);
     s = last_launch_status();
     if (s != GS_OK) return s;
-    k_l1_static_final<<<1, 1024, 0, st>>>(scratch, nblocks, inv_n, d_loss);
+    launch_k(k_l1_static_final, dim3(1), dim3(1024), 0, st, scratch, nblocks, inv_n, d_loss);
     return last_launch_status();
 }

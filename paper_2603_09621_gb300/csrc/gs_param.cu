@@ -12,6 +12,7 @@ namespace gs {
 // ------------------------------------------------------------------------ Eq. 2
 __global__ void k_signal_proxy(const float* __restrict__ T1, const float* __restrict__ T2,
                                int64_t n, float TR, float TE, float* __restrict__ out) {
+    pdl_enter();
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += int64_t(gridDim.x) * blockDim.x)
         out[i] = -expm1f(-TR / T1[i]) * expf(-TE / T2[i]);
@@ -147,6 +148,7 @@ __device__ __forceinline__ void store12(float* dst, const float* d) {
 __global__ void __launch_bounds__(256) k_param_bwd(const float* __restrict__ params,
                                                    const float* __restrict__ gacc, int64_t N,
                                                    ChainGeo C, float* __restrict__ dparams) {
+    pdl_enter();
     const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= N) return;
     float p[12], gv[12], out[12];
@@ -163,7 +165,8 @@ gs_status launch_param_bwd(const float* params, const float* gacc, int64_t n, co
     C.signal_mode = cfg->signal_mode;
     C.a_act = cfg->a_act;
     C.t_act = cfg->t_act;
-    k_param_bwd<<<static_cast<unsigned>((n + 255) / 256), 256, 0, st>>>(params, gacc, n, C, dparams);
+    launch_k(k_param_bwd, dim3(static_cast<unsigned>((n + 255) / 256)), dim3(256), 0, st, params,
+        gacc, n, C, dparams);
     return last_launch_status();
 }
 
@@ -207,6 +210,7 @@ __device__ __forceinline__ float adam_one(float& p, float gr, float& m, float& v
 __global__ void __launch_bounds__(256) k_adam(float* __restrict__ params, const float* __restrict__ grad,
                                               float* __restrict__ m, float* __restrict__ v, int64_t n,
                                               AdamLr hp, const int32_t* __restrict__ d_step) {
+    pdl_enter();
     const AdamCoef c = adam_coef(hp, d_step);
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += int64_t(gridDim.x) * blockDim.x) {
@@ -227,6 +231,7 @@ __global__ void __launch_bounds__(256) k_chain_adam(
     float* __restrict__ v, const float* __restrict__ part, const float* __restrict__ gacc,
     const int32_t* __restrict__ gm_off, const int64_t* __restrict__ npairs, int64_t capacity,
     int64_t N, ChainGeo C, AdamLr hp, const int32_t* __restrict__ d_step) {
+    pdl_enter();
     const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= N) return;
     float gv[12];
@@ -269,6 +274,7 @@ __global__ void __launch_bounds__(256) k_chain_adam(
 // Counts a step, unless npairs is given and the step's binning overflowed the pair capacity
 // (then the fitting step was a no-op).
 __global__ void k_step_inc(int32_t* d_step, const int64_t* __restrict__ npairs, int64_t capacity) {
+    pdl_enter();
     if (npairs) {
         const int64_t P = *npairs;
         if (P < 0 || P > capacity) return;
@@ -288,6 +294,7 @@ struct InitGeo {
 
 __global__ void __launch_bounds__(256) k_init_lattice(const float* __restrict__ lr, InitGeo G,
                                                       float* __restrict__ params) {
+    pdl_enter();
     const int64_t n = int64_t(G.nl[0]) * G.nl[1] * G.nl[2];
     const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= n) return;
@@ -367,14 +374,14 @@ gs_status launch_chain_adam(float* params, float* grad, float* m, float* v, cons
     const AdamLr a = make_adam_lr(hp);
     const unsigned gb = static_cast<unsigned>((n + 255) / 256);
     if (cfg->deterministic)
-        k_chain_adam<true><<<gb, 256, 0, st>>>(params, grad, m, v, part, gacc, bins->gm_off,
-                                               bins->d_npairs, bins->capacity, n, C, a, d_step);
+        launch_k(k_chain_adam<true>, dim3(gb), dim3(256), 0, st, params, grad, m, v, part, gacc,
+            bins->gm_off, bins->d_npairs, bins->capacity, n, C, a, d_step);
     else
-        k_chain_adam<false><<<gb, 256, 0, st>>>(params, grad, m, v, part, gacc, bins->gm_off,
-                                                bins->d_npairs, bins->capacity, n, C, a, d_step);
+        launch_k(k_chain_adam<false>, dim3(gb), dim3(256), 0, st, params, grad, m, v, part, gacc,
+            bins->gm_off, bins->d_npairs, bins->capacity, n, C, a, d_step);
     gs_status s = last_launch_status();
     if (s != GS_OK) return s;
-    k_step_inc<<<1, 1, 0, st>>>(d_step, bins->d_npairs, bins->capacity);
+    launch_k(k_step_inc, dim3(1), dim3(1), 0, st, d_step, bins->d_npairs, bins->capacity);
     return last_launch_status();
 }
 }  // namespace gs
@@ -386,7 +393,8 @@ extern "C" gs_status gs_signal_proxy(const float* T1, const float* T2, int64_t n
     if (!T1 || !T2 || !T_out) return GS_ERR_INVALID_ARG;
     const int64_t blocks64 = (n + 255) / 256;
     const unsigned blocks = static_cast<unsigned>(blocks64 < 65536 ? blocks64 : 65536);
-    k_signal_proxy<<<blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(T1, T2, n, TR, TE, T_out);
+    launch_k(k_signal_proxy, dim3(blocks), dim3(256), 0, reinterpret_cast<cudaStream_t>(stream), T1,
+        T2, n, TR, TE, T_out);
     return last_launch_status();
 }
 
@@ -402,11 +410,11 @@ extern "C" gs_status gs_adam_step(float* params, const float* grad, float* m, fl
         const int64_t n = n_gauss * 12;
         const int64_t blocks64 = (n + 255) / 256;
         const unsigned blocks = static_cast<unsigned>(blocks64 < 65536 ? blocks64 : 65536);
-        k_adam<<<blocks, 256, 0, st>>>(params, grad, m, v, n, a, d_step);
+        launch_k(k_adam, dim3(blocks), dim3(256), 0, st, params, grad, m, v, n, a, d_step);
         gs_status s = last_launch_status();
         if (s != GS_OK) return s;
     }
-    k_step_inc<<<1, 1, 0, st>>>(d_step, nullptr, 0);
+    launch_k(k_step_inc, dim3(1), dim3(1), 0, st, d_step, nullptr, 0);
     return last_launch_status();
 }
 
@@ -434,8 +442,8 @@ extern "C" gs_status gs_init_lattice_lr(const float* lr, int32_t lnz, int32_t ln
     }
     G.t_raw = t_act ? static_cast<float>(log(double(t_init) / (1.0 - double(t_init)))) : t_init;
     const int64_t N = int64_t(nlx) * nly * nlz;
-    k_init_lattice<<<static_cast<unsigned>((N + 255) / 256), 256, 0,
-                     reinterpret_cast<cudaStream_t>(stream)>>>(lr, G, params);
+    launch_k(k_init_lattice, dim3(static_cast<unsigned>((N + 255) / 256)), dim3(256), 0,
+        reinterpret_cast<cudaStream_t>(stream), lr, G, params);
     return last_launch_status();
 }
 
@@ -460,7 +468,7 @@ extern "C" gs_status gs_init_lattice(const float* lr, const gs_grid* g, int32_t 
     }
     G.t_raw = t_act ? static_cast<float>(log(double(t_init) / (1.0 - double(t_init)))) : t_init;
     const int64_t N = int64_t(nlx) * nly * nlz;
-    k_init_lattice<<<static_cast<unsigned>((N + 255) / 256), 256, 0,
-                     reinterpret_cast<cudaStream_t>(stream)>>>(lr, G, params);
+    launch_k(k_init_lattice, dim3(static_cast<unsigned>((N + 255) / 256)), dim3(256), 0,
+        reinterpret_cast<cudaStream_t>(stream), lr, G, params);
     return last_launch_status();
 }

@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(128, 14) k_render_fwd(const int32_t* __restric
                                                     const float4* __restrict__ rec4, RenderGeo G,
                                                     float* __restrict__ I, float* __restrict__ W,
                                                     unsigned long long* __restrict__ stats) {
+    pdl_enter();
     __shared__ float4 srec[kFwdChunk][REC_F4];
     const int tid = threadIdx.x, lane = tid & 31;
     const int nthreads = blockDim.x;
@@ -262,6 +263,7 @@ __global__ void __launch_bounds__(256) k_bwd_prep(const float* __restrict__ Iv,
                                                   const float* __restrict__ Wv,
                                                   const float* __restrict__ dIv, int64_t n,
                                                   float eps, float2* __restrict__ aip) {
+    pdl_enter();
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += int64_t(gridDim.x) * blockDim.x) {
         const float w = Wv[i], gI = dIv[i];
@@ -353,6 +355,7 @@ __global__ void __launch_bounds__(kBwdThreads, 8) k_render_bwd(
     const int32_t* __restrict__ pair_brick, const int64_t* __restrict__ npairs, int64_t capacity,
     const float4* __restrict__ rec4, RenderGeo G, const float2* __restrict__ aip,
     float* __restrict__ part, float* __restrict__ gacc) {
+    pdl_enter();
     __shared__ float4 srec[kBwdThreads][REC_F4];
     __shared__ __align__(16) float2 sfac[kBwdStage][kMaxBrickVoxels];
     __shared__ unsigned long long smask[kBwdThreads];
@@ -506,6 +509,7 @@ __global__ void __launch_bounds__(256) k_pair_reduce(const float* __restrict__ p
                                                      const int64_t* __restrict__ npairs,
                                                      int64_t capacity, int64_t N,
                                                      float* __restrict__ gacc) {
+    pdl_enter();
     const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= N) return;
     float acc[12];
@@ -552,11 +556,11 @@ gs_status render_fwd_impl(const gs_bins* bins, const gs_grid* grid, const gs_con
     const int threads = 32 * ((G.fx * G.fy * G.fz + 1) / 2);  // a half-warp per footprint
     const float4* rec4 = reinterpret_cast<const float4*>(bins->rec);
     if (stats)
-        k_render_fwd<true><<<bins->n_bricks, threads, 0, st>>>(bins->brick_off, bins->pair_gid, rec4,
-                                                               G, I, W, stats);
+        launch_k(k_render_fwd<true>, dim3(bins->n_bricks), dim3(threads), 0, st, bins->brick_off,
+            bins->pair_gid, rec4, G, I, W, stats);
     else
-        k_render_fwd<false><<<bins->n_bricks, threads, 0, st>>>(bins->brick_off, bins->pair_gid,
-                                                                rec4, G, I, W, nullptr);
+        launch_k(k_render_fwd<false>, dim3(bins->n_bricks), dim3(threads), 0, st, bins->brick_off,
+            bins->pair_gid, rec4, G, I, W, nullptr);
     return last_launch_status();
 }
 
@@ -568,8 +572,8 @@ gs_status launch_bwd_prep(const float* I, const float* W, const float* dI, const
                           const Workspace& ws, cudaStream_t st) {
     const int64_t nv = int64_t(G.nx) * G.ny * G.nz;
     const int64_t pb = (nv + 255) / 256;
-    k_bwd_prep<<<static_cast<unsigned>(pb < 65536 ? pb : 65536), 256, 0, st>>>(I, W, dI, nv, G.eps,
-                                                                              ws.aip);
+    launch_k(k_bwd_prep, dim3(static_cast<unsigned>(pb < 65536 ? pb : 65536)), dim3(256), 0, st, I,
+        W, dI, nv, G.eps, ws.aip);
     return last_launch_status();
 }
 
@@ -579,9 +583,9 @@ static gs_status launch_bwd_pairs(const gs_bins* bins, const RenderGeo& G, const
     if (bins->capacity == 0) return GS_OK;
     const unsigned gb = static_cast<unsigned>((bins->capacity + kBwdThreads - 1) / kBwdThreads);
     const float4* rec4 = reinterpret_cast<const float4*>(bins->rec);
-    k_render_bwd<BX, kDet><<<gb, kBwdThreads, 0, st>>>(
-        bins->pair_gid, bins->pair_gmj, bins->pair_brick, bins->d_npairs, bins->capacity, rec4, G,
-        ws.aip, kDet ? ws.part : nullptr, kDet ? nullptr : ws.gacc);
+    launch_k(k_render_bwd<BX, kDet>, dim3(gb), dim3(kBwdThreads), 0, st, bins->pair_gid,
+        bins->pair_gmj, bins->pair_brick, bins->d_npairs, bins->capacity, rec4, G, ws.aip,
+        kDet ? ws.part : nullptr, kDet ? nullptr : ws.gacc);
     return last_launch_status();
 }
 
@@ -614,7 +618,7 @@ static gs_status render_bwd_geo(const gs_bins* bins, const gs_grid* grid, const 
     if (s != GS_OK) return s;
     const int64_t N = bins->n_gauss;
     if (cfg->deterministic && N > 0) {
-        k_pair_reduce<<<static_cast<unsigned>((N + 255) / 256), 256, 0, st>>>(
+        launch_k(k_pair_reduce, dim3(static_cast<unsigned>((N + 255) / 256)), dim3(256), 0, st,
             ws.part, bins->gm_off, bins->d_npairs, bins->capacity, N, ws.gacc);
         s = last_launch_status();
     }

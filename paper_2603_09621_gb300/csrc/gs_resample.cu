@@ -50,6 +50,7 @@ __device__ __forceinline__ void res_range(const ResAxis& A, int i, int& jlo, int
 
 __global__ void __launch_bounds__(256) k_resample_fwd(const float* __restrict__ src, ResGeo G,
                                                       float* __restrict__ dst) {
+    pdl_enter();
     const ResAxis &AX = G.a[0], &AY = G.a[1], &AZ = G.a[2];
     const int64_t n = int64_t(AX.n_dst) * AY.n_dst * AZ.n_dst;
     for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n;
@@ -153,6 +154,7 @@ __device__ __forceinline__ float res_gather(const float* __restrict__ ddst, cons
 
 __global__ void __launch_bounds__(256) k_resample_bwd(const float* __restrict__ ddst, ResGeo G,
                                                       float* __restrict__ dsrc) {
+    pdl_enter();
     const ResAxis &AX = G.a[0], &AY = G.a[1], &AZ = G.a[2];
     const int64_t n = int64_t(AX.n_src) * AY.n_src * AZ.n_src;
     for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n;
@@ -183,6 +185,7 @@ __global__ void __launch_bounds__(256) k_resample_adj_tab(const float* __restric
                                                           const float* __restrict__ Wv, float eps,
                                                           float* __restrict__ dsrc,
                                                           float2* __restrict__ aip) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char res_smem[];
     ResRun<K>* tab = reinterpret_cast<ResRun<K>*>(res_smem);
     const ResAxis &AX = G.a[0], &AY = G.a[1], &AZ = G.a[2];
@@ -245,6 +248,7 @@ __global__ void __launch_bounds__(256) k_resample_adj_prep(const float* __restri
                                                            const float* __restrict__ Iv,
                                                            const float* __restrict__ Wv, float eps,
                                                            float2* __restrict__ aip) {
+    pdl_enter();
     const ResAxis &AX = G.a[0], &AY = G.a[1], &AZ = G.a[2];
     const int64_t n = int64_t(AX.n_src) * AY.n_src * AZ.n_src;
     for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n;
@@ -283,7 +287,8 @@ static unsigned res_blocks(int64_t n) {
 gs_status resample_fwd_impl(const float* src, int32_t snz, int32_t sny, int32_t snx, float* dst,
                             int32_t dnz, int32_t dny, int32_t dnx, cudaStream_t st) {
     const ResGeo G = make_res(snz, sny, snx, dnz, dny, dnx);
-    k_resample_fwd<<<res_blocks(int64_t(dnz) * dny * dnx), 256, 0, st>>>(src, G, dst);
+    launch_k(k_resample_fwd, dim3(res_blocks(int64_t(dnz) * dny * dnx)), dim3(256), 0, st, src, G,
+        dst);
     return last_launch_status();
 }
 
@@ -297,6 +302,7 @@ __global__ void __launch_bounds__(256) k_resample_adj_plane(const float* __restr
                                                             const float* __restrict__ Wv, float eps,
                                                             float* __restrict__ dsrc,
                                                             float2* __restrict__ aip) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char res_smem[];
     const ResAxis &AX = G.a[0], &AY = G.a[1], &AZ = G.a[2];
     const int nx = AX.n_src, ny = AY.n_src;
@@ -369,14 +375,14 @@ static bool launch_adj_plane_k(const float* dd, const ResGeo& G, const float* I,
     if (nz > 65535) return false;
     if (base + (sizeof(ResRun<K>) + sizeof(float) * lnx) * 32 <= size_t(kPlaneSmem)) {
         const size_t smem = base + (sizeof(ResRun<K>) + sizeof(float) * lnx) * 32;
-        k_resample_adj_plane<kPrep, K, 32><<<dim3(nz, (ny + 31) / 32), 256, smem, st>>>(dd, G, I, W, eps,
-                                                                                       dsrc, aip);
+        launch_k(k_resample_adj_plane<kPrep, K, 32>, dim3(dim3(nz, (ny + 31) / 32)), dim3(256),
+            smem, st, dd, G, I, W, eps, dsrc, aip);
         return true;
     }
     if (base + (sizeof(ResRun<K>) + sizeof(float) * lnx) * 8 <= size_t(kPlaneSmem)) {
         const size_t smem = base + (sizeof(ResRun<K>) + sizeof(float) * lnx) * 8;
-        k_resample_adj_plane<kPrep, K, 8><<<dim3(nz, (ny + 7) / 8), 256, smem, st>>>(dd, G, I, W, eps,
-                                                                                   dsrc, aip);
+        launch_k(k_resample_adj_plane<kPrep, K, 8>, dim3(dim3(nz, (ny + 7) / 8)), dim3(256), smem,
+            st, dd, G, I, W, eps, dsrc, aip);
         return true;
     }
     return false;
@@ -398,11 +404,11 @@ static bool launch_adj_tab(const float* dd, const ResGeo& G, const float* I, con
     const int64_t rows = int64_t(G.a[2].n_src) * G.a[1].n_src;
     const unsigned nb = static_cast<unsigned>(rows < 152 * 8 ? rows : 152 * 8);
     if (res_two_taps(G))
-        k_resample_adj_tab<kPrep, 2><<<nb, 256, sizeof(ResRun<2>) * n_tab, st>>>(dd, G, I, W, eps,
-                                                                                dsrc, aip);
-    else
-        k_resample_adj_tab<kPrep, kResList><<<nb, 256, sizeof(ResRun<kResList>) * n_tab, st>>>(
+        launch_k(k_resample_adj_tab<kPrep, 2>, dim3(nb), dim3(256), sizeof(ResRun<2>) * n_tab, st,
             dd, G, I, W, eps, dsrc, aip);
+    else
+        launch_k(k_resample_adj_tab<kPrep, kResList>, dim3(nb), dim3(256),
+            sizeof(ResRun<kResList>) * n_tab, st, dd, G, I, W, eps, dsrc, aip);
     return true;
 }
 
@@ -412,7 +418,8 @@ gs_status resample_adj_prep_impl(const float* dlr, int32_t lnz, int32_t lny, int
     const ResGeo G = make_res(nz, ny, nx, lnz, lny, lnx);
     if (!launch_adj_plane<true>(dlr, G, I, W, eps, nullptr, aip, st) &&
         !launch_adj_tab<true>(dlr, G, I, W, eps, nullptr, aip, st))
-        k_resample_adj_prep<<<res_blocks(int64_t(nz) * ny * nx), 256, 0, st>>>(dlr, G, I, W, eps, aip);
+        launch_k(k_resample_adj_prep, dim3(res_blocks(int64_t(nz) * ny * nx)), dim3(256), 0, st,
+            dlr, G, I, W, eps, aip);
     return last_launch_status();
 }
 
@@ -436,6 +443,7 @@ extern "C" gs_status gs_resample_bwd(const float* ddst, int32_t dnz, int32_t dny
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (!launch_adj_plane<false>(ddst, G, nullptr, nullptr, 0.f, dsrc, nullptr, st) &&
         !launch_adj_tab<false>(ddst, G, nullptr, nullptr, 0.f, dsrc, nullptr, st))
-        k_resample_bwd<<<res_blocks(int64_t(snz) * sny * snx), 256, 0, st>>>(ddst, G, dsrc);
+        launch_k(k_resample_bwd, dim3(res_blocks(int64_t(snz) * sny * snx)), dim3(256), 0, st, ddst,
+            G, dsrc);
     return last_launch_status();
 }

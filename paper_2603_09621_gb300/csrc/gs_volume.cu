@@ -16,6 +16,7 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 __global__ void __launch_bounds__(256) k_downsample_fwd(const float* __restrict__ hr, int ny, int nx,
                                                         int nzl, int s, float inv_s,
                                                         float* __restrict__ lr) {
+    pdl_enter();
     const int64_t plane = int64_t(ny) * nx;
     const int64_t n = plane * nzl;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
@@ -31,6 +32,7 @@ __global__ void __launch_bounds__(256) k_downsample_fwd(const float* __restrict_
 __global__ void __launch_bounds__(256) k_downsample_bwd(const float* __restrict__ dlr, int nz, int ny,
                                                         int nx, int s, float inv_s,
                                                         float* __restrict__ dhr) {
+    pdl_enter();
     const int64_t plane = int64_t(ny) * nx;
     const int64_t n = plane * nz;
     const int zmax = s * (nz / s);
@@ -47,6 +49,7 @@ __global__ void __launch_bounds__(256) k_l1_partial(const float* __restrict__ pr
                                                     const float* __restrict__ target, int64_t n,
                                                     float inv_n, float* __restrict__ dpred,
                                                     float* __restrict__ partials) {
+    pdl_enter();
     __shared__ float sm[256];
     float acc = 0.f;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
@@ -66,6 +69,7 @@ __global__ void __launch_bounds__(256) k_l1_partial(const float* __restrict__ pr
 
 __global__ void __launch_bounds__(1024) k_l1_final(const float* __restrict__ partials, float inv_n,
                                                    float* __restrict__ loss) {
+    pdl_enter();
     __shared__ float sm[kL1Blocks];
     sm[threadIdx.x] = partials[threadIdx.x];
     __syncthreads();
@@ -88,6 +92,7 @@ static unsigned grid_for(int64_t n) {
 __global__ void __launch_bounds__(256) k_downsample_fwd4(const float4* __restrict__ hr, int plane4,
                                                          int s, float inv_s,
                                                          float4* __restrict__ lr) {
+    pdl_enter();
     const int k = blockIdx.y;
     const float4* src = hr + int64_t(k) * s * plane4;
     float4* dst = lr + int64_t(k) * plane4;
@@ -114,6 +119,7 @@ __global__ void __launch_bounds__(256) k_profile_adj_prep4(const float4* __restr
                                                            const float4* __restrict__ Wv,
                                                            int plane4, int zmax, int s, float inv_s,
                                                            float eps, float4* __restrict__ aip) {
+    pdl_enter();
     const int z = blockIdx.y;
     const bool in = z < zmax;
     const int64_t base = int64_t(z) * plane4;
@@ -145,10 +151,11 @@ static bool vec_ok(const void* a, const void* b, int64_t plane, int slices) {
 gs_status launch_l1(const float* pred, const float* target, int64_t n, float* d_loss, float* dpred,
                     float* partials, cudaStream_t st) {
     const float inv_n = n > 0 ? 1.0f / float(n) : 0.0f;
-    k_l1_partial<<<kL1Blocks, 256, 0, st>>>(pred, target, n, inv_n, dpred, partials);
+    launch_k(k_l1_partial, dim3(kL1Blocks), dim3(256), 0, st, pred, target, n, inv_n, dpred,
+        partials);
     gs_status s = last_launch_status();
     if (s != GS_OK) return s;
-    k_l1_final<<<1, kL1Blocks, 0, st>>>(partials, inv_n, d_loss);
+    launch_k(k_l1_final, dim3(1), dim3(kL1Blocks), 0, st, partials, inv_n, d_loss);
     return last_launch_status();
 }
 
@@ -160,10 +167,12 @@ gs_status downsample_fwd_impl(const float* hr, int nz, int ny, int nx, int s, fl
     const int64_t plane = int64_t(ny) * nx;
     if (vec_ok(hr, lr, plane, nzl) && plane / 4 <= (int64_t(1) << 30)) {
         const int plane4 = static_cast<int>(plane / 4);
-        k_downsample_fwd4<<<grid2d(plane4, nzl), 256, 0, st>>>(
-            reinterpret_cast<const float4*>(hr), plane4, s, 1.0f / float(s), reinterpret_cast<float4*>(lr));
+        launch_k(k_downsample_fwd4, dim3(grid2d(plane4, nzl)), dim3(256), 0, st,
+            reinterpret_cast<const float4*>(hr), plane4, s, 1.0f / float(s),
+            reinterpret_cast<float4*>(lr));
     } else {
-        k_downsample_fwd<<<grid_for(n), 256, 0, st>>>(hr, ny, nx, nzl, s, 1.0f / float(s), lr);
+        launch_k(k_downsample_fwd, dim3(grid_for(n)), dim3(256), 0, st, hr, ny, nx, nzl, s,
+            1.0f / float(s), lr);
     }
     return last_launch_status();
 }
@@ -171,7 +180,8 @@ gs_status downsample_fwd_impl(const float* hr, int nz, int ny, int nx, int s, fl
 gs_status downsample_bwd_impl(const float* dlr, int nz, int ny, int nx, int s, float* dhr,
                               cudaStream_t st) {
     const int64_t n = int64_t(nz) * ny * nx;
-    k_downsample_bwd<<<grid_for(n), 256, 0, st>>>(dlr, nz, ny, nx, s, 1.0f / float(s), dhr);
+    launch_k(k_downsample_bwd, dim3(grid_for(n)), dim3(256), 0, st, dlr, nz, ny, nx, s,
+        1.0f / float(s), dhr);
     return last_launch_status();
 }
 
@@ -198,6 +208,7 @@ __global__ void __launch_bounds__(256) k_profile_adj_prep(const float* __restric
                                                           const float* __restrict__ Wv, int nz,
                                                           int ny, int nx, int s, float inv_s,
                                                           float eps, float2* __restrict__ aip) {
+    pdl_enter();
     const int64_t plane = int64_t(ny) * nx;
     const int64_t n = plane * nz;
     const int zmax = s * (nz / s);
@@ -306,14 +317,14 @@ extern "C" gs_status gs_fit_step(gs_fit_state* st, gs_stream stream) {
         if (vec_ok(st->lr_pred, st->I, plane, g.nz) && vec_ok(st->W, w.aip, plane, g.nz) &&
             plane / 4 <= (int64_t(1) << 30)) {
             const int plane4 = static_cast<int>(plane / 4);
-            k_profile_adj_prep4<<<grid2d(plane4, g.nz), 256, 0, cs>>>(
-                reinterpret_cast<const float4*>(st->lr_pred), reinterpret_cast<const float4*>(st->I),
-                reinterpret_cast<const float4*>(st->W), plane4, st->s * (g.nz / st->s), st->s,
-                1.0f / float(st->s), st->cfg.eps, reinterpret_cast<float4*>(w.aip));
+            launch_k(k_profile_adj_prep4, dim3(grid2d(plane4, g.nz)), dim3(256), 0, cs,
+                reinterpret_cast<const float4*>(st->lr_pred),
+                reinterpret_cast<const float4*>(st->I), reinterpret_cast<const float4*>(st->W),
+                plane4, st->s * (g.nz / st->s), st->s, 1.0f / float(st->s), st->cfg.eps,
+                reinterpret_cast<float4*>(w.aip));
         } else {
-            k_profile_adj_prep<<<grid_for(nv), 256, 0, cs>>>(st->lr_pred, st->I, st->W, g.nz, g.ny,
-                                                             g.nx, st->s, 1.0f / float(st->s),
-                                                             st->cfg.eps, w.aip);
+            launch_k(k_profile_adj_prep, dim3(grid_for(nv)), dim3(256), 0, cs, st->lr_pred, st->I,
+                st->W, g.nz, g.ny, g.nx, st->s, 1.0f / float(st->s), st->cfg.eps, w.aip);
         }
         s = last_launch_status();
         if (s != GS_OK) return s;
