@@ -13,8 +13,9 @@
 //                  histograms, a digit-major scan, and a stable scatter whose in-tile ranks
 //                  come from warp match masks. Stability keeps ascending Gaussian ids inside
 //                  each brick, so the lists are deterministic.
-//   k_finalize     pair_gmj (Gaussian-major position), pair_gid (owner) and pair_brick per
-//                  brick-major pair; brick_off from the boundaries of the sorted keys.
+//                  The last pass stores pair_brick (key), pair_gmj (Gaussian-major position)
+//                  and pair_gid (owner) directly.
+//   k_brick_off    brick_off from the boundaries of the sorted keys.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -467,12 +468,14 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const int32_t* __re
 // masks), so the tile sits in shared memory sorted by digit, ties in tile order. The tile is
 // then written out in that order: digit d's run goes to [hist_off[d][tile], ...), so
 // consecutive threads store consecutive addresses.
-template <bool kFirst>
+// kLast: the last pass stores the bins' per-pair arrays directly: brick (the key),
+// Gaussian-major position (the value) and owner (gm_gid of the value).
+template <bool kFirst, bool kLast>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in,
     int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out,
     const int32_t* __restrict__ hist_off, const int64_t* __restrict__ npairs, int64_t capacity,
-    int shift, int n_tiles) {
+    int shift, int n_tiles, const int32_t* __restrict__ gm_gid, int32_t* __restrict__ pair_gid) {
     pdl_enter();
     constexpr int kWarps = kSortThreads / 32;
     constexpr int kPerWarp = kSortTile / kWarps;
@@ -555,20 +558,16 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
         const int pos = gstart[dk] + (j - dstart[dk]);
         keys_out[pos] = key;
         vals_out[pos] = sval[j];
+        if (kLast) pair_gid[pos] = gm_gid[sval[j]];
     }
 }
 
-// Per brick-major pair: Gaussian-major position, owner and brick; and the brick offsets,
-// read off the sorted keys (brick_off[b] = first pair of brick b, or the next non-empty
-// brick's first pair; brick_off[nb] = P).
-__global__ void __launch_bounds__(256) k_finalize(const int32_t* __restrict__ keys,
-                                                  const int32_t* __restrict__ vals,
-                                                  const int32_t* __restrict__ gm_gid,
-                                                  const int64_t* __restrict__ npairs, int64_t capacity,
-                                                  int nb, int32_t* __restrict__ pair_gmj,
-                                                  int32_t* __restrict__ pair_gid,
-                                                  int32_t* __restrict__ pair_brick,
-                                                  int32_t* __restrict__ brick_off) {
+// brick_off from the boundaries of the sorted keys (brick_off[b] = first pair of brick b, or
+// the next non-empty brick's first pair; brick_off[nb] = P).
+__global__ void __launch_bounds__(256) k_brick_off(const int32_t* __restrict__ keys,
+                                                   const int64_t* __restrict__ npairs,
+                                                   int64_t capacity, int nb,
+                                                   int32_t* __restrict__ brick_off) {
     pdl_enter();
     const int64_t P = valid_pairs(npairs, capacity);
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i <= P;
@@ -576,12 +575,6 @@ __global__ void __launch_bounds__(256) k_finalize(const int32_t* __restrict__ ke
         const int cur = (i < P) ? keys[i] : nb;
         const int prev = (i > 0) ? keys[i - 1] : -1;
         for (int bb = prev + 1; bb <= cur; ++bb) brick_off[bb] = static_cast<int32_t>(i);
-        if (i < P) {
-            const int j = vals[i];
-            pair_gmj[i] = j;
-            pair_gid[i] = gm_gid[j];
-            pair_brick[i] = keys[i];
-        }
     }
 }
 
@@ -780,19 +773,23 @@ gs_status bin_bricks_impl(const float* params, const gs_grid* grid, const gs_con
         if (s != GS_OK) return s;
         s = exclusive_scan_i32(ws.hist, ws.hist, hist_len, nullptr, ws.scan_tmp, ws.scan_tmp_len - 1, st);
         if (s != GS_OK) return s;
-        if (pass == 0)
-            launch_k(k_radix_scatter<true>, dim3(nt), dim3(kSortThreads), 0, st, kin, vin, kout,
-                vout, ws.hist, bins->d_npairs, cap, shift, nt);
-        else
-            launch_k(k_radix_scatter<false>, dim3(nt), dim3(kSortThreads), 0, st, kin, vin, kout,
-                vout, ws.hist, bins->d_npairs, cap, shift, nt);
+        // the last pass writes the bins' pair arrays (brick, Gaussian-major position, owner)
+        const bool last = pass == passes - 1;
+        int32_t* ko = last ? bins->pair_brick : kout;
+        int32_t* vo = last ? bins->pair_gmj : vout;
+        using ScatterFn = void (*)(const int32_t*, const int32_t*, int32_t*, int32_t*, const int32_t*,
+                                   const int64_t*, int64_t, int, int, const int32_t*, int32_t*);
+        ScatterFn kern = pass == 0 ? (last ? k_radix_scatter<true, true> : k_radix_scatter<true, false>)
+                                   : (last ? k_radix_scatter<false, true> : k_radix_scatter<false, false>);
+        launch_k(kern, dim3(nt), dim3(kSortThreads), 0, st, kin, vin, ko, vo, ws.hist,
+            bins->d_npairs, cap, shift, nt, ws.gm_gid, bins->pair_gid);
         s = last_launch_status();
         if (s != GS_OK) return s;
         int32_t* t = kin; kin = kout; kout = t;
         t = vin; vin = vout; vout = t;
     }
-    launch_k(k_finalize, dim3(1184), dim3(256), 0, st, kin, vin, ws.gm_gid, bins->d_npairs, cap,
-        bins->n_bricks, bins->pair_gmj, bins->pair_gid, bins->pair_brick, bins->brick_off);
+    launch_k(k_brick_off, dim3(1184), dim3(256), 0, st, bins->pair_brick, bins->d_npairs, cap,
+        bins->n_bricks, bins->brick_off);
     return last_launch_status();
 }
 
