@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(128, 14) k_render_fwd(const int32_t* __restric
     const int start = brick_off[b], end = brick_off[b + 1];
     for (int c0 = start; c0 < end; c0 += kFwdChunk) {
         const int cnt = min(kFwdChunk, end - c0);
-        __syncthreads();
+        if (c0 != start) __syncthreads();  // the previous chunk's records are no longer read
         for (int i = tid; i < cnt * REC_F4; i += nthreads) {
             const int k = i / REC_F4, part = i - k * REC_F4;
             srec[k][part] = rec4[int64_t(pair_gid[c0 + k]) * REC_F4 + part];
