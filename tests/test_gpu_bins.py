@@ -80,6 +80,15 @@ def test_bins_fit_workload_full_size():
     assert P > 500_000
 
 
+def test_bins_three_radix_passes():
+    """512 x 512 x 128 grid with 4^3 bricks: 524,288 bricks, so the brick keys take three 8-bit
+    radix passes (the third reuses the first pass's look-back words); 20,000 Gaussians."""
+    import oracle
+    og = oracle.Grid(512, 512, 128)
+    d = inputs.gaussian_cloud(9, 20000, (128, 512, 512))
+    assert _compare(cloud_params(d), og, brick=(4, 4, 4)) > 20000
+
+
 def test_bins_capacity_overflow_reports_and_empties():
     params, og = c1()
     bins = _bin(params, og, capacity=1000)
