@@ -275,7 +275,10 @@ __global__ void __launch_bounds__(256) k_bwd_prep(const float* __restrict__ Iv,
 // The rows of one (brick, Gaussian) pair: for each row in the mask, bx voxel slots with the
 // factors (alpha, alpha I') read from the block's staged copy (kStaged) or from the volume.
 // Accumulates with h = gamma g (gamma = dL/dw): acc[10] = sum h, acc[9] = sum alpha g and the
-// first and second moments of h about the Gaussian's mean (acc[0..8]).
+// moments of h (acc[0..8]). Along x they are taken about the brick row's centre slot:
+// every row of the pair has the same x origin x0, so with u = uc + k' (uc = x0 + (bx-1)/2
+// minus the mean, k' = slot - (bx-1)/2 a compile-time constant) the moments about the mean
+// follow once per pair, and a slot costs three accumulations instead of five.
 template <int BX, bool kStaged>
 __device__ __forceinline__ void adjoint_rows(const Rec& R, unsigned long long m, const RenderGeo& G,
                                              int x0, int y0, int z0,
@@ -283,9 +286,7 @@ __device__ __forceinline__ void adjoint_rows(const Rec& R, unsigned long long m,
                                              const float2* __restrict__ aip, float (&acc)[11]) {
     const int x1 = min(x0 + BX, G.nx) - 1;
     const bool full_row = (x1 == x0 + BX - 1) && ((G.nx & 1) == 0);  // 16-byte aligned rows
-    float ux4[BX / 4];
-#pragma unroll
-    for (int j = 0; j < BX / 4; ++j) ux4[j] = ux_base(R, x0 + 4 * j);
+    constexpr float kc = 0.5f * float(BX - 1);
     while (m) {
         const int r = __ffsll(static_cast<long long>(m)) - 1;
         m &= m - 1;
@@ -325,15 +326,14 @@ __device__ __forceinline__ void adjoint_rows(const Rec& R, unsigned long long m,
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
 #pragma unroll
         for (int xb = 0; xb < BX; ++xb) {
-            const float u = ux4[xb >> 2] + float(xb & 3);
+            const float kp = float(xb) - kc;
             const float q = q_of_k(R, tq4[xb >> 2], xb & 3, S);
             const float g = (q <= G.T) ? ex2_approx(-q) : 0.0f;
             const float h = fmaf(R.v, av[xb].x, -av[xb].y) * g;
             acc[9] = fmaf(av[xb].x, g, acc[9]);
             s0 += h;
-            const float tg = h * u;
-            s1 += tg;
-            s2 = fmaf(tg, u, s2);
+            s1 = fmaf(h, kp, s1);
+            s2 = fmaf(h, kp * kp, s2);
         }
         acc[10] += s0;
         acc[0] += s1;
@@ -481,8 +481,12 @@ __global__ void __launch_bounds__(kBwdThreads, 8) k_render_bwd(
         adjoint_rows<BX, true>(R, m, G, x0, y0, z0, &sfac[stage][0], aip, acc);
     else
         adjoint_rows<BX, false>(R, m, G, x0, y0, z0, nullptr, aip, acc);
-    float m1x = acc[0], m1y = acc[1], m1z = acc[2], m2xx = acc[3], m2yy = acc[4], m2zz = acc[5];
-    float m2xy = acc[6], m2xz = acc[7], m2yz = acc[8];
+    // x moments about the mean from those about the row centre: u = uc + k'
+    const float uc = ux_base(R, x0) + 0.5f * float(BX - 1);
+    float m1x = fmaf(uc, acc[10], acc[0]);
+    float m2xx = fmaf(uc, fmaf(uc, acc[10], 2.0f * acc[0]), acc[3]);
+    float m2xy = fmaf(uc, acc[1], acc[6]), m2xz = fmaf(uc, acc[2], acc[7]);
+    float m1y = acc[1], m1z = acc[2], m2yy = acc[4], m2zz = acc[5], m2yz = acc[8];
     const float dvp = acc[9], dr = acc[10];
     const float rr = R.r;
     const float dv = rr * dvp;
