@@ -21,7 +21,9 @@
 // shared memory, so each warp runs pairs of equal length. The per-voxel factors
 // (alpha, alpha I'), alpha = dL/dI / max(W, eps), are precomputed into one float2 volume; a
 // block copies those of its first three bricks into shared memory (zero outside the grid), so
-// rows read them without range tests. Each pair's partial is summed by one thread in a fixed
+// rows read them without range tests; one 16-byte pad after every 128 bytes spreads the rows
+// that the lanes of a warp read at once over the shared-memory banks. A row's slots are
+// evaluated in packed FP32x2 pairs (FFMA2). Each pair's partial is summed by one thread in a fixed
 // voxel order (the processing order does not change results) and goes to a per-pair slot
 // (deterministic mode, reduced later in Gaussian-major order) or to one float atomic per
 // value (fast mode).
@@ -272,80 +274,104 @@ __global__ void __launch_bounds__(256) k_bwd_prep(const float* __restrict__ Iv,
     }
 }
 
-// The rows of one (brick, Gaussian) pair: for each row in the mask, bx voxel slots with the
-// factors (alpha, alpha I') read from the block's staged copy (kStaged) or from the volume.
-// Accumulates with h = gamma g (gamma = dL/dw): acc[10] = sum h, acc[9] = sum alpha g and the
-// moments of h (acc[0..8]). Along x they are taken about the brick row's centre slot:
-// every row of the pair has the same x origin x0, so with u = uc + k' (uc = x0 + (bx-1)/2
-// minus the mean, k' = slot - (bx-1)/2 a compile-time constant) the moments about the mean
-// follow once per pair, and a slot costs three accumulations instead of five.
+// Packed FP32x2 arithmetic (one FFMA2 / FADD2 / FMUL2 instruction for two single-precision
+// operations; each element is rounded exactly as the scalar fmaf / + / *).
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+// Adjoint sums of one (brick, Gaussian) pair, with h = gamma g (gamma = dL/dw) per voxel.
+// A brick row of bx voxels is taken as bx/2 voxel pairs (p, p + bx/2); element e of a float2
+// holds the sums over the voxels p + e bx/2 (offset u = uc_e + p from the mean along x).
+struct AdjAcc {
+    float2 h, hy, hz;     // sum h, sum h dy, sum h dz
+    float2 p1, p1y, p1z;  // sum h p, sum h p dy, sum h p dz
+    float2 pq;            // sum h p (p + 1) / 2  (so sum h p^2 = 2 pq - p1)
+    float2 ag;            // sum alpha g
+    float yy, zz, yz;     // sum h dy^2, sum h dz^2, sum h dy dz
+};
+
+// The rows of one (brick, Gaussian) pair: for each row in the mask, bx voxel slots in bx/2
+// packed pairs, with the factors read from the block's staged copy (kStaged: per row, float4
+// (alpha_p, alpha_{p+bx/2}, -alpha I'_p, -alpha I'_{p+bx/2}) for p < bx/2) or from the volume.
+// The exponent of every slot takes the forward's operation sequence element by element, so
+// both kernels agree on every inclusion q <= T. The slot moments along x are running sums
+// over p (descending), which need no per-slot constants.
 template <int BX, bool kStaged>
 __device__ __forceinline__ void adjoint_rows(const Rec& R, unsigned long long m, const RenderGeo& G,
                                              int x0, int y0, int z0,
-                                             const float2* __restrict__ sfac_b,
-                                             const float2* __restrict__ aip, float (&acc)[11]) {
+                                             const float4* __restrict__ sfac_b,
+                                             const float2* __restrict__ aip, AdjAcc& A) {
+    constexpr int P = BX / 2;                    // voxel pairs per row
+    constexpr int NT = (BX >= 8) ? BX / 8 : 1;   // packed group bases per row
     const int x1 = min(x0 + BX, G.nx) - 1;
-    const bool full_row = (x1 == x0 + BX - 1) && ((G.nx & 1) == 0);  // 16-byte aligned rows
-    constexpr float kc = 0.5f * float(BX - 1);
+    const float2 sa2 = f2(R.sa, R.sa), v2 = f2(R.v, R.v);
+    // x offsets of the 4-voxel groups that pair p reads: (group p/4, group p/4 + bx/8)
+    float2 uxp[NT];
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+        uxp[j] = (BX >= 8) ? f2(ux_base(R, x0 + 4 * j), ux_base(R, x0 + 4 * j + P))
+                           : f2(ux_base(R, x0), ux_base(R, x0));
     while (m) {
         const int r = __ffsll(static_cast<long long>(m)) - 1;
         m &= m - 1;
         const int y = y0 + (r & G.bsy_mask), z = z0 + (r >> G.bsy_shift);
         float dy, dz, S, dxs;
         row_terms(R, float(y), float(z), dy, dz, S, dxs);
-        float tq4[BX / 4];
+        const float2 S2 = f2(S, S), nd2 = f2(-dxs, -dxs);
+        float2 tq0[NT];  // tq_base of each group, the forward's sa * (ux - dx*)
 #pragma unroll
-        for (int j = 0; j < BX / 4; ++j) tq4[j] = tq_base(R, x0 + 4 * j, dxs);
-        // (alpha, alpha I') of the row's voxels; zero outside the grid
-        float2 av[BX];
-        if (kStaged) {
-            const float4* s4 = reinterpret_cast<const float4*>(sfac_b + r * BX);
+        for (int j = 0; j < NT; ++j) tq0[j] = mul2(sa2, add2(uxp[j], nd2));
+        const bool row_in = kStaged || ((y < G.ny) && (z < G.nz));
+        const float2* arow = kStaged ? nullptr
+                                     : aip + (int64_t(min(z, G.nz - 1)) * G.ny + min(y, G.ny - 1)) * G.nx + x0;
+        float2 rs = f2(0.f, 0.f), m1 = f2(0.f, 0.f), qs = f2(0.f, 0.f);
 #pragma unroll
-            for (int k = 0; k < BX / 2; ++k) {
-                const float4 v = s4[k];
-                av[2 * k] = make_float2(v.x, v.y);
-                av[2 * k + 1] = make_float2(v.z, v.w);
-            }
-        } else {
-            const bool row_in = (y < G.ny) && (z < G.nz);
-            const float2* arow = aip + (int64_t(min(z, G.nz - 1)) * G.ny + min(y, G.ny - 1)) * G.nx + x0;
-            if (full_row && row_in) {
-                const float4* a4 = reinterpret_cast<const float4*>(arow);
-#pragma unroll
-                for (int k = 0; k < BX / 2; ++k) {
-                    const float4 v = a4[k];
-                    av[2 * k] = make_float2(v.x, v.y);
-                    av[2 * k + 1] = make_float2(v.z, v.w);
-                }
+        for (int p = P - 1; p >= 0; --p) {
+            // exponent of the two slots: in-group index k, group base tq0
+            float2 tq;
+            if (BX >= 8) {
+                const int k = p & 3;
+                tq = (k == 0) ? tq0[p >> 2] : fma2(f2(float(k), float(k)), sa2, tq0[p >> 2]);
             } else {
-#pragma unroll
-                for (int k = 0; k < BX; ++k)
-                    av[k] = (row_in && x0 + k <= x1) ? arow[k] : make_float2(0.f, 0.f);
+                tq = fma2(f2(float(p), float(p + 2)), sa2, tq0[0]);
+            }
+            const float2 q = fma2(tq, tq, S2);
+            const float2 g = f2((q.x <= G.T) ? ex2_approx(-q.x) : 0.0f,
+                                (q.y <= G.T) ? ex2_approx(-q.y) : 0.0f);
+            float2 al, nai;  // (alpha, -alpha I') of the two slots, zero outside the grid
+            if (kStaged) {
+                const float4 f = sfac_b[r * P + ((r * P) >> 3) + p];
+                al = f2(f.x, f.y);
+                nai = f2(f.z, f.w);
+            } else {
+                const float2 fa = (row_in && x0 + p <= x1) ? arow[p] : f2(0.f, 0.f);
+                const float2 fb = (row_in && x0 + p + P <= x1) ? arow[p + P] : f2(0.f, 0.f);
+                al = f2(fa.x, fb.x);
+                nai = f2(-fa.y, -fb.y);
+            }
+            const float2 h = mul2(fma2(v2, al, nai), g);
+            A.ag = fma2(al, g, A.ag);
+            rs = add2(rs, h);            // sum over slots >= p
+            if (p >= 1) {
+                m1 = add2(m1, rs);       // ends as sum h p
+                qs = add2(qs, m1);       // ends as sum h p (p + 1) / 2
             }
         }
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-#pragma unroll
-        for (int xb = 0; xb < BX; ++xb) {
-            const float kp = float(xb) - kc;
-            const float q = q_of_k(R, tq4[xb >> 2], xb & 3, S);
-            const float g = (q <= G.T) ? ex2_approx(-q) : 0.0f;
-            const float h = fmaf(R.v, av[xb].x, -av[xb].y) * g;
-            acc[9] = fmaf(av[xb].x, g, acc[9]);
-            s0 += h;
-            s1 = fmaf(h, kp, s1);
-            s2 = fmaf(h, kp * kp, s2);
-        }
-        acc[10] += s0;
-        acc[0] += s1;
-        acc[1] = fmaf(dy, s0, acc[1]);
-        acc[2] = fmaf(dz, s0, acc[2]);
-        acc[3] += s2;
-        acc[6] = fmaf(dy, s1, acc[6]);
-        acc[7] = fmaf(dz, s1, acc[7]);
+        const float2 dy2 = f2(dy, dy), dz2 = f2(dz, dz);
+        A.h = add2(A.h, rs);
+        A.p1 = add2(A.p1, m1);
+        A.pq = add2(A.pq, qs);
+        A.hy = fma2(dy2, rs, A.hy);
+        A.hz = fma2(dz2, rs, A.hz);
+        A.p1y = fma2(dy2, m1, A.p1y);
+        A.p1z = fma2(dz2, m1, A.p1z);
+        const float s0 = rs.x + rs.y;
         const float ty = dy * s0;
-        acc[4] = fmaf(ty, dy, acc[4]);
-        acc[8] = fmaf(ty, dz, acc[8]);
-        acc[5] = fmaf(dz * s0, dz, acc[5]);
+        A.yy = fmaf(ty, dy, A.yy);
+        A.yz = fmaf(ty, dz, A.yz);
+        A.zz = fmaf(dz * s0, dz, A.zz);
     }
 }
 
@@ -357,7 +383,7 @@ __global__ void __launch_bounds__(kBwdThreads, 8) k_render_bwd(
     float* __restrict__ part, float* __restrict__ gacc) {
     pdl_enter();
     __shared__ float4 srec[kBwdThreads][REC_F4];
-    __shared__ __align__(16) float2 sfac[kBwdStage][kMaxBrickVoxels];
+    __shared__ float4 sfac[kBwdStage][kMaxBrickVoxels / 2 + kMaxBrickVoxels / 16];
     __shared__ unsigned long long smask[kBwdThreads];
     __shared__ unsigned short sorder[kBwdThreads];
     __shared__ unsigned char sstage[kBwdThreads];
@@ -433,30 +459,41 @@ __global__ void __launch_bounds__(kBwdThreads, 8) k_render_bwd(
         }
     }
     // per-voxel factors of the first kBwdStage bricks into shared memory, zero outside the
-    // grid, so the row loop needs no range tests
+    // grid, so the row loop needs no range tests; per row and voxel pair (p, p + bx/2) one
+    // float4 (alpha_p, alpha_{p+bx/2}, -alpha I'_p, -alpha I'_{p+bx/2}), float4 index
+    // i = row * bx/2 + p stored at i + i/8 (rows of the lanes of a warp fall on other banks)
     const int n_stage = min(n_bricks, kBwdStage);
-    const int bvox = BX * G.bsy * G.bsz;
+    constexpr int kPairs = BX / 2;
+    const int bpairs = kPairs * G.bsy * G.bsz;
     for (int k = 0; k < n_stage; ++k) {
         const int b = sbrick[k];
         const int x0 = (b % G.nbx) * BX, y0 = ((b / G.nbx) % G.nby) * G.bsy,
                   z0 = (b / (G.nbx * G.nby)) * G.bsz;
+        float4* dst = reinterpret_cast<float4*>(&sfac[k][0]);
         if (x0 + BX <= G.nx && y0 + G.bsy <= G.ny && z0 + G.bsz <= G.nz && (G.nx & 1) == 0) {
-            // brick inside the grid, rows 16-byte aligned: one float4 (two voxels) per load
-            constexpr int kPerRow = BX / 2;
-            float4* dst = reinterpret_cast<float4*>(&sfac[k][0]);
-            for (int e = tid; e < bvox / 2; e += kBwdThreads) {
-                const int r = e / kPerRow, c = e - r * kPerRow;
+            // brick inside the grid, rows 16-byte aligned: float4 loads of voxels (2c, 2c+1)
+            // and (2c+P, 2c+P+1) give the entries of pairs 2c and 2c+1
+            constexpr int kHalf = kPairs / 2;
+            for (int e = tid; e < bpairs / 2; e += kBwdThreads) {
+                const int r = e / kHalf, c = e - r * kHalf;
                 const int y = y0 + (r & G.bsy_mask), z = z0 + (r >> G.bsy_shift);
-                dst[e] = *reinterpret_cast<const float4*>(aip + (int64_t(z) * G.ny + y) * G.nx + x0 + 2 * c);
+                const float2* src = aip + (int64_t(z) * G.ny + y) * G.nx + x0 + 2 * c;
+                const float4 fa = *reinterpret_cast<const float4*>(src);
+                const float4 fb = *reinterpret_cast<const float4*>(src + kPairs);
+                dst[r * kPairs + ((r * kPairs) >> 3) + 2 * c] = make_float4(fa.x, fb.x, -fa.y, -fb.y);
+                dst[r * kPairs + ((r * kPairs) >> 3) + 2 * c + 1] = make_float4(fa.z, fb.z, -fa.w, -fb.w);
             }
             continue;
         }
-        for (int e = tid; e < bvox; e += kBwdThreads) {
-            const int xb = e % BX, r = e / BX;
-            const int x = x0 + xb, y = y0 + (r & G.bsy_mask), z = z0 + (r >> G.bsy_shift);
-            sfac[k][e] = (x < G.nx && y < G.ny && z < G.nz)
-                             ? aip[(int64_t(z) * G.ny + y) * G.nx + x]
-                             : make_float2(0.f, 0.f);
+        for (int e = tid; e < bpairs; e += kBwdThreads) {
+            const int r = e / kPairs, pp = e - r * kPairs;
+            const int y = y0 + (r & G.bsy_mask), z = z0 + (r >> G.bsy_shift);
+            const int xa = x0 + pp, xb = xa + kPairs;
+            const float2* src = aip + (int64_t(min(z, G.nz - 1)) * G.ny + min(y, G.ny - 1)) * G.nx;
+            const bool row_ok = y < G.ny && z < G.nz;
+            const float2 fa = (row_ok && xa < G.nx) ? src[xa] : make_float2(0.f, 0.f);
+            const float2 fb = (row_ok && xb < G.nx) ? src[xb] : make_float2(0.f, 0.f);
+            dst[e + (e >> 3)] = make_float4(fa.x, fb.x, -fa.y, -fb.y);
         }
     }
     __syncthreads();
@@ -473,21 +510,26 @@ __global__ void __launch_bounds__(kBwdThreads, 8) k_render_bwd(
     const Rec R = load_rec_bwd(srec[lt]);
     const unsigned long long m = smask[lt];
     const bool any = m != 0ull;
-    // acc: m1 (x, y, z), m2 (xx, yy, zz, xy, xz, yz), sum alpha g, sum h
-    float acc[11];
-#pragma unroll
-    for (int k = 0; k < 11; ++k) acc[k] = 0.f;
+    AdjAcc A;
+    A.h = A.hy = A.hz = A.p1 = A.p1y = A.p1z = A.pq = A.ag = f2(0.f, 0.f);
+    A.yy = A.zz = A.yz = 0.f;
     if (stage < kBwdStage)
-        adjoint_rows<BX, true>(R, m, G, x0, y0, z0, &sfac[stage][0], aip, acc);
+        adjoint_rows<BX, true>(R, m, G, x0, y0, z0, reinterpret_cast<const float4*>(&sfac[stage][0]),
+                               aip, A);
     else
-        adjoint_rows<BX, false>(R, m, G, x0, y0, z0, nullptr, aip, acc);
-    // x moments about the mean from those about the row centre: u = uc + k'
-    const float uc = ux_base(R, x0) + 0.5f * float(BX - 1);
-    float m1x = fmaf(uc, acc[10], acc[0]);
-    float m2xx = fmaf(uc, fmaf(uc, acc[10], 2.0f * acc[0]), acc[3]);
-    float m2xy = fmaf(uc, acc[1], acc[6]), m2xz = fmaf(uc, acc[2], acc[7]);
-    float m1y = acc[1], m1z = acc[2], m2yy = acc[4], m2zz = acc[5], m2yz = acc[8];
-    const float dvp = acc[9], dr = acc[10];
+        adjoint_rows<BX, false>(R, m, G, x0, y0, z0, nullptr, aip, A);
+    // moments about the mean: slot p of element e sits at u = uc_e + p along x
+    const float uc0 = ux_base(R, x0);
+    const float uc1 = (BX >= 8) ? ux_base(R, x0 + BX / 2) : uc0 + 2.0f;
+    float m1x = fmaf(uc0, A.h.x, A.p1.x) + fmaf(uc1, A.h.y, A.p1.y);
+    // sum h u^2 = uc^2 sum h + 2 uc sum h p + (2 pq - p1)
+    float m2xx = fmaf(uc0, fmaf(uc0, A.h.x, 2.0f * A.p1.x), fmaf(2.0f, A.pq.x, -A.p1.x)) +
+                 fmaf(uc1, fmaf(uc1, A.h.y, 2.0f * A.p1.y), fmaf(2.0f, A.pq.y, -A.p1.y));
+    float m2xy = fmaf(uc0, A.hy.x, A.p1y.x) + fmaf(uc1, A.hy.y, A.p1y.y);
+    float m2xz = fmaf(uc0, A.hz.x, A.p1z.x) + fmaf(uc1, A.hz.y, A.p1z.y);
+    float m1y = A.hy.x + A.hy.y, m1z = A.hz.x + A.hz.y;
+    float m2yy = A.yy, m2zz = A.zz, m2yz = A.yz;
+    const float dvp = A.ag.x + A.ag.y, dr = A.h.x + A.h.y;
     const float rr = R.r;
     const float dv = rr * dvp;
     m1x *= rr; m1y *= rr; m1z *= rr;
