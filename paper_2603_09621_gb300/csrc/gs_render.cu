@@ -13,7 +13,8 @@
 // ballot (triangle inequality in whitened space: |M (p - mu)| >= |M (c - mu)| - rho4, with
 // rho4 the whitened radius of the footprint around its centre c, so a footprint whose centre
 // is farther than sqrt(T) + rho4 is missed; a margin absorbs FP32 rounding) and evaluates the
-// hits in ascending Gaussian id, accumulating S and W in registers (deterministic).
+// hits in ascending Gaussian id, accumulating S and W in registers (deterministic; one packed
+// FFMA2 updates a voxel's (S, W) with (v r, r) g).
 // Adjoint: one thread per (brick, Gaussian) pair evaluates the brick rows the Gaussian
 // reaches (the row shadow, per z-row a quadratic in dy), each row as bx predicated voxel
 // slots, so lanes never diverge inside a row. A block takes 128 consecutive brick-major pairs
@@ -127,6 +128,13 @@ __device__ __forceinline__ bool foot_hit(const float4* s, float cx, float cy, fl
     return sqrt_approx(fmaxf(qc, 0.0f)) - R.rho4 <= sqrtTcull;
 }
 
+// Packed FP32x2 arithmetic (one FFMA2 / FADD2 / FMUL2 instruction for two single-precision
+// operations; each element is rounded exactly as the scalar fmaf / + / *).
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
 // ------------------------------------------------------------------------ forward
 
 template <bool kStats>
@@ -153,7 +161,9 @@ __global__ void __launch_bounds__(128, 14) k_render_fwd(const int32_t* __restric
     const float cx = float(ox) + 1.5f, cy = float(oy) + 1.5f, cz = float(oz) + 1.5f;
     const unsigned half_sel = (lane < 16) ? 0x0000ffffu : 0xffff0000u;
 
-    float S[4] = {0.f, 0.f, 0.f, 0.f}, Wt[4] = {0.f, 0.f, 0.f, 0.f};
+    float2 SW[4];  // (S, W) of the lane's four voxels
+#pragma unroll
+    for (int xi = 0; xi < 4; ++xi) SW[xi] = f2(0.f, 0.f);
     unsigned long long n_eff = 0, n_eval = 0;
     const int start = brick_off[b], end = brick_off[b + 1];
     for (int c0 = start; c0 < end; c0 += kFwdChunk) {
@@ -180,13 +190,13 @@ __global__ void __launch_bounds__(128, 14) k_render_fwd(const int32_t* __restric
                     float dy, dz, Sr, dxs;
                     row_terms(R, fy, fz, dy, dz, Sr, dxs);
                     const float tq0 = tq_base(R, ox, dxs);
+                    const float2 vrr = f2(R.vr, R.r);
 #pragma unroll
                     for (int xi = 0; xi < 4; ++xi) {
                         const float q = q_of_k(R, tq0, xi, Sr);
                         if (q <= G.T) {
                             const float g = ex2_approx(-q);
-                            S[xi] = fmaf(R.vr, g, S[xi]);
-                            Wt[xi] = fmaf(R.r, g, Wt[xi]);
+                            SW[xi] = fma2(vrr, f2(g, g), SW[xi]);
                         }
                         if (kStats) {
                             n_eff += (y < G.ny && z < G.nz && ox + xi < G.nx && q <= G.T) ? 1 : 0;
@@ -201,16 +211,16 @@ __global__ void __launch_bounds__(128, 14) k_render_fwd(const int32_t* __restric
         const int64_t row = (int64_t(z) * G.ny + y) * G.nx + ox;
         float Iv[4];
 #pragma unroll
-        for (int xi = 0; xi < 4; ++xi) Iv[xi] = S[xi] / (Wt[xi] > G.eps ? Wt[xi] : G.eps);
+        for (int xi = 0; xi < 4; ++xi) Iv[xi] = SW[xi].x / (SW[xi].y > G.eps ? SW[xi].y : G.eps);
         if (ox + 3 < G.nx && (G.nx & 3) == 0) {
             *reinterpret_cast<float4*>(I + row) = make_float4(Iv[0], Iv[1], Iv[2], Iv[3]);
-            *reinterpret_cast<float4*>(W + row) = make_float4(Wt[0], Wt[1], Wt[2], Wt[3]);
+            *reinterpret_cast<float4*>(W + row) = make_float4(SW[0].y, SW[1].y, SW[2].y, SW[3].y);
         } else {
 #pragma unroll
             for (int xi = 0; xi < 4; ++xi)
                 if (ox + xi < G.nx) {
                     I[row + xi] = Iv[xi];
-                    W[row + xi] = Wt[xi];
+                    W[row + xi] = SW[xi].y;
                 }
         }
     }
@@ -273,13 +283,6 @@ __global__ void __launch_bounds__(256) k_bwd_prep(const float* __restrict__ Iv,
         aip[i] = make_float2(al, (w > eps) ? al * Iv[i] : 0.0f);
     }
 }
-
-// Packed FP32x2 arithmetic (one FFMA2 / FADD2 / FMUL2 instruction for two single-precision
-// operations; each element is rounded exactly as the scalar fmaf / + / *).
-__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
 // Adjoint sums of one (brick, Gaussian) pair, with h = gamma g (gamma = dL/dw) per voxel.
 // A brick row of bx voxels is taken as bx/2 voxel pairs (p, p + bx/2); element e of a float2
