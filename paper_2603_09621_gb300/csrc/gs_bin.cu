@@ -358,8 +358,8 @@ __global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ pa
         v = A * T;
         r = 1.0f;
     }
-    r4[0] = make_float4(mh[0], mh[1], mh[2], ml[0]);
-    r4[1] = make_float4(ml[1], ml[2], Pyy, P2yz);
+    r4[0] = make_float4(-mh[0], -ml[0], -mh[1], -mh[2]);
+    r4[1] = make_float4(-ml[1], -ml[2], Pyy, P2yz);
     r4[2] = make_float4(Pzz, -d1, -d2, nrm[0]);
     // radius of a 4^3 footprint in whitened units: |M d|^2 <= sum_jk |m_j . m_k| (3/2)^2
     float gsum = 0.0f;

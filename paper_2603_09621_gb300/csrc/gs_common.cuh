@@ -13,8 +13,9 @@ namespace gs {
 // Per-Gaussian record (20 floats = 5 float4, 80 bytes) written by the preprocess kernel and
 // staged into shared memory by the render kernels. Coordinates are voxel-index space: voxel
 // (i, j, k) sits at (i, j, k). The mean mu' = (mu - o) / h - 1/2 is a float head plus a
-// float tail (double-float arithmetic), so d = (i - head) - tail is accurate to one rounding
-// of d even at large coordinates.
+// float tail (double-float arithmetic), stored negated, so d = (i + (-head)) + (-tail) =
+// (i - head) - tail is accurate to one rounding of d even at large coordinates, and the
+// (y, z) components of a row's offset are one packed pair of additions.
 // The exponent q = (log2 e / 2) d^T Sigma'^{-1} d (Sigma' the covariance in voxel units, the
 // Gaussian kernel is 2^-q) is stored by completing the square along x:
 //     q(dx, dy, dz) = S(dy, dz) + (sa (dx - dx*(dy, dz)))^2,
@@ -29,8 +30,9 @@ namespace gs {
 // rho4 bounds |M (p - c)| over a 4 x 4 x 4 voxel footprint around its centre c:
 // |M d|^2 <= sum_jk |m_j . m_k| |d_j| |d_k| <= (3/2)^2 sum_jk |m_j . m_k| (culling).
 enum RecField : int {
-    R_MHX = 0, R_MHY = 1, R_MHZ = 2,        // mu' head
-    R_MLX = 3, R_MLY = 4, R_MLZ = 5,        // mu' tail
+    R_NMHX = 0, R_NMLX = 1,                 // -(mu' head, tail) along x
+    R_NMHY = 2, R_NMHZ = 3,                 // -mu' head along y, z
+    R_NMLY = 4, R_NMLZ = 5,                 // -mu' tail along y, z
     R_PYY = 6, R_P2YZ = 7, R_PZZ = 8,       // row shadow S
     R_C1 = 9, R_C2 = 10,                    // dx* = c1 dy + c2 dz
     R_SA = 11, R_A = 12,                    // sa = |m0| and a = |m0|^2

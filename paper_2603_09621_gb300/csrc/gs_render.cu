@@ -41,6 +41,13 @@ constexpr int kBwdThreads = 128;
 constexpr int kBwdStage = 3;          // bricks of per-voxel factors staged per adjoint block
 constexpr int kMaxBrickVoxels = 512;  // brick volume limit (x * y * z <= 512)
 
+// Packed FP32x2 arithmetic (one FFMA2 / FADD2 / FMUL2 instruction for two single-precision
+// operations; each element is rounded exactly as the scalar fmaf / + / *).
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
 struct RenderGeo {
     int nx, ny, nz;
     int bsx, bsy, bsz;  // brick shape
@@ -54,15 +61,16 @@ struct RenderGeo {
 };
 
 struct Rec {
-    float mhx, mhy, mhz, mlx, mly, mlz;
+    float nmhx, nmlx;        // minus the mean's x head and tail
+    float2 nmh_yz, nml_yz;   // minus the mean's (y, z) head and tail
     float pyy, p2yz, pzz, c1, c2, sa, rho4, vr, r, v;
 };
 
 __device__ __forceinline__ Rec load_rec(const float4* s) {
     const float4 a = s[0], b = s[1], c = s[2], d = s[3], e = s[4];
     Rec R;
-    R.mhx = a.x; R.mhy = a.y; R.mhz = a.z; R.mlx = a.w;
-    R.mly = b.x; R.mlz = b.y; R.pyy = b.z; R.p2yz = b.w;
+    R.nmhx = a.x; R.nmlx = a.y; R.nmh_yz = make_float2(a.z, a.w);
+    R.nml_yz = make_float2(b.x, b.y); R.pyy = b.z; R.p2yz = b.w;
     R.pzz = c.x; R.c1 = c.y; R.c2 = c.z; R.sa = c.w;
     R.rho4 = d.y;
     R.vr = e.x; R.r = e.y; R.v = e.z;
@@ -75,8 +83,8 @@ __device__ __forceinline__ Rec load_rec(const float4* s) {
 __device__ __forceinline__ Rec load_rec_bwd(const float4* s) {
     const float4 a = s[0], b = s[1], c = s[2], e = s[4];
     Rec R;
-    R.mhx = a.x; R.mhy = a.y; R.mhz = a.z; R.mlx = a.w;
-    R.mly = b.x; R.mlz = b.y; R.pyy = b.z; R.p2yz = b.w;
+    R.nmhx = a.x; R.nmlx = a.y; R.nmh_yz = make_float2(a.z, a.w);
+    R.nml_yz = make_float2(b.x, b.y); R.pyy = b.z; R.p2yz = b.w;
     R.pzz = c.x; R.c1 = c.y; R.c2 = c.z; R.sa = c.w;
     R.rho4 = 0.f;
     R.vr = e.x; R.r = e.y; R.v = e.z;
@@ -85,17 +93,19 @@ __device__ __forceinline__ Rec load_rec_bwd(const float4* s) {
 
 // Row quantities of the Gaussian for the row through voxel centres (., y, z): the row shadow
 // S and the position dx* of the row minimum. One operation sequence for both kernels.
-__device__ __forceinline__ void row_terms(const Rec& R, float fy, float fz, float& dy, float& dz,
+__device__ __forceinline__ void row_terms(const Rec& R, float2 fyz, float& dy, float& dz,
                                           float& S, float& dxs) {
-    dy = (fy - R.mhy) - R.mly;
-    dz = (fz - R.mhz) - R.mlz;
+    // (dy, dz) = ((y, z) - head) - tail as one packed pair of additions of the negated mean
+    const float2 d = add2(add2(fyz, R.nmh_yz), R.nml_yz);
+    dy = d.x;
+    dz = d.y;
     S = fmaf(dy, fmaf(R.pyy, dy, R.p2yz * dz), R.pzz * dz * dz);
     dxs = fmaf(R.c1, dy, R.c2 * dz);
 }
 
 // x offset of voxel x from the mean, u = ux_base(R, x & ~3) + (x & 3).
 __device__ __forceinline__ float ux_base(const Rec& R, int x4) {
-    return (float(x4) - R.mhx) - R.mlx;
+    return (float(x4) + R.nmhx) + R.nmlx;
 }
 
 // Scaled x offset of voxel x = x4 + k (x4 = x & ~3) from the row minimum, tq = sa (u - dx*),
@@ -113,7 +123,7 @@ __device__ __forceinline__ float q_of_k(const Rec& R, float tq0, int k, float S)
 
 // q at the point with (fractional) x index fx, given the row terms (footprint culling).
 __device__ __forceinline__ float q_at(const Rec& R, float fx, float S, float dxs) {
-    const float tq = R.sa * (((fx - R.mhx) - R.mlx) - dxs);
+    const float tq = R.sa * (((fx + R.nmhx) + R.nmlx) - dxs);
     return fmaf(tq, tq, S);
 }
 
@@ -123,17 +133,10 @@ __device__ __forceinline__ bool foot_hit(const float4* s, float cx, float cy, fl
                                          float sqrtTcull) {
     const Rec R = load_rec(s);
     float dy, dz, S, dxs;
-    row_terms(R, cy, cz, dy, dz, S, dxs);
+    row_terms(R, f2(cy, cz), dy, dz, S, dxs);
     const float qc = q_at(R, cx, S, dxs);
     return sqrt_approx(fmaxf(qc, 0.0f)) - R.rho4 <= sqrtTcull;
 }
-
-// Packed FP32x2 arithmetic (one FFMA2 / FADD2 / FMUL2 instruction for two single-precision
-// operations; each element is rounded exactly as the scalar fmaf / + / *).
-__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
 // ------------------------------------------------------------------------ forward
 
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(128, 14) k_render_fwd(const int32_t* __restric
     const int wx = f % G.fx, wy = (f / G.fx) % G.fy, wz = f / (G.fx * G.fy);
     const int ox = bx * G.bsx + wx * 4, oy = by * G.bsy + wy * 4, oz = bz * G.bsz + wz * 4;
     const int y = oy + (l16 & 3), z = oz + (l16 >> 2);
-    const float fy = float(y), fz = float(z);
+    const float2 fyz = f2(float(y), float(z));
     const float cx = float(ox) + 1.5f, cy = float(oy) + 1.5f, cz = float(oz) + 1.5f;
     const unsigned half_sel = (lane < 16) ? 0x0000ffffu : 0xffff0000u;
 
@@ -188,7 +191,7 @@ __global__ void __launch_bounds__(128, 14) k_render_fwd(const int32_t* __restric
                     mask &= mask - 1;
                     const Rec R = load_rec(srec[kk]);
                     float dy, dz, Sr, dxs;
-                    row_terms(R, fy, fz, dy, dz, Sr, dxs);
+                    row_terms(R, fyz, dy, dz, Sr, dxs);
                     const float tq0 = tq_base(R, ox, dxs);
                     const float2 vrr = f2(R.vr, R.r);
 #pragma unroll
@@ -246,14 +249,14 @@ __global__ void __launch_bounds__(128, 14) k_render_fwd(const int32_t* __restric
 __device__ __forceinline__ unsigned long long brick_row_mask(const Rec& R, const RenderGeo& G,
                                                              int y0, int z0) {
     unsigned long long mask = 0;
-    const float mu_y = R.mhy + R.mly;
+    const float mu_y = -(R.nmh_yz.x + R.nml_yz.x);
     const float ipyy = __fdividef(1.0f, R.pyy);
     const float k1 = -0.5f * (R.p2yz * ipyy);
     const float c3 = (R.pzz - 0.25f * R.p2yz * (R.p2yz * ipyy)) * ipyy;
     const float h0 = G.Tcull * ipyy;
     const float pad = 1e-3f + 1e-5f * fabsf(mu_y);
     for (int rz = 0; rz < G.bsz; ++rz) {
-        const float dz = (float(z0 + rz) - R.mhz) - R.mlz;
+        const float dz = (float(z0 + rz) + R.nmh_yz.y) + R.nml_yz.y;
         const float hw2 = fmaf(-c3 * dz, dz, h0);
         if (!(hw2 >= 0.0f)) continue;
         const float hw = sqrt_approx(hw2) + pad;
@@ -321,7 +324,7 @@ __device__ __forceinline__ void adjoint_rows(const Rec& R, unsigned long long m,
         m &= m - 1;
         const int y = y0 + (r & G.bsy_mask), z = z0 + (r >> G.bsy_shift);
         float dy, dz, S, dxs;
-        row_terms(R, float(y), float(z), dy, dz, S, dxs);
+        row_terms(R, f2(float(y), float(z)), dy, dz, S, dxs);
         const float2 S2 = f2(S, S), nd2 = f2(-dxs, -dxs);
         float2 tq0[NT];  // tq_base of each group, the forward's sa * (ux - dx*)
 #pragma unroll
