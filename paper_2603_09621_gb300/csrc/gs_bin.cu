@@ -359,8 +359,8 @@ __global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ pa
         r = 1.0f;
     }
     r4[0] = make_float4(-mh[0], -ml[0], -mh[1], -mh[2]);
-    r4[1] = make_float4(-ml[1], -ml[2], Pyy, P2yz);
-    r4[2] = make_float4(Pzz, -d1, -d2, nrm[0]);
+    r4[1] = make_float4(-ml[1], -ml[2], P2yz, -d2);
+    r4[2] = make_float4(Pyy, -d1, Pzz, nrm[0]);
     // radius of a 4^3 footprint in whitened units: |M d|^2 <= sum_jk |m_j . m_k| (3/2)^2
     float gsum = 0.0f;
 #pragma unroll
@@ -369,7 +369,17 @@ __global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ pa
         for (int k = 0; k < 3; ++k)
             gsum += fabsf(col[j][0] * col[k][0] + col[j][1] * col[k][1] + col[j][2] * col[k][2]);
     const float rho4 = 1.5f * sqrtf(gsum);
-    r4[3] = make_float4(am0, rho4, nrm[1], nrm[2]);
+    // half-extents of the truncated ellipsoid's box in voxels, widened by 1 % and by a 4^3
+    // footprint's half-width: a footprint whose centre is farther along an axis is missed
+    float ext[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float sig = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) sig += (R[k][j] * s[j]) * (R[k][j] * s[j]);
+        ext[k] = 1.01f * trunc_sigma * sqrtf(sig) * G.ih[k] + 1.5f + 1e-3f;
+    }
+    r4[3] = make_float4(ext[0], rho4, ext[1], ext[2]);
     r4[4] = make_float4(v * r, r, v, 0.0f);
 }
 

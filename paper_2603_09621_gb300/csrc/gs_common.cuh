@@ -20,7 +20,9 @@ namespace gs {
 // Gaussian kernel is 2^-q) is stored by completing the square along x:
 //     q(dx, dy, dz) = S(dy, dz) + (sa (dx - dx*(dy, dz)))^2,
 //     S(dy, dz) = Pyy dy^2 + P2yz dy dz + Pzz dz^2   (the minimum of q along the x-row),
-//     dx*(dy, dz) = c1 dy + c2 dz                      (where that minimum is reached).
+//     dx*(dy, dz) = c1 dy + c2 dz                      (where that minimum is reached);
+// (P2yz, c2) and (Pyy, c1) sit side by side, so (Pyy dy + P2yz dz, c1 dy + c2 dz) is one
+// packed multiply and one packed FMA.
 // With M = sqrt(log2 e / 2) diag(1/s) R^T H (columns m0, m1, m2, the whitened steps of one
 // voxel along x, y, z): sa = |m0| (the whitened length of one voxel step along x),
 // c_j = -(m_j . m0) / |m0|^2, and S is the Gram form of m1, m2 with their components along m0
@@ -29,15 +31,19 @@ namespace gs {
 // Gaussians, and the value at a voxel depends only on the voxel and the Gaussian.
 // rho4 bounds |M (p - c)| over a 4 x 4 x 4 voxel footprint around its centre c:
 // |M d|^2 <= sum_jk |m_j . m_k| |d_j| |d_k| <= (3/2)^2 sum_jk |m_j . m_k| (culling).
+// ext_k = 1.01 trunc_sigma sigma_k + 3/2 + 10^-3 (sigma_k the standard deviation along axis k
+// in voxels) bounds the offset of a 4^3 footprint's centre from the mean when the truncated
+// ellipsoid reaches one of its voxels (culling).
 enum RecField : int {
     R_NMHX = 0, R_NMLX = 1,                 // -(mu' head, tail) along x
     R_NMHY = 2, R_NMHZ = 3,                 // -mu' head along y, z
     R_NMLY = 4, R_NMLZ = 5,                 // -mu' tail along y, z
-    R_PYY = 6, R_P2YZ = 7, R_PZZ = 8,       // row shadow S
-    R_C1 = 9, R_C2 = 10,                    // dx* = c1 dy + c2 dz
-    R_SA = 11, R_A = 12,                    // sa = |m0| and a = |m0|^2
+    R_P2YZ = 6, R_C2 = 7,                   // dz coefficients of the row terms (S, dx*)
+    R_PYY = 8, R_C1 = 9,                    // their dy coefficients
+    R_PZZ = 10, R_SA = 11,                  // dz^2 coefficient of S; sa = |m0|
+    R_EXTX = 12,                            // box half-extent along x (see below)
     R_RHO4 = 13,                            // footprint radius (see above)
-    R_N1 = 14, R_N2 = 15,                   // |m1|, |m2| (unused by the kernels)
+    R_EXTY = 14, R_EXTZ = 15,               // box half-extents along y, z
     R_VR = 16,                              // v * r
     R_R = 17,                               // r
     R_V = 18,                               // v

@@ -12,7 +12,8 @@
 // x-row of four voxels. A half-warp tests 16 staged Gaussians against its footprint with one
 // ballot (triangle inequality in whitened space: |M (p - mu)| >= |M (c - mu)| - rho4, with
 // rho4 the whitened radius of the footprint around its centre c, so a footprint whose centre
-// is farther than sqrt(T) + rho4 is missed; a margin absorbs FP32 rounding) and evaluates the
+// is farther than sqrt(T) + rho4 is missed; so is one whose centre lies outside the truncated
+// ellipsoid's bounding box widened by 3/2 along an axis; a margin absorbs FP32 rounding) and evaluates the
 // hits in ascending Gaussian id, accumulating S and W in registers (deterministic; one packed
 // FFMA2 updates a voxel's (S, W) with (v r, r) g).
 // Adjoint: one thread per (brick, Gaussian) pair evaluates the brick rows the Gaussian
@@ -63,16 +64,20 @@ struct RenderGeo {
 struct Rec {
     float nmhx, nmlx;        // minus the mean's x head and tail
     float2 nmh_yz, nml_yz;   // minus the mean's (y, z) head and tail
-    float pyy, p2yz, pzz, c1, c2, sa, rho4, vr, r, v;
+    float2 pc2;              // (P2yz, c2): the dz coefficients of the row terms
+    float2 pyc1;             // (Pyy, c1): their dy coefficients
+    float pzz, sa, rho4, vr, r, v;
+    float ex, ey, ez;        // footprint-centre box half-extents (culling)
 };
 
 __device__ __forceinline__ Rec load_rec(const float4* s) {
     const float4 a = s[0], b = s[1], c = s[2], d = s[3], e = s[4];
     Rec R;
     R.nmhx = a.x; R.nmlx = a.y; R.nmh_yz = make_float2(a.z, a.w);
-    R.nml_yz = make_float2(b.x, b.y); R.pyy = b.z; R.p2yz = b.w;
-    R.pzz = c.x; R.c1 = c.y; R.c2 = c.z; R.sa = c.w;
+    R.nml_yz = make_float2(b.x, b.y); R.pc2 = make_float2(b.z, b.w);
+    R.pyc1 = make_float2(c.x, c.y); R.pzz = c.z; R.sa = c.w;
     R.rho4 = d.y;
+    R.ex = d.x; R.ey = d.z; R.ez = d.w;
     R.vr = e.x; R.r = e.y; R.v = e.z;
     return R;
 }
@@ -84,9 +89,10 @@ __device__ __forceinline__ Rec load_rec_bwd(const float4* s) {
     const float4 a = s[0], b = s[1], c = s[2], e = s[4];
     Rec R;
     R.nmhx = a.x; R.nmlx = a.y; R.nmh_yz = make_float2(a.z, a.w);
-    R.nml_yz = make_float2(b.x, b.y); R.pyy = b.z; R.p2yz = b.w;
-    R.pzz = c.x; R.c1 = c.y; R.c2 = c.z; R.sa = c.w;
+    R.nml_yz = make_float2(b.x, b.y); R.pc2 = make_float2(b.z, b.w);
+    R.pyc1 = make_float2(c.x, c.y); R.pzz = c.z; R.sa = c.w;
     R.rho4 = 0.f;
+    R.ex = R.ey = R.ez = 0.f;
     R.vr = e.x; R.r = e.y; R.v = e.z;
     return R;
 }
@@ -99,8 +105,10 @@ __device__ __forceinline__ void row_terms(const Rec& R, float2 fyz, float& dy, f
     const float2 d = add2(add2(fyz, R.nmh_yz), R.nml_yz);
     dy = d.x;
     dz = d.y;
-    S = fmaf(dy, fmaf(R.pyy, dy, R.p2yz * dz), R.pzz * dz * dz);
-    dxs = fmaf(R.c1, dy, R.c2 * dz);
+    // (Pyy dy + P2yz dz, c1 dy + c2 dz) as one packed multiply and one packed FMA
+    const float2 t = fma2(R.pyc1, f2(dy, dy), mul2(R.pc2, f2(dz, dz)));
+    S = fmaf(dy, t.x, R.pzz * dz * dz);
+    dxs = t.y;
 }
 
 // x offset of voxel x from the mean, u = ux_base(R, x & ~3) + (x & 3).
@@ -121,21 +129,20 @@ __device__ __forceinline__ float q_of_k(const Rec& R, float tq0, int k, float S)
     return fmaf(tq, tq, S);
 }
 
-// q at the point with (fractional) x index fx, given the row terms (footprint culling).
-__device__ __forceinline__ float q_at(const Rec& R, float fx, float S, float dxs) {
-    const float tq = R.sa * (((fx + R.nmhx) + R.nmlx) - dxs);
-    return fmaf(tq, tq, S);
-}
-
 // Footprint cull: may the Gaussian reach a voxel centre within 3/2 of (cx, cy, cz) per axis?
+// Two conservative tests: the whitened triangle inequality, and the footprint centre's offset
+// from the mean against the truncated ellipsoid's box widened by the footprint's half-width.
 // (An approximate square root suffices: Tcull carries a 1 % margin over T.)
 __device__ __forceinline__ bool foot_hit(const float4* s, float cx, float cy, float cz,
                                          float sqrtTcull) {
     const Rec R = load_rec(s);
     float dy, dz, S, dxs;
     row_terms(R, f2(cy, cz), dy, dz, S, dxs);
-    const float qc = q_at(R, cx, S, dxs);
-    return sqrt_approx(fmaxf(qc, 0.0f)) - R.rho4 <= sqrtTcull;
+    const float ux = (cx + R.nmhx) + R.nmlx;
+    const float tq = R.sa * (ux - dxs);
+    const float qc = fmaf(tq, tq, S);
+    return (sqrt_approx(fmaxf(qc, 0.0f)) - R.rho4 <= sqrtTcull) & (fabsf(ux) <= R.ex) &
+           (fabsf(dy) <= R.ey) & (fabsf(dz) <= R.ez);
 }
 
 // ------------------------------------------------------------------------ forward
@@ -250,9 +257,9 @@ __device__ __forceinline__ unsigned long long brick_row_mask(const Rec& R, const
                                                              int y0, int z0) {
     unsigned long long mask = 0;
     const float mu_y = -(R.nmh_yz.x + R.nml_yz.x);
-    const float ipyy = __fdividef(1.0f, R.pyy);
-    const float k1 = -0.5f * (R.p2yz * ipyy);
-    const float c3 = (R.pzz - 0.25f * R.p2yz * (R.p2yz * ipyy)) * ipyy;
+    const float ipyy = __fdividef(1.0f, R.pyc1.x);
+    const float k1 = -0.5f * (R.pc2.x * ipyy);
+    const float c3 = (R.pzz - 0.25f * R.pc2.x * (R.pc2.x * ipyy)) * ipyy;
     const float h0 = G.Tcull * ipyy;
     const float pad = 1e-3f + 1e-5f * fabsf(mu_y);
     for (int rz = 0; rz < G.bsz; ++rz) {
