@@ -253,20 +253,32 @@ __global__ void __launch_bounds__(128, 14) k_render_fwd(const int32_t* __restric
 // shadow S(dy, dz) <= Tcull holds on the y-interval yc(dz) +- hw(dz), with
 // yc = mu_y - (P2yz / 2 Pyy) dz and hw^2 = Tcull / Pyy - c3 dz^2,
 // c3 = (Pzz - P2yz^2 / 4 Pyy) / Pyy (the interval is padded; Tcull carries a 1 % margin).
+// A z-plane whose section of the truncated ellipsoid misses the brick's x range is skipped.
 __device__ __forceinline__ unsigned long long brick_row_mask(const Rec& R, const RenderGeo& G,
-                                                             int y0, int z0) {
+                                                             int x0, int y0, int z0) {
     unsigned long long mask = 0;
     const float mu_y = -(R.nmh_yz.x + R.nml_yz.x);
+    const float mu_x = -(R.nmhx + R.nmlx);
     const float ipyy = __fdividef(1.0f, R.pyc1.x);
     const float k1 = -0.5f * (R.pc2.x * ipyy);
     const float c3 = (R.pzz - 0.25f * R.pc2.x * (R.pc2.x * ipyy)) * ipyy;
     const float h0 = G.Tcull * ipyy;
     const float pad = 1e-3f + 1e-5f * fabsf(mu_y);
+    // x extent of the section through plane dz: centre mu_x + (c1 k1 + c2) dz, half-width
+    // hw_y sqrt(Pyy / a + c1^2) (hw_y the y half-width of the same section)
+    const float kx = fmaf(R.pyc1.y, k1, R.pc2.y);
+    const float lam = sqrt_approx(fmaf(R.pyc1.x, __fdividef(1.0f, R.sa * R.sa), R.pyc1.y * R.pyc1.y));
+    const float padx = 1e-3f + 1e-5f * fabsf(mu_x);
+    const float xa = float(x0), xb = float(x0 + G.bsx - 1);
     for (int rz = 0; rz < G.bsz; ++rz) {
         const float dz = (float(z0 + rz) + R.nmh_yz.y) + R.nml_yz.y;
         const float hw2 = fmaf(-c3 * dz, dz, h0);
         if (!(hw2 >= 0.0f)) continue;
-        const float hw = sqrt_approx(hw2) + pad;
+        const float sh = sqrt_approx(hw2);
+        const float hwx = fmaf(sh, lam, padx);
+        const float xc = fmaf(kx, dz, mu_x);
+        if (xc + hwx < xa || xc - hwx > xb) continue;
+        const float hw = sh + pad;
         const float yc = fmaf(k1, dz, mu_y);
         int ia = static_cast<int>(ceilf(fmaxf(yc - hw, float(y0) - 1.0f))) - y0;
         int ib = static_cast<int>(floorf(fminf(yc + hw, float(y0 + G.bsy)))) - y0;
@@ -443,7 +455,7 @@ __global__ void __launch_bounds__(kBwdThreads, 8) k_render_bwd(
         srec[tid][1] = src[1];
         srec[tid][2] = src[2];
         srec[tid][4] = src[4];
-        const unsigned long long m = brick_row_mask(load_rec_bwd(srec[tid]), G, by * G.bsy, bz * G.bsz);
+        const unsigned long long m = brick_row_mask(load_rec_bwd(srec[tid]), G, (b_t % G.nbx) * G.bsx, by * G.bsy, bz * G.bsz);
         smask[tid] = m;
         bucket = 64 - __popcll(static_cast<long long>(m));
         atomicAdd(&hist[bucket], 1);
