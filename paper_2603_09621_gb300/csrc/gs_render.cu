@@ -18,11 +18,13 @@
 // FFMA2 updates a voxel's (S, W) with (v r, r) g).
 // Adjoint: one thread per (brick, Gaussian) pair evaluates the brick rows the Gaussian
 // reaches (the row shadow, per z-row a quadratic in dy), each row as bx predicated voxel
-// slots, so lanes never diverge inside a row. A block takes 128 consecutive brick-major pairs
-// (one or two bricks), computes their row masks and counting-sorts them by number of rows in
-// shared memory, so each warp runs pairs of equal length. The per-voxel factors
+// slots, so lanes never diverge inside a row. A block takes 256 consecutive brick-major pairs
+// (one to three bricks), computes their row masks and counting-sorts them by number of rows in
+// shared memory; its four warps then take 32-pair chunks of the sorted list, longest first,
+// from a shared counter, so lanes of a warp run pairs of equal length and a warp that drew
+// short pairs moves on to the next chunk (72 registers without spills, 7 blocks per SM). The per-voxel factors
 // (alpha, alpha I'), alpha = dL/dI / max(W, eps), are precomputed into one float2 volume; a
-// block copies those of its first three bricks into shared memory (zero outside the grid), so
+// block copies those of its first four bricks into shared memory (zero outside the grid), so
 // rows read them without range tests; one 16-byte pad after every 128 bytes spreads the rows
 // that the lanes of a warp read at once over the shared-memory banks. A row's slots are
 // evaluated in packed FP32x2 pairs (FFMA2). Each pair's partial is summed by one thread in a fixed
@@ -39,7 +41,8 @@ namespace gs {
 
 constexpr int kFwdChunk = 128;   // Gaussians staged per forward round
 constexpr int kBwdThreads = 128;
-constexpr int kBwdStage = 3;          // bricks of per-voxel factors staged per adjoint block
+constexpr int kBwdPairs = 256;        // pairs per adjoint block, taken by warps 32 at a time
+constexpr int kBwdStage = 4;          // bricks of per-voxel factors staged per adjoint block
 constexpr int kMaxBrickVoxels = 512;  // brick volume limit (x * y * z <= 512)
 
 // Packed FP32x2 arithmetic (one FFMA2 / FADD2 / FMUL2 instruction for two single-precision
@@ -148,7 +151,7 @@ __device__ __forceinline__ bool foot_hit(const float4* s, float cx, float cy, fl
 // ------------------------------------------------------------------------ forward
 
 template <bool kStats>
-__global__ void __launch_bounds__(128, 14) k_render_fwd(const int32_t* __restrict__ brick_off,
+__global__ void __launch_bounds__(128, 10) k_render_fwd(const int32_t* __restrict__ brick_off,
                                                     const int32_t* __restrict__ pair_gid,
                                                     const float4* __restrict__ rec4, RenderGeo G,
                                                     float* __restrict__ I, float* __restrict__ W,
@@ -401,64 +404,78 @@ __device__ __forceinline__ void adjoint_rows(const Rec& R, unsigned long long m,
 }
 
 template <int BX, bool kDet>
-__global__ void __launch_bounds__(kBwdThreads, 8) k_render_bwd(
+__global__ void __launch_bounds__(kBwdThreads, 7) k_render_bwd(
     const int32_t* __restrict__ pair_gid, const int32_t* __restrict__ pair_gmj,
     const int32_t* __restrict__ pair_brick, const int64_t* __restrict__ npairs, int64_t capacity,
     const float4* __restrict__ rec4, RenderGeo G, const float2* __restrict__ aip,
     float* __restrict__ part, float* __restrict__ gacc) {
     pdl_enter();
-    __shared__ float4 srec[kBwdThreads][REC_F4];
+    constexpr int kPer = kBwdPairs / kBwdThreads;  // pairs per thread in the prologue
+    constexpr int kWarps = kBwdThreads / 32;
     __shared__ float4 sfac[kBwdStage][kMaxBrickVoxels / 2 + kMaxBrickVoxels / 16];
-    __shared__ unsigned long long smask[kBwdThreads];
-    __shared__ unsigned short sorder[kBwdThreads];
-    __shared__ unsigned char sstage[kBwdThreads];
+    __shared__ unsigned long long smask[kBwdPairs];
+    __shared__ int sgid[kBwdPairs];
+    __shared__ unsigned short sorder[kBwdPairs];
+    __shared__ unsigned char sstage[kBwdPairs];
     __shared__ int hist[66];
     __shared__ int cursor[66];
     __shared__ int sbrick[kBwdStage];
-    __shared__ int wcount[kBwdThreads / 32];
+    __shared__ int gcount[kBwdPairs / 32];
+    __shared__ int chunk_next;
     int64_t P = *npairs;
     if (P < 0 || P > capacity) P = 0;
-    const int64_t base = int64_t(blockIdx.x) * kBwdThreads;
+    const int64_t base = int64_t(blockIdx.x) * kBwdPairs;
     if (base >= P) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nvalid = static_cast<int>(min(int64_t(kBwdThreads), P - base));
-    for (int k = tid; k < 66; k += blockDim.x) {
+    const int nvalid = static_cast<int>(min(int64_t(kBwdPairs), P - base));
+    for (int k = tid; k < 66; k += kBwdThreads) {
         hist[k] = 0;
         cursor[k] = 0;
     }
-    // distinct bricks of the block's pairs (brick-major order: a new brick starts a run)
-    int b_t = 0;
-    bool newb = false;
-    if (tid < nvalid) {
-        b_t = pair_brick[base + tid];
-        newb = (tid == 0) || (b_t != pair_brick[base + tid - 1]);
-    }
-    const unsigned bal = __ballot_sync(0xffffffffu, newb);
-    if (lane == 0) wcount[warp] = __popc(bal);
-    __syncthreads();
-    int run_before = 0, n_bricks = 0;
+    if (tid == 0) chunk_next = 0;
+    // distinct bricks of the block's pairs (brick-major order: a new brick starts a run);
+    // thread tid holds pairs tid + h * 128 (32-pair group warp + 4 h)
+    int b_t[kPer];
+    unsigned bal[kPer];
+    bool newb[kPer];
 #pragma unroll
-    for (int w = 0; w < kBwdThreads / 32; ++w) {
-        run_before += (w < warp) ? wcount[w] : 0;
-        n_bricks += wcount[w];
+    for (int h = 0; h < kPer; ++h) {
+        const int q = tid + h * kBwdThreads;
+        b_t[h] = 0;
+        newb[h] = false;
+        if (q < nvalid) {
+            b_t[h] = pair_brick[base + q];
+            newb[h] = (q == 0) || (b_t[h] != pair_brick[base + q - 1]);
+        }
+        bal[h] = __ballot_sync(0xffffffffu, newb[h]);
+        if (lane == 0) gcount[warp + h * kWarps] = __popc(bal[h]);
     }
-    // row mask of this thread's pair, staged record, histogram of row counts (most first)
-    int bucket = 0;
-    if (tid < nvalid) {
-        const int kb = run_before + __popc(bal & ((1u << lane) - 1u)) + (newb ? 1 : 0) - 1;
-        if (newb && kb < kBwdStage) sbrick[kb] = b_t;
-        sstage[tid] = static_cast<unsigned char>(min(kb, kBwdStage));
-        const int64_t i = base + tid;
-        const int by = (b_t / G.nbx) % G.nby, bz = b_t / (G.nbx * G.nby);
-        const float4* src = rec4 + int64_t(pair_gid[i]) * REC_F4;
-        srec[tid][0] = src[0];
-        srec[tid][1] = src[1];
-        srec[tid][2] = src[2];
-        srec[tid][4] = src[4];
-        const unsigned long long m = brick_row_mask(load_rec_bwd(srec[tid]), G, (b_t % G.nbx) * G.bsx, by * G.bsy, bz * G.bsz);
-        smask[tid] = m;
-        bucket = 64 - __popcll(static_cast<long long>(m));
-        atomicAdd(&hist[bucket], 1);
+    __syncthreads();
+    int n_bricks = 0;
+#pragma unroll
+    for (int g = 0; g < kBwdPairs / 32; ++g) n_bricks += gcount[g];
+    // row mask of each pair, its staged brick, histogram of row counts (most first)
+    int bucket[kPer];
+#pragma unroll
+    for (int h = 0; h < kPer; ++h) {
+        const int q = tid + h * kBwdThreads;
+        const int grp = warp + h * kWarps;
+        bucket[h] = 0;
+        if (q < nvalid) {
+            int run_before = 0;
+            for (int g = 0; g < grp; ++g) run_before += gcount[g];
+            const int kb = run_before + __popc(bal[h] & ((1u << lane) - 1u)) + (newb[h] ? 1 : 0) - 1;
+            if (newb[h] && kb < kBwdStage) sbrick[kb] = b_t[h];
+            sstage[q] = static_cast<unsigned char>(min(kb, kBwdStage));
+            const int gid = pair_gid[base + q];
+            sgid[q] = gid;
+            const int by = (b_t[h] / G.nbx) % G.nby, bz = b_t[h] / (G.nbx * G.nby);
+            const unsigned long long m = brick_row_mask(load_rec_bwd(rec4 + int64_t(gid) * REC_F4), G,
+                                                        (b_t[h] % G.nbx) * G.bsx, by * G.bsy, bz * G.bsz);
+            smask[q] = m;
+            bucket[h] = 64 - __popcll(static_cast<long long>(m));
+            atomicAdd(&hist[bucket[h]], 1);
+        }
     }
     __syncthreads();
     if (warp == 0) {  // exclusive prefix of the 65 bucket counts: lane l owns buckets 3l..3l+2
@@ -522,17 +539,30 @@ __global__ void __launch_bounds__(kBwdThreads, 8) k_render_bwd(
         }
     }
     __syncthreads();
-    if (tid < nvalid) sorder[hist[bucket] + atomicAdd(&cursor[bucket], 1)] = static_cast<unsigned short>(tid);
+#pragma unroll
+    for (int h = 0; h < kPer; ++h) {
+        const int q = tid + h * kBwdThreads;
+        if (q < nvalid)
+            sorder[hist[bucket[h]] + atomicAdd(&cursor[bucket[h]], 1)] = static_cast<unsigned short>(q);
+    }
     __syncthreads();
-    if (tid >= nvalid) return;
-
-    const int lt = sorder[tid];
+    // warps take 32-pair chunks of the sorted list (longest first) until none is left, so a
+    // warp that drew short pairs goes on with the next chunk instead of idling
+    const int nchunks = (nvalid + 31) / 32;
+    for (;;) {
+        int c = 0;
+        if (lane == 0) c = atomicAdd(&chunk_next, 1);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= nchunks) break;
+        const int rank = c * 32 + lane;
+        if (rank >= nvalid) continue;
+    const int lt = sorder[rank];
     const int64_t i = base + lt;
     const int b = pair_brick[i];
     const int bx = b % G.nbx, by = (b / G.nbx) % G.nby, bz = b / (G.nbx * G.nby);
     const int x0 = bx * BX, y0 = by * G.bsy, z0 = bz * G.bsz;
     const int stage = sstage[lt];
-    const Rec R = load_rec_bwd(srec[lt]);
+    const Rec R = load_rec_bwd(rec4 + int64_t(sgid[lt]) * REC_F4);
     const unsigned long long m = smask[lt];
     const bool any = m != 0ull;
     AdjAcc A;
@@ -566,10 +596,11 @@ __global__ void __launch_bounds__(kBwdThreads, 8) k_render_bwd(
         dst[1] = make_float4(m2yy, m2zz, m2xy, m2xz);
         dst[2] = make_float4(m2yz, dv, dr, 0.f);
     } else if (any) {
-        float* dst = gacc + int64_t(pair_gid[i]) * GRAD_FLOATS;
+        float* dst = gacc + int64_t(sgid[lt]) * GRAD_FLOATS;
         const float vals[11] = {m1x, m1y, m1z, m2xx, m2yy, m2zz, m2xy, m2xz, m2yz, dv, dr};
 #pragma unroll
         for (int q = 0; q < 11; ++q) atomicAdd(dst + q, vals[q]);
+    }
     }
 }
 
@@ -652,7 +683,7 @@ template <int BX, bool kDet>
 static gs_status launch_bwd_pairs(const gs_bins* bins, const RenderGeo& G, const Workspace& ws,
                                   cudaStream_t st) {
     if (bins->capacity == 0) return GS_OK;
-    const unsigned gb = static_cast<unsigned>((bins->capacity + kBwdThreads - 1) / kBwdThreads);
+    const unsigned gb = static_cast<unsigned>((bins->capacity + kBwdPairs - 1) / kBwdPairs);
     const float4* rec4 = reinterpret_cast<const float4*>(bins->rec);
     launch_k(k_render_bwd<BX, kDet>, dim3(gb), dim3(kBwdThreads), 0, st, bins->pair_gid,
         bins->pair_gmj, bins->pair_brick, bins->d_npairs, bins->capacity, rec4, G, ws.aip,
