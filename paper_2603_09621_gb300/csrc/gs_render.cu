@@ -412,7 +412,10 @@ __global__ void __launch_bounds__(kBwdThreads, 7) k_render_bwd(
     pdl_enter();
     constexpr int kPer = kBwdPairs / kBwdThreads;  // pairs per thread in the prologue
     constexpr int kWarps = kBwdThreads / 32;
-    __shared__ float4 sfac[kBwdStage][kMaxBrickVoxels / 2 + kMaxBrickVoxels / 16];
+    // staged bricks 2 float4 apart beyond their padded size: rows of different bricks that the
+    // lanes of a warp read at once fall on different banks
+    constexpr int kStageStride = kMaxBrickVoxels / 2 + kMaxBrickVoxels / 16 + 2;
+    __shared__ float4 sfac[kBwdStage * kStageStride];
     __shared__ unsigned long long smask[kBwdPairs];
     __shared__ int sgid[kBwdPairs];
     __shared__ unsigned short sorder[kBwdPairs];
@@ -511,7 +514,7 @@ __global__ void __launch_bounds__(kBwdThreads, 7) k_render_bwd(
         const int b = sbrick[k];
         const int x0 = (b % G.nbx) * BX, y0 = ((b / G.nbx) % G.nby) * G.bsy,
                   z0 = (b / (G.nbx * G.nby)) * G.bsz;
-        float4* dst = reinterpret_cast<float4*>(&sfac[k][0]);
+        float4* dst = &sfac[k * kStageStride];
         if (x0 + BX <= G.nx && y0 + G.bsy <= G.ny && z0 + G.bsz <= G.nz && (G.nx & 1) == 0) {
             // brick inside the grid, rows 16-byte aligned: float4 loads of voxels (2c, 2c+1)
             // and (2c+P, 2c+P+1) give the entries of pairs 2c and 2c+1
@@ -569,7 +572,7 @@ __global__ void __launch_bounds__(kBwdThreads, 7) k_render_bwd(
     A.h = A.hy = A.hz = A.p1 = A.p1y = A.p1z = A.pq = A.ag = f2(0.f, 0.f);
     A.yy = A.zz = A.yz = 0.f;
     if (stage < kBwdStage)
-        adjoint_rows<BX, true>(R, m, G, x0, y0, z0, reinterpret_cast<const float4*>(&sfac[stage][0]),
+        adjoint_rows<BX, true>(R, m, G, x0, y0, z0, &sfac[stage * kStageStride],
                                aip, A);
     else
         adjoint_rows<BX, false>(R, m, G, x0, y0, z0, nullptr, aip, A);
