@@ -156,3 +156,27 @@ def test_autograd_function_central_differences():
         lm = float((gs.GaussianRender.apply(pm, og, cfg) * w).double().sum())
         num = (lp - lm) / (2 * h)
         assert abs(ana[i, k] - num) <= 3e-2 * max(abs(num), 1e-2 * np.abs(ana).max()), (i, k)
+
+
+def test_grad_sparse_cloud_unstaged_bricks():
+    """A sparse cloud (about two pairs per brick): each 256-pair adjoint block spans many
+    bricks, so most pairs read their per-voxel factors from the volume instead of the block's
+    four staged bricks. Both reduction modes against the FP64 oracle."""
+    import torch
+    import oracle
+    gs = _gs()
+    og = oracle.Grid(61, 64, 57)
+    d = inputs.gaussian_cloud(21, 350, (57, 64, 61), scale_range=(0.5, 1.5))
+    p = cloud_params(d)
+    # the path is exercised: blocks of 256 consecutive brick-major pairs span > 4 bricks
+    g = _grid(og)
+    _, _, bins, _ = gs.render(to_dev(p), g, gs.Config())
+    torch.cuda.synchronize()
+    pb = bins.pair_brick(bins.npairs()).cpu().numpy()
+    spans = [len(np.unique(pb[i:i + 256])) for i in range(0, len(pb), 256)]
+    assert max(spans) > 4, spans
+    ref_f = oracle.render(p.astype(np.float64), og)
+    dI = masked_dI(22, og, ref_f["amb"])
+    ref = oracle.render_grad(p.astype(np.float64), og, dI.astype(np.float64))
+    for det in (1, 0):
+        check_grad(gpu_grad(p, og, dI, deterministic=det), ref)
