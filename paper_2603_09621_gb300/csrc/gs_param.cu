@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ params, const 
 // order (deterministic mode) or take the atomically accumulated gradient, chain it to the
 // raw parameters (written to grad), and apply Adam to params, m, v.
 template <bool kDet>
-__global__ void __launch_bounds__(256) k_chain_adam(
+__global__ void __launch_bounds__(256, 4) k_chain_adam(
     float* __restrict__ params, float* __restrict__ grad, float* __restrict__ m,
     float* __restrict__ v, const float* __restrict__ part, const float* __restrict__ gacc,
     const int32_t* __restrict__ gm_off, const int64_t* __restrict__ npairs, int64_t capacity,

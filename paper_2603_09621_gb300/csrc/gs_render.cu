@@ -438,16 +438,18 @@ __global__ void __launch_bounds__(kBwdThreads, 7) k_render_bwd(
     if (tid == 0) chunk_next = 0;
     // distinct bricks of the block's pairs (brick-major order: a new brick starts a run);
     // thread tid holds pairs tid + h * 128 (32-pair group warp + 4 h)
-    int b_t[kPer];
+    int b_t[kPer], gidv[kPer];
     unsigned bal[kPer];
     bool newb[kPer];
 #pragma unroll
     for (int h = 0; h < kPer; ++h) {
         const int q = tid + h * kBwdThreads;
         b_t[h] = 0;
+        gidv[h] = 0;
         newb[h] = false;
         if (q < nvalid) {
             b_t[h] = pair_brick[base + q];
+            gidv[h] = pair_gid[base + q];
             newb[h] = (q == 0) || (b_t[h] != pair_brick[base + q - 1]);
         }
         bal[h] = __ballot_sync(0xffffffffu, newb[h]);
@@ -470,7 +472,7 @@ __global__ void __launch_bounds__(kBwdThreads, 7) k_render_bwd(
             const int kb = run_before + __popc(bal[h] & ((1u << lane) - 1u)) + (newb[h] ? 1 : 0) - 1;
             if (newb[h] && kb < kBwdStage) sbrick[kb] = b_t[h];
             sstage[q] = static_cast<unsigned char>(min(kb, kBwdStage));
-            const int gid = pair_gid[base + q];
+            const int gid = gidv[h];
             sgid[q] = gid;
             const int by = (b_t[h] / G.nbx) % G.nby, bz = b_t[h] / (G.nbx * G.nby);
             const unsigned long long m = brick_row_mask(load_rec_bwd(rec4 + int64_t(gid) * REC_F4), G,
