@@ -561,51 +561,51 @@ __global__ void __launch_bounds__(kBwdThreads, 7) k_render_bwd(
         if (c >= nchunks) break;
         const int rank = c * 32 + lane;
         if (rank >= nvalid) continue;
-    const int lt = sorder[rank];
-    const int64_t i = base + lt;
-    const int b = pair_brick[i];
-    const int bx = b % G.nbx, by = (b / G.nbx) % G.nby, bz = b / (G.nbx * G.nby);
-    const int x0 = bx * BX, y0 = by * G.bsy, z0 = bz * G.bsz;
-    const int stage = sstage[lt];
-    const Rec R = load_rec_bwd(rec4 + int64_t(sgid[lt]) * REC_F4);
-    const unsigned long long m = smask[lt];
-    const bool any = m != 0ull;
-    AdjAcc A;
-    A.h = A.hy = A.hz = A.p1 = A.p1y = A.p1z = A.pq = A.ag = f2(0.f, 0.f);
-    A.yy = A.zz = A.yz = 0.f;
-    if (stage < kBwdStage)
-        adjoint_rows<BX, true>(R, m, G, x0, y0, z0, &sfac[stage * kStageStride],
-                               aip, A);
-    else
-        adjoint_rows<BX, false>(R, m, G, x0, y0, z0, nullptr, aip, A);
-    // moments about the mean: slot p of element e sits at u = uc_e + p along x
-    const float uc0 = ux_base(R, x0);
-    const float uc1 = (BX >= 8) ? ux_base(R, x0 + BX / 2) : uc0 + 2.0f;
-    float m1x = fmaf(uc0, A.h.x, A.p1.x) + fmaf(uc1, A.h.y, A.p1.y);
-    // sum h u^2 = uc^2 sum h + 2 uc sum h p + (2 pq - p1)
-    float m2xx = fmaf(uc0, fmaf(uc0, A.h.x, 2.0f * A.p1.x), fmaf(2.0f, A.pq.x, -A.p1.x)) +
-                 fmaf(uc1, fmaf(uc1, A.h.y, 2.0f * A.p1.y), fmaf(2.0f, A.pq.y, -A.p1.y));
-    float m2xy = fmaf(uc0, A.hy.x, A.p1y.x) + fmaf(uc1, A.hy.y, A.p1y.y);
-    float m2xz = fmaf(uc0, A.hz.x, A.p1z.x) + fmaf(uc1, A.hz.y, A.p1z.y);
-    float m1y = A.hy.x + A.hy.y, m1z = A.hz.x + A.hz.y;
-    float m2yy = A.yy, m2zz = A.zz, m2yz = A.yz;
-    const float dvp = A.ag.x + A.ag.y, dr = A.h.x + A.h.y;
-    const float rr = R.r;
-    const float dv = rr * dvp;
-    m1x *= rr; m1y *= rr; m1z *= rr;
-    m2xx *= rr; m2yy *= rr; m2zz *= rr; m2xy *= rr; m2xz *= rr; m2yz *= rr;
-    if (kDet) {
-        const int64_t j = pair_gmj[i];
-        float4* dst = reinterpret_cast<float4*>(part + j * GRAD_FLOATS);
-        dst[0] = make_float4(m1x, m1y, m1z, m2xx);
-        dst[1] = make_float4(m2yy, m2zz, m2xy, m2xz);
-        dst[2] = make_float4(m2yz, dv, dr, 0.f);
-    } else if (any) {
-        float* dst = gacc + int64_t(sgid[lt]) * GRAD_FLOATS;
-        const float vals[11] = {m1x, m1y, m1z, m2xx, m2yy, m2zz, m2xy, m2xz, m2yz, dv, dr};
+        const int lt = sorder[rank];
+        const int64_t i = base + lt;
+        const int b = pair_brick[i];
+        const int bx = b % G.nbx, by = (b / G.nbx) % G.nby, bz = b / (G.nbx * G.nby);
+        const int x0 = bx * BX, y0 = by * G.bsy, z0 = bz * G.bsz;
+        const int stage = sstage[lt];
+        const Rec R = load_rec_bwd(rec4 + int64_t(sgid[lt]) * REC_F4);
+        const unsigned long long m = smask[lt];
+        const bool any = m != 0ull;
+        AdjAcc A;
+        A.h = A.hy = A.hz = A.p1 = A.p1y = A.p1z = A.pq = A.ag = f2(0.f, 0.f);
+        A.yy = A.zz = A.yz = 0.f;
+        if (stage < kBwdStage)
+            adjoint_rows<BX, true>(R, m, G, x0, y0, z0, &sfac[stage * kStageStride],
+                                   aip, A);
+        else
+            adjoint_rows<BX, false>(R, m, G, x0, y0, z0, nullptr, aip, A);
+        // moments about the mean: slot p of element e sits at u = uc_e + p along x
+        const float uc0 = ux_base(R, x0);
+        const float uc1 = (BX >= 8) ? ux_base(R, x0 + BX / 2) : uc0 + 2.0f;
+        float m1x = fmaf(uc0, A.h.x, A.p1.x) + fmaf(uc1, A.h.y, A.p1.y);
+        // sum h u^2 = uc^2 sum h + 2 uc sum h p + (2 pq - p1)
+        float m2xx = fmaf(uc0, fmaf(uc0, A.h.x, 2.0f * A.p1.x), fmaf(2.0f, A.pq.x, -A.p1.x)) +
+                     fmaf(uc1, fmaf(uc1, A.h.y, 2.0f * A.p1.y), fmaf(2.0f, A.pq.y, -A.p1.y));
+        float m2xy = fmaf(uc0, A.hy.x, A.p1y.x) + fmaf(uc1, A.hy.y, A.p1y.y);
+        float m2xz = fmaf(uc0, A.hz.x, A.p1z.x) + fmaf(uc1, A.hz.y, A.p1z.y);
+        float m1y = A.hy.x + A.hy.y, m1z = A.hz.x + A.hz.y;
+        float m2yy = A.yy, m2zz = A.zz, m2yz = A.yz;
+        const float dvp = A.ag.x + A.ag.y, dr = A.h.x + A.h.y;
+        const float rr = R.r;
+        const float dv = rr * dvp;
+        m1x *= rr; m1y *= rr; m1z *= rr;
+        m2xx *= rr; m2yy *= rr; m2zz *= rr; m2xy *= rr; m2xz *= rr; m2yz *= rr;
+        if (kDet) {
+            const int64_t j = pair_gmj[i];
+            float4* dst = reinterpret_cast<float4*>(part + j * GRAD_FLOATS);
+            dst[0] = make_float4(m1x, m1y, m1z, m2xx);
+            dst[1] = make_float4(m2yy, m2zz, m2xy, m2xz);
+            dst[2] = make_float4(m2yz, dv, dr, 0.f);
+        } else if (any) {
+            float* dst = gacc + int64_t(sgid[lt]) * GRAD_FLOATS;
+            const float vals[11] = {m1x, m1y, m1z, m2xx, m2yy, m2zz, m2xy, m2xz, m2yz, dv, dr};
 #pragma unroll
-        for (int q = 0; q < 11; ++q) atomicAdd(dst + q, vals[q]);
-    }
+            for (int q = 0; q < 11; ++q) atomicAdd(dst + q, vals[q]);
+        }
     }
 }
 
