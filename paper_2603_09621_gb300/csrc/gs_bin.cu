@@ -471,8 +471,9 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const int32_t* __re
 }
 
 // Stable scatter of one tile of kSortTile keys. Warp w owns the contiguous sub-tile
-// [w * 512, (w + 1) * 512) and visits it in 16 rounds of 32 consecutive keys (kept in
-// registers). Pass 1 counts each warp's digits. A block-wide prefix then gives, per digit,
+// [w * 384, (w + 1) * 384) and visits it in 12 rounds of 32 consecutive keys (kept in
+// registers; 3,072-key tiles measured faster than 4,096 at the fitting size, with 4 blocks
+// per SM and shorter tail waves). Pass 1 counts each warp's digits. A block-wide prefix then gives, per digit,
 // the tile-local start of its run and each warp's start inside it. Pass 2 places every key in
 // shared memory at its warp's start + its rank among equal digits in lower lanes (warp match
 // masks), so the tile sits in shared memory sorted by digit, ties in tile order. The tile is
