@@ -48,10 +48,11 @@ FIT_ITERS = 2000
 L2_FLUSH_BYTES = 256 << 20
 SM_COUNT_NOMINAL = 152
 EX2_PER_CLK_SM = 16           # MUFU ex2 results per clock per SM
-FP32_LANES_PER_CLK_SM = 128   # FP32 instructions issued per clock per SM (4 x 32 lanes)
-# FP32 instructions an effective pair needs at the least: about 15 in the forward (offset,
-# quadratic form, truncation test, two accumulations) and about 35 in the adjoint (the same
-# plus the Eq. 5-6 factors and the first and second moments of the gradient); one ex2 each.
+FP32_LANES_PER_CLK_SM = 128   # FP32 lane operations per clock per SM (4 x 32 lanes)
+# FP32 operations an effective pair needs at the least (a packed FP32x2 instruction counts as
+# two): about 15 in the forward (offset, quadratic form, truncation test, two accumulations)
+# and about 35 in the adjoint (the same plus the Eq. 5-6 factors and the first and second
+# moments of the gradient); one ex2 each.
 MIN_FP32_PER_PAIR = {"k_render_fwd": 15, "k_render_bwd": 35}
 FALLBACK_SM_MHZ = 2070.0
 
@@ -449,7 +450,7 @@ def run_ours(args, world, rank, local):
                 "unit": "Gpair/s", "frac": achieved / peak_gpairs,
                 "traffic": traffic_for(kern),
                 "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_CLK_SM} FP32 lanes/clk / "
-                              f"{MIN_FP32_PER_PAIR[kern]} FP32 instructions per effective pair "
+                              f"{MIN_FP32_PER_PAIR[kern]} FP32 operations per effective pair "
                               f"x {f_mhz:.0f} MHz (SM max clock, {peak_src}); the SFU ceiling "
                               f"(one ex2 per pair, {EX2_PER_CLK_SM}/clk/SM) is "
                               f"{n_sm * EX2_PER_CLK_SM * f_mhz * 1e-3:.0f} Gpair/s"}
