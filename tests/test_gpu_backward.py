@@ -75,7 +75,7 @@ def test_grad_deterministic_bitwise():
 
 
 @pytest.mark.parametrize("mode,a_act,t_act,brick", [(1, 0, 0, (8, 8, 8)), (0, 1, 1, (8, 8, 4)),
-                                                    (1, 1, 1, (4, 4, 4))])
+                                                    (1, 1, 1, (4, 4, 4)), (0, 0, 1, (16, 8, 4))])
 def test_grad_modes_activations_bricks(mode, a_act, t_act, brick):
     import oracle
     og = oracle.Grid(33, 27, 19, (1.1, 0.9, 1.3), (0.5, -1.0, 2.0))
