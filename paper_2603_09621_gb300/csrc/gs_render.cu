@@ -10,27 +10,28 @@
 //
 // Forward: the brick is split into 4 x 4 x 4 footprints, one half-warp each; a lane owns one
 // x-row of four voxels. A half-warp tests 16 staged Gaussians against its footprint with one
-// ballot (triangle inequality in whitened space: |M (p - mu)| >= |M (c - mu)| - rho4, with
-// rho4 the whitened radius of the footprint around its centre c, so a footprint whose centre
-// is farther than sqrt(T) + rho4 is missed; so is one whose centre lies outside the truncated
-// ellipsoid's bounding box widened by 3/2 along an axis; a margin absorbs FP32 rounding) and evaluates the
-// hits in ascending Gaussian id, accumulating S and W in registers (deterministic; one packed
-// FFMA2 updates a voxel's (S, W) with (v r, r) g).
+// ballot and two conservative tests: the triangle inequality in whitened space
+// (|M (p - mu)| >= |M (c - mu)| - rho4, with rho4 the whitened radius of the footprint around
+// its centre c, so a footprint whose centre is farther than sqrt(T) + rho4 is missed) and the
+// truncated ellipsoid's bounding box widened by 3/2 along each axis; a margin absorbs FP32
+// rounding. It evaluates the hits in ascending Gaussian id, accumulating S and W in registers
+// (deterministic; one packed FFMA2 updates a voxel's (S, W) with (v r, r) g).
 // Adjoint: one thread per (brick, Gaussian) pair evaluates the brick rows the Gaussian
-// reaches (the row shadow, per z-row a quadratic in dy), each row as bx predicated voxel
-// slots, so lanes never diverge inside a row. A block takes 256 consecutive brick-major pairs
-// (one to three bricks), computes their row masks and counting-sorts them by number of rows in
-// shared memory; its four warps then take 32-pair chunks of the sorted list, longest first,
-// from a shared counter, so lanes of a warp run pairs of equal length and a warp that drew
-// short pairs moves on to the next chunk (72 registers without spills, 7 blocks per SM). The per-voxel factors
-// (alpha, alpha I'), alpha = dL/dI / max(W, eps), are precomputed into one float2 volume; a
-// block copies those of its first four bricks into shared memory (zero outside the grid), so
-// rows read them without range tests; one 16-byte pad after every 128 bytes spreads the rows
-// that the lanes of a warp read at once over the shared-memory banks. A row's slots are
-// evaluated in packed FP32x2 pairs (FFMA2). Each pair's partial is summed by one thread in a fixed
-// voxel order (the processing order does not change results) and goes to a per-pair slot
-// (deterministic mode, reduced later in Gaussian-major order) or to one float atomic per
-// value (fast mode).
+// reaches (the row shadow, per z-row a quadratic in dy; z-planes whose section of the
+// ellipsoid misses the brick's x range are skipped), each row as bx predicated voxel slots in
+// packed FP32x2 pairs, so lanes never diverge inside a row. A block takes 256 consecutive
+// brick-major pairs (one to three bricks), computes their row masks and counting-sorts them
+// by number of rows in shared memory; its four warps then take 32-pair chunks of the sorted
+// list, longest first, from a shared counter, so the lanes of a warp run pairs of equal length
+// and a warp that drew short pairs moves on to the next chunk (72 registers without spills,
+// 7 blocks per SM). The per-voxel factors (alpha, alpha I'), alpha = dL/dI / max(W, eps), are
+// precomputed into one float2 volume; a block copies those of its first four bricks into
+// shared memory (zero outside the grid), so rows read them without range tests; a 16-byte pad
+// after every 128 bytes and a 32-byte offset between staged bricks spread the rows that the
+// lanes of a warp read at once over the shared-memory banks. Each pair's partial is summed by
+// one thread in a fixed voxel order (the processing order does not change results) and goes
+// to a per-pair slot (deterministic mode, reduced later in Gaussian-major order) or to one
+// float atomic per value (fast mode).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
