@@ -17,9 +17,9 @@ Volumes are ``[nz, ny, nx]`` arrays (x fastest); voxel (i, j, k) has centre
 ``origin + (i + 1/2, j + 1/2, k + 1/2) * h``.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py`` against closed
-forms, invariants, brute force or library routines, except ``ssim3d`` (a stated reading of
-the paper's evaluation metric whose window the paper does not give: parity unpinned beyond
-the identity and symmetry checks).
+forms, invariants, brute force or library routines. ``ssim3d`` is a stated reading of the
+paper's evaluation metric whose window the paper does not give (Gaussian, std 1.5 voxels);
+it is pinned to that reading by closed forms (constant volumes; an impulse against zero).
 """
 from __future__ import annotations
 

@@ -604,6 +604,34 @@ def test_psnr_ssim_basic():
     assert oracle.ssim3d(x, y) < 0.99
 
 
+def test_ssim_closed_forms():
+    """SSIM (Wang et al. 2004, cited in Sec. 4.2) in closed form for two configurations:
+    * constant volumes a and b: the variances vanish, so SSIM = (2ab + C1) / (a^2 + b^2 + C1);
+    * a unit impulse against zero: at offset q from the impulse the local mean is the window
+      weight w(q) and the variance w - w^2, so SSIM(q) = C1 / (w^2 + C1) * C2 / (w - w^2 + C2),
+      with w the separable Gaussian window (std 1.5 voxels, radius 5 voxels, each axis
+      normalised) written out here; the mean runs over the whole volume.
+    A wrong constant (K1, K2), a dropped factor 2 or another window fails one of them."""
+    import oracle
+    c1, c2 = 0.01 ** 2, 0.03 ** 2
+    for a, b in ((0.2, 0.7), (0.5, 0.5), (0.9, 0.1)):
+        x = np.full((12, 12, 12), a)
+        y = np.full((12, 12, 12), b)
+        assert oracle.ssim3d(x, y) == pytest.approx((2 * a * b + c1) / (a * a + b * b + c1),
+                                                    rel=1e-10)
+    n = 21
+    x = np.zeros((n, n, n))
+    x[n // 2, n // 2, n // 2] = 1.0
+    k = np.arange(-5, 6, dtype=np.float64)
+    g1 = np.exp(-k * k / (2 * 1.5 ** 2))
+    g1 /= g1.sum()
+    w = np.zeros((n, n, n))
+    c = n // 2
+    w[c - 5:c + 6, c - 5:c + 6, c - 5:c + 6] = g1[:, None, None] * g1[None, :, None] * g1[None, None, :]
+    expect = np.mean(c1 / (w * w + c1) * c2 / (w - w * w + c2))
+    assert oracle.ssim3d(x, np.zeros_like(x)) == pytest.approx(expect, rel=1e-9)
+
+
 # ----------------------------------------------------------- composed pieces: closed forms
 
 def test_rician_closed_forms():
