@@ -212,9 +212,12 @@ gs_status gs_l1_loss(const float* pred, const float* target, int64_t n, float* d
  * NULL (sign(pred - target) / n). n must be in [1, GS_L1_STATIC_MAX_N]; larger n returns
  * GS_ERR_INVALID_ARG before any launch. The first call on a device looks up the array's
  * device address (with that device current); make that first call before any stream
- * capture. All calls share the one array and it keeps the last call's partial sums; every
- * call overwrites the entries it reads, so nothing needs clearing, but calls that overlap on
- * the GPU (concurrent streams, or other processes' threads on the same device) race on it:
+ * capture. The address found then belongs to the context current at that first call; after
+ * that context is destroyed (cudaDeviceReset, or a context rebuilt after an error) the
+ * process must not call this entry point again. All calls in one process share the one array
+ * (each process has its own copy) and it keeps the last call's partial sums; every call
+ * overwrites the entries it reads, so nothing needs clearing, but calls of one process that
+ * overlap on the GPU (from concurrent streams or threads on the same device) race on it:
  * issue them in order on one stream. */
 gs_status gs_l1_loss_static(const float* pred, const float* target, int64_t n, float* d_loss,
                             float* dpred, gs_stream stream);

@@ -76,7 +76,9 @@ __global__ void __launch_bounds__(1024) k_l1_static_final(const float* __restric
     if (threadIdx.x == 0) *loss = sm[0] * inv_n;
 }
 
-// Device address of the static scratch on the current device (looked up once per device).
+// Device address of the static scratch on the current device, looked up once per device and
+// kept for the life of the process: it is valid for the context that was current at the first
+// call (a context destroyed and rebuilt later reloads the module at another address).
 gs_status scratch_for_current_device(float** out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GS_ERR_CUDA;

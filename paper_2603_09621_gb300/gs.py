@@ -410,8 +410,27 @@ def gs_l1_loss(pred, target, ws: Workspace, d_loss=None, dpred=None, stream=None
 GS_L1_STATIC_MAX_N = 33554432
 
 
+def _check_f32_cuda(name, t, n):
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} has {t.numel()} values, expected {n}")
+
+
 def gs_l1_loss_static(pred, target, d_loss=None, dpred=None, stream=None):
-    """L1 loss without a workspace (for callers that cannot allocate device memory)."""
+    """L1 loss without a workspace (for callers that cannot allocate device memory).
+
+    pred, target (and dpred, if given) are contiguous float32 CUDA tensors of equal size,
+    at most GS_L1_STATIC_MAX_N values; d_loss, if given, is a float32 CUDA scalar."""
+    n = pred.numel()
+    _check_f32_cuda("pred", pred, None)
+    _check_f32_cuda("target", target, n)
+    if dpred is not None:
+        _check_f32_cuda("dpred", dpred, n)
+    if n < 1 or n > GS_L1_STATIC_MAX_N:
+        raise ValueError(f"gs_l1_loss_static takes 1 to {GS_L1_STATIC_MAX_N} values, got {n}")
+    if d_loss is not None:
+        _check_f32_cuda("d_loss", d_loss, 1)
     d_loss = torch.empty((), dtype=torch.float32, device=pred.device) if d_loss is None else d_loss
     _check(load().gs_l1_loss_static(_ptr(pred), _ptr(target), pred.numel(), _ptr(d_loss),
                                     _ptr(dpred), _stream(stream)), "gs_l1_loss_static")
