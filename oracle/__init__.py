@@ -60,10 +60,10 @@ def lib():
         i64, f64, f32, i32 = ctypes.c_int64, ctypes.c_double, ctypes.c_float, ctypes.c_int
         _lib.og_render.restype = i64
         _lib.og_render.argtypes = [P, i64, P, P, P, P, f64, f64, i32, i32, i32, f64, i32,
-                                   P, P, P, P, P]
+                                   P, P, P, P, P, P, P, P, P, P, P, P]
         _lib.og_render_grad.restype = i64
-        _lib.og_render_grad.argtypes = [P, i64, P, P, P, P, f64, f64, i32, i32, i32, i32,
-                                        P, P, P]
+        _lib.og_render_grad.argtypes = [P, i64, P, P, P, P, f64, f64, i32, i32, i32, f64, i32,
+                                        P, P, P, P, P, P]
         _lib.og_bins_fp32.restype = None
         _lib.og_bins_fp32.argtypes = [P, i64, P, P, P, P, f32, P]
         _lib.og_signal_proxy.restype = None
@@ -140,58 +140,109 @@ def signal_proxy(T1, T2, TR: float, TE: float) -> np.ndarray:
 
 # --------------------------------------------------------------------- Eq. 3-4
 
-def render(params, grid: Grid, cfg: Config = Config(), crop=None, amb_tol=None, prune=True):
+# Ambiguous pairs recorded per voxel by render(..., want_amb=True) (og_render's slots).
+AMB_SLOTS = 8
+
+# Default half-width of the ambiguity band around the truncation boundary, relative to
+# sum_ab |C_ab d_a d_b| (the rounding scale of the quadratic form): a pair with
+# |d^2 - sigma_t^2| <= AMB_TOL sum_ab |C_ab d_a d_b| may be decided either way by a rounded
+# FP32 evaluation. The value is derived from the FP32 operation sequence of a renderer that
+# builds its per-Gaussian coefficients and evaluates the form in single precision (about
+# 335 units of 2^-24).
+AMB_TOL = 2e-5
+
+
+def render(params, grid: Grid, cfg: Config = Config(), crop=None, amb_tol=None, prune=True,
+           want_amb=False):
     """Eq. 3-4 with the Sec. 3.3 truncation, brute force in FP64.
 
     Returns dict(I, W, S, amb, npair, n_invalid), each volume crop-shaped ``[z, y, x]``.
     ``amb`` counts, per voxel, the pairs with |d^2 - sigma_t^2| <= amb_tol sum_ab
-    |C_ab d_a d_b| (default amb_tol 2e-5, about 170 FP32 units in the last place of the
-    form's absolute terms): a rounded FP32 evaluation of d^2 may put them on either side of
-    the truncation boundary, so parity tests compare only voxels with ``amb == 0``.
+    |C_ab d_a d_b| (default ``AMB_TOL``): a rounded FP32 evaluation of d^2 may put them on
+    either side of the truncation boundary, so either decision is a valid result.
     ``npair`` counts the contributing pairs per voxel.
+
+    With ``want_amb`` the dict also holds, for validating a result that took its own
+    decisions on the ambiguous pairs: ``S_sure``, ``W_sure`` (sums over the contributing pairs
+    that are not ambiguous); per voxel and slot k < ``AMB_SLOTS`` (the first ambiguous pairs in
+    Gaussian order) ``amb_id`` (the Gaussian, -1 for an unused slot), ``amb_vw`` (v w),
+    ``amb_w`` (w = exp(-d^2/2) r whichever side of the boundary), ``amb_rel``
+    ((d^2 - sigma_t^2) / sum_ab |C_ab d_a d_b|; <= 0 means the FP64 decision includes it);
+    and ``cond_w`` (sum over contributing pairs of w sum_ab |C_ab d_a d_b|).
     """
     p = np.ascontiguousarray(params, dtype=np.float64).reshape(-1, 12)
     dims, h, o = _grid_arrays(grid)
     carr, shape = _crop_array(grid, crop)
     if amb_tol is None:
-        amb_tol = 2e-5
+        amb_tol = AMB_TOL
     I = np.zeros(shape, np.float64)
     W = np.zeros(shape, np.float64)
     S = np.zeros(shape, np.float64)
     amb = np.zeros(shape, np.int32)
     npair = np.zeros(shape, np.int32)
+    extra = {}
+    if want_amb:
+        extra = dict(S_sure=np.zeros(shape, np.float64), W_sure=np.zeros(shape, np.float64),
+                     amb_id=np.full(shape + (AMB_SLOTS,), -1, np.int32),
+                     amb_vw=np.zeros(shape + (AMB_SLOTS,), np.float64),
+                     amb_w=np.zeros(shape + (AMB_SLOTS,), np.float64),
+                     amb_rel=np.zeros(shape + (AMB_SLOTS,), np.float64),
+                     cond_w=np.zeros(shape, np.float64))
+    ep = (lambda k: _ptr(extra[k]) if want_amb else None)
     n_bad = lib().og_render(_ptr(p), p.shape[0], _ptr(dims), _ptr(h), _ptr(o),
                             None if carr is None else _ptr(carr), cfg.trunc_sigma, cfg.eps,
                             cfg.signal_mode, cfg.a_act, cfg.t_act, float(amb_tol),
                             1 if prune else 0, _ptr(I), _ptr(W), _ptr(S), _ptr(amb),
-                            _ptr(npair))
+                            _ptr(npair), ep("S_sure"), ep("W_sure"), ep("amb_id"),
+                            ep("amb_vw"), ep("amb_w"), ep("amb_rel"), ep("cond_w"))
     if n_bad < 0:
         raise MemoryError("oracle render: allocation failed")
-    return dict(I=I, W=W, S=S, amb=amb, npair=npair, n_invalid=int(n_bad))
+    out = dict(I=I, W=W, S=S, amb=amb, npair=npair, n_invalid=int(n_bad))
+    out.update(extra)
+    return out
 
 
 def render_grad(params, grid: Grid, dI, cfg: Config = Config(), crop=None, prune=True,
-                want_geo=False):
+                want_geo=False, want_box=False, amb_tol=None):
     """Eq. 5-6 (Sec. 3.3) and the chain to the raw parameters, FP64.
 
     ``dI`` is dL/dI on the crop (crop-shaped); voxels outside the crop have dL/dI = 0.
     Returns dL/d(raw params) ``[N, 12]`` and, with ``want_geo``, dL/d(mu, c_xx, c_yy, c_zz,
     c_xy, c_xz, c_yz, v, r) ``[N, 11]``.
+
+    With ``want_box`` it returns a dict(grad, lo, hi, n_unenum) instead: ``lo`` and ``hi``
+    bound, per Gaussian and parameter, the gradient of every renderer that decides each pair
+    of the ambiguity band (``amb_tol``, default ``AMB_TOL``; see ``render``) either way,
+    voxel by voxel (all include/exclude subsets of a voxel's ambiguous pairs, up to
+    ``AMB_SLOTS`` of them). ``n_unenum`` counts voxels with dI != 0 and more ambiguous pairs
+    than that (not covered by the bounds). ``grad`` is the FP64 decision's gradient.
     """
     p = np.ascontiguousarray(params, dtype=np.float64).reshape(-1, 12)
     dims, h, o = _grid_arrays(grid)
     carr, shape = _crop_array(grid, crop)
     dI = np.ascontiguousarray(dI, dtype=np.float64)
     assert dI.shape == shape, (dI.shape, shape)
+    if amb_tol is None:
+        amb_tol = AMB_TOL
     out = np.zeros((p.shape[0], 12), np.float64)
     geo = np.zeros((p.shape[0], 11), np.float64) if want_geo else None
+    lo = np.zeros((p.shape[0], 12), np.float64) if want_box else None
+    hi = np.zeros((p.shape[0], 12), np.float64) if want_box else None
+    nun = np.zeros(1, np.int64)
     n_bad = lib().og_render_grad(_ptr(p), p.shape[0], _ptr(dims), _ptr(h), _ptr(o),
                                  None if carr is None else _ptr(carr), cfg.trunc_sigma,
                                  cfg.eps, cfg.signal_mode, cfg.a_act, cfg.t_act,
-                                 1 if prune else 0, _ptr(dI), _ptr(out),
-                                 None if geo is None else _ptr(geo))
+                                 float(amb_tol) if want_box else 0.0, 1 if prune else 0,
+                                 _ptr(dI), _ptr(out), None if geo is None else _ptr(geo),
+                                 None if lo is None else _ptr(lo),
+                                 None if hi is None else _ptr(hi), _ptr(nun))
     if n_bad < 0:
         raise MemoryError("oracle render_grad: allocation failed")
+    if want_box:
+        res = dict(grad=out, lo=lo, hi=hi, n_unenum=int(nun[0]))
+        if want_geo:
+            res["geo"] = geo
+        return res
     return (out, geo) if want_geo else out
 
 
@@ -556,3 +607,106 @@ def fit_step(params, lr_target, grid: Grid, s: int, cfg: Config, m, v, step: int
     p2, m2, v2 = adam_step(p, grad, m, v, step, acfg)
     return dict(loss=loss, grad=grad, params=p2, m=m2, v=v2, I=r["I"], lr_pred=lr_pred,
                 amb=r["amb"])
+
+
+# ------------------------------------------------ validating a renderer's tie decisions
+
+def _subset_masks(n: int) -> np.ndarray:
+    """[2^n, n] 0/1 matrix: row s lists which of n items subset s includes (bit k of s)."""
+    s = np.arange(1 << n)[:, None]
+    return ((s >> np.arange(n)[None, :]) & 1).astype(np.float64)
+
+
+def forward_subset_check(I, W, ref, tol: float = 1e-5, tol_w=1e-5, w_min: float = 1e-6,
+                         eps: float = 1e-12, max_unenum_frac: float = 1e-3):
+    """Check a rendered (I, W) against ``render(..., want_amb=True)`` output ``ref``, voxel by
+    voxel, accepting any include/exclude decision on the ambiguous pairs (Sec. 3.3 truncation
+    read as d^2 <= sigma_t^2; a pair within the band may be decided either way by rounding).
+
+    A voxel passes if some subset s of its ambiguous pairs gives W_s = W_sure + sum_{k in s} w_k
+    with |W - W_s| <= tol_w max(W_s, w_min) and, where W_s > w_min, I_s = S_s / max(W_s, eps)
+    with |I - I_s| <= tol |I_s|. Voxels with no ambiguous pair must match the FP64 decision
+    (a voxel no Gaussian reaches renders exactly zero). ``tol_w`` may be an array (per voxel).
+    Voxels with more than AMB_SLOTS ambiguous pairs cannot be enumerated; their share of the
+    voxels with W > w_min must stay below ``max_unenum_frac``.
+
+    Returns a dict of statistics, including ``flips`` (ambiguous pairs whose matched decision
+    differs from the FP64 one) and ``max_flip_rel`` (the largest |d^2 - sigma_t^2| /
+    sum_ab |C_ab d_a d_b| among them). Raises AssertionError on failure."""
+    I = np.asarray(I, np.float64)
+    W = np.asarray(W, np.float64)
+    amb = ref["amb"]
+    tw = np.broadcast_to(np.asarray(tol_w, np.float64), amb.shape)
+    live = ref["W"] > w_min
+    stats = dict(n_live=int(live.sum()), n_plain=0, n_tie=0, n_unenum=0, flips=0,
+                 tie_pairs=0, max_flip_rel=0.0, max_relI=0.0, max_relW=0.0)
+    # voxels without ambiguous pairs: the FP64 decision is the only valid one
+    m = live & (amb == 0)
+    Io, Wo = ref["I"][m], ref["W"][m]
+    relI = np.abs(I[m] - Io) / np.maximum(np.abs(Io), 1e-30)
+    relW = np.abs(W[m] - Wo) / Wo
+    stats["n_plain"] = int(m.sum())
+    if m.any():
+        stats["max_relI"] = float(relI.max())
+        stats["max_relW"] = float(relW.max())
+        stats["max_relW_over_tol"] = float((relW / tw[m]).max())
+        bad = (relI > tol) | (relW > tw[m])
+        assert not bad.any(), ("plain voxels", int(bad.sum()), float(relI.max()),
+                               float(relW.max()))
+    none = (ref["W"] == 0) & (amb == 0)
+    assert np.all(W[none] == 0) and np.all(I[none] == 0), "voxels nobody reaches"
+    # voxels with 1..AMB_SLOTS ambiguous pairs: some subset must match
+    for n in range(1, AMB_SLOTS + 1):
+        sel = amb == n
+        if not sel.any():
+            continue
+        masks = _subset_masks(n)
+        vw = ref["amb_vw"][sel][:, :n]
+        w = ref["amb_w"][sel][:, :n]
+        Ws = ref["W_sure"][sel][:, None] + w @ masks.T
+        Ss = ref["S_sure"][sel][:, None] + vw @ masks.T
+        Is = Ss / np.maximum(Ws, eps)
+        Wg, Ig, twv = W[sel][:, None], I[sel][:, None], tw[sel][:, None]
+        errW = np.abs(Wg - Ws) / np.maximum(Ws, w_min)
+        errI = np.abs(Ig - Is) / np.maximum(np.abs(Is), 1e-30)
+        okI = (Ws <= w_min) | (errI <= tol)
+        ok = (errW <= twv) & okI
+        good = ok.any(axis=1)
+        assert good.all(), ("tie voxels", int((~good).sum()), n)
+        # the matching subset with the smallest error, against the FP64 decisions
+        score = np.where(ok, errW + np.where(Ws > w_min, errI, 0.0), np.inf)
+        best = masks[np.argmin(score, axis=1)]
+        fp64 = (ref["amb_rel"][sel][:, :n] <= 0).astype(np.float64)
+        flip = best != fp64
+        rel = np.abs(ref["amb_rel"][sel][:, :n])
+        stats["n_tie"] += int(sel.sum())
+        stats["tie_pairs"] += int(n * sel.sum())
+        stats["flips"] += int(flip.sum())
+        if flip.any():
+            stats["max_flip_rel"] = max(stats["max_flip_rel"], float(rel[flip].max()))
+    un = live & (amb > AMB_SLOTS)
+    stats["n_unenum"] = int(un.sum())
+    assert stats["n_unenum"] <= max_unenum_frac * max(stats["n_live"], 1), stats
+    return stats
+
+
+def gradient_box_check(got, box, tol: float = 1e-4, group_tol: float = 1e-3):
+    """Check a gradient ``got`` [N, 12] against ``render_grad(..., want_box=True)`` output:
+    the distance from ``got`` to the box [lo, hi] (the gradients of every decision on the
+    ambiguous pairs) must be at most ``tol`` of the FP64 gradient's norm (relative L2), and per
+    parameter group (means, log-scales, quaternion, a, t) at most ``group_tol`` of the group's
+    norm (floored at 1e-3 of the total: rotation gradients of isotropic Gaussians vanish).
+    Returns (distance, relative box width)."""
+    got = np.asarray(got, np.float64)
+    ref, lo, hi = box["grad"], box["lo"], box["hi"]
+    assert box["n_unenum"] == 0, box["n_unenum"]
+    proj = np.clip(got, lo, hi)
+    tot = float(np.linalg.norm(ref))
+    den = tot if tot > 0 else 1.0
+    dist = float(np.linalg.norm(got - proj)) / den
+    assert dist <= tol, dist
+    for a, b in ((0, 3), (3, 6), (6, 10), (10, 11), (11, 12)):
+        diff = np.linalg.norm(got[:, a:b] - proj[:, a:b])
+        gden = max(np.linalg.norm(ref[:, a:b]), 1e-3 * tot)
+        assert diff <= group_tol * gden, (a, b, diff / gden)
+    return dist, float(np.linalg.norm(hi - lo)) / den

@@ -128,16 +128,24 @@ static void og_activate(const double* p, const int32_t dims[3], const double h[3
         g->v = g->A * g->T;
         g->r = 1.0;
     }
-    /* Exact bounding box: d^2 >= |p-mu|^2 / s_max^2. The radius is padded by 1 % in d^2 so
-     * that pairs in the ambiguity band just outside the ellipsoid are visited as well, then
-     * one voxel is added. */
-    double smax = g->s[0];
-    if (g->s[1] > smax) smax = g->s[1];
-    if (g->s[2] > smax) smax = g->s[2];
-    double rad = sqrt(sigma_t * sigma_t * (1.0 + (amb_tol > 0.0 ? 0.01 : 0.0))) * smax *
+    /* Exact bounding box: d^2 >= |p-mu|^2 / s_max^2. Pairs of the ambiguity band have
+     * d^2 <= sigma_t^2 + amb_tol sum_ab |C_ab d_a d_b| and sum_ab |C_ab d_a d_b| <=
+     * 3 |p-mu|^2 / s_min^2 (|C_ab| <= 1 / s_min^2), so they lie within
+     * |p-mu|^2 <= sigma_t^2 s_max^2 / (1 - 3 amb_tol s_max^2 / s_min^2); the radius is padded
+     * by a further 1 % in d^2 and one voxel is added. A Gaussian so anisotropic that the
+     * denominator is not clearly positive is not pruned. */
+    double smax = g->s[0], smin = g->s[0];
+    for (int k = 1; k < 3; ++k) {
+        if (g->s[k] > smax) smax = g->s[k];
+        if (g->s[k] < smin) smin = g->s[k];
+    }
+    double shrink = 1.0;
+    if (amb_tol > 0.0) shrink = 1.0 - 3.0 * amb_tol * (smax * smax) / (smin * smin);
+    int no_prune = !prune || shrink < 0.05;
+    double rad = sqrt(sigma_t * sigma_t * (amb_tol > 0.0 ? 1.01 : 1.0) / shrink) * smax *
                      (1.0 + 1e-6) + 1e-9;
     for (int k = 0; k < 3; ++k) {
-        if (!prune) {
+        if (no_prune) {
             g->lo[k] = 0;
             g->hi[k] = dims[k] - 1;
             continue;
@@ -186,20 +194,32 @@ static double og_d2_abs(const og_gauss* g, const double d[3]) {
 
 /* ------------------------------------------------------------- Eq. 3-4 */
 
+/* Ambiguous pairs recorded per voxel (the rest are only counted). */
+#define OG_AMB_SLOTS 8
+
 /*
  * Forward render of the voxels in crop = [x0,x1) x [y0,y1) x [z0,z1) (NULL: whole grid).
  * Outputs are crop-shaped, z-major, x fastest:
  *   S = sum_i v_i w_i, W = sum_i w_i, I = S / max(W, eps),
  *   amb = number of pairs with |d^2 - sigma_t^2| <= amb_tol * sum_ab |C_ab d_a d_b| (a
- *         rounded evaluation of d^2 may fall on either side of the truncation boundary;
- *         tests compare only voxels with amb == 0),
+ *         rounded evaluation of d^2 may fall on either side of the truncation boundary),
  *   npair (optional) = number of contributing pairs (d^2 <= sigma_t^2) per voxel.
+ * Optional outputs for validating a result that took its own decisions on ambiguous pairs:
+ *   S_sure, W_sure = the sums over contributing pairs that are not ambiguous;
+ *   for the first OG_AMB_SLOTS ambiguous pairs of a voxel (ascending Gaussian order), slot k
+ *   of voxel j (index j * OG_AMB_SLOTS + k): amb_id = the Gaussian, amb_vw = v_i w_i and
+ *   amb_w = w_i with w_i = exp(-d^2/2) r_i whichever side of the boundary d^2 lies,
+ *   amb_rel = (d^2 - sigma_t^2) / sum_ab |C_ab d_a d_b| (<= 0: the pair contributes to S, W);
+ *   cond_w = sum_i w_i sum_ab |C_ab d_a d_b| over contributing pairs (the rounding scale of
+ *   the voxel's quadratic forms, weighted as W).
  * Returns the number of invalid Gaussians.
  */
 int64_t og_render(const double* params, int64_t N, const int32_t dims[3], const double h[3],
                   const double origin[3], const int32_t* crop, double sigma_t, double eps,
                   int signal_mode, int a_act, int t_act, double amb_tol, int prune, double* I,
-                  double* W, double* S, int32_t* amb, int32_t* npair) {
+                  double* W, double* S, int32_t* amb, int32_t* npair, double* S_sure,
+                  double* W_sure, int32_t* amb_id, double* amb_vw, double* amb_w,
+                  double* amb_rel, double* cond_w) {
     int32_t c[6] = {0, dims[0], 0, dims[1], 0, dims[2]};
     if (crop) memcpy(c, crop, sizeof(c));
     const int64_t cx = c[1] - c[0], cy = c[3] - c[2], cz = c[5] - c[4];
@@ -209,21 +229,26 @@ int64_t og_render(const double* params, int64_t N, const int32_t dims[3], const 
     int64_t n_invalid = 0;
     for (int64_t i = 0; i < N; ++i) n_invalid += G[i].valid ? 0 : 1;
     const double s2 = sigma_t * sigma_t;
+    const int want_abs = amb_tol > 0.0 || cond_w != NULL;
 
     /* One z-slice per task: each voxel is owned by one thread and sums Gaussians in
      * ascending order, so the result does not depend on the thread count. */
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t zz = 0; zz < cz; ++zz) {
         const int z = (int)(zz + c[4]);
-        double* Sz = S + zz * cy * cx;
-        double* Wz = W + zz * cy * cx;
-        int32_t* Az = amb + zz * cy * cx;
-        int32_t* Nz = npair ? npair + zz * cy * cx : NULL;
+        const int64_t zoff = zz * cy * cx;
+        double* Sz = S + zoff;
+        double* Wz = W + zoff;
+        int32_t* Az = amb + zoff;
+        int32_t* Nz = npair ? npair + zoff : NULL;
         for (int64_t k = 0; k < cy * cx; ++k) {
             Sz[k] = 0.0;
             Wz[k] = 0.0;
             Az[k] = 0;
             if (Nz) Nz[k] = 0;
+            if (S_sure) S_sure[zoff + k] = 0.0;
+            if (W_sure) W_sure[zoff + k] = 0.0;
+            if (cond_w) cond_w[zoff + k] = 0.0;
         }
         const double pz = origin[2] + (z + 0.5) * h[2];
         for (int64_t i = 0; i < N; ++i) {
@@ -239,24 +264,98 @@ int64_t og_render(const double* params, int64_t N, const int32_t dims[3], const 
                     const double px = origin[0] + (x + 0.5) * h[0];
                     double d[3] = {px - g->mu[0], py - g->mu[1], pz - g->mu[2]};
                     double d2 = og_d2(g, d);
+                    double dabs = want_abs ? og_d2_abs(g, d) : 0.0;
                     int64_t idx = (int64_t)(y - c[2]) * cx + (x - c[0]);
-                    if (amb_tol > 0.0 && fabs(d2 - s2) <= amb_tol * og_d2_abs(g, d)) Az[idx] += 1;
+                    int is_amb = amb_tol > 0.0 && fabs(d2 - s2) <= amb_tol * dabs;
+                    if (is_amb) {
+                        int k = Az[idx];
+                        if (amb_id && k < OG_AMB_SLOTS) {
+                            int64_t sl = (zoff + idx) * OG_AMB_SLOTS + k;
+                            double wk = exp(-0.5 * d2) * g->r;
+                            amb_id[sl] = (int32_t)i;
+                            amb_vw[sl] = g->v * wk;
+                            amb_w[sl] = wk;
+                            amb_rel[sl] = (d2 - s2) / dabs;
+                        }
+                        Az[idx] += 1;
+                    }
                     if (d2 <= s2) {
                         double w = exp(-0.5 * d2) * g->r;
                         Sz[idx] += g->v * w;
                         Wz[idx] += w;
                         if (Nz) Nz[idx] += 1;
+                        if (!is_amb && S_sure) S_sure[zoff + idx] += g->v * w;
+                        if (!is_amb && W_sure) W_sure[zoff + idx] += w;
+                        if (cond_w) cond_w[zoff + idx] += w * dabs;
                     }
                 }
             }
         }
-        for (int64_t k = 0; k < cy * cx; ++k) I[zz * cy * cx + k] = Sz[k] / (Wz[k] > eps ? Wz[k] : eps);
+        for (int64_t k = 0; k < cy * cx; ++k) I[zoff + k] = Sz[k] / (Wz[k] > eps ? Wz[k] : eps);
     }
     free(G);
     return n_invalid;
 }
 
 /* ------------------------------------------------------------- Eq. 5-6 */
+
+/*
+ * Chain from the render-space gradient of one Gaussian -- dL/dmu, dL/dC (the full symmetric
+ * 3 x 3 matrix of entry derivatives), dL/dv, dL/dr -- to its 12 raw parameters:
+ * C = R D R^T with D = diag(s^-2), s = exp(log_s), R from the normalised quaternion;
+ * (v, r) from (A, T) by the signal mode; A, T from (a, t) by their activations.
+ * The map is linear in the render-space gradient.
+ */
+static void og_chain(const og_gauss* g, int signal_mode, int a_act, int t_act,
+                     const double dmu[3], double dC[3][3], double dv, double dr, double* dp) {
+    /* dL/dD_mm = (R^T G R)_mm, dL/dR = 2 G R D (G = dL/dC). */
+    double RtGR[3];
+    for (int m = 0; m < 3; ++m) {
+        double acc = 0.0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) acc += g->R[a][m] * dC[a][b] * g->R[b][m];
+        RtGR[m] = acc;
+    }
+    for (int m = 0; m < 3; ++m) {
+        /* D_mm = exp(-2 log_s_m)  =>  dD_mm/dlog_s_m = -2 D_mm */
+        double Dmm = 1.0 / (g->s[m] * g->s[m]);
+        dp[3 + m] = RtGR[m] * (-2.0 * Dmm);
+    }
+    double dR[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int m = 0; m < 3; ++m) {
+            double acc = 0.0;
+            for (int b = 0; b < 3; ++b) acc += dC[a][b] * g->R[b][m];
+            dR[a][m] = 2.0 * acc / (g->s[m] * g->s[m]);
+        }
+    /* dR/dq for R(w, x, y, z) as in og_quat_to_R. */
+    double w = g->qn[0], x = g->qn[1], y = g->qn[2], z = g->qn[3];
+    double dqn[4];
+    dqn[0] = 2.0 * (-z * dR[0][1] + y * dR[0][2] + z * dR[1][0] - x * dR[1][2] - y * dR[2][0] +
+                    x * dR[2][1]);
+    dqn[1] = 2.0 * (y * dR[0][1] + z * dR[0][2] + y * dR[1][0] - 2.0 * x * dR[1][1] -
+                    w * dR[1][2] + z * dR[2][0] + w * dR[2][1] - 2.0 * x * dR[2][2]);
+    dqn[2] = 2.0 * (-2.0 * y * dR[0][0] + x * dR[0][1] + w * dR[0][2] + x * dR[1][0] +
+                    z * dR[1][2] - w * dR[2][0] + z * dR[2][1] - 2.0 * y * dR[2][2]);
+    dqn[3] = 2.0 * (-2.0 * z * dR[0][0] - w * dR[0][1] + x * dR[0][2] + w * dR[1][0] -
+                    2.0 * z * dR[1][1] + y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
+    /* q_n = q / |q|  =>  dq = (dq_n - q_n (q_n . dq_n)) / |q| */
+    double dot = 0.0;
+    for (int k = 0; k < 4; ++k) dot += g->qn[k] * dqn[k];
+    for (int k = 0; k < 4; ++k) dp[6 + k] = (dqn[k] - g->qn[k] * dot) / g->qnorm;
+    for (int a = 0; a < 3; ++a) dp[a] = dmu[a];
+    /* (v, r) -> (A, T) -> raw (a, t) */
+    double dA, dT;
+    if (signal_mode == 0) {
+        dA = dv;
+        dT = dr;
+    } else {
+        dA = dv * g->T;
+        dT = dv * g->A;
+    }
+    dp[10] = a_act ? dA * g->A * (1.0 - g->A) : dA;
+    dp[11] = t_act ? dT * g->T * (1.0 - g->T) : dT;
+}
 
 /*
  * Gradient of L with respect to the raw parameters, given dI = dL/dI on the crop
@@ -266,25 +365,56 @@ int64_t og_render(const double* params, int64_t N, const int32_t dims[3], const 
  *   dgeo [N,11] (optional): dL/d(mu(3), c_xx, c_yy, c_zz, c_xy, c_xz, c_yz, v, r), where c_ab
  *     is the single variable that sets both symmetric entries C_ab = C_ba of the inverse
  *     covariance (so an off-diagonal derivative is the sum of the two entry derivatives).
+ *   dlo, dhi [N,12] (optional, need amb_tol > 0): bounds of every gradient a renderer can
+ *     produce that decides each ambiguous pair (band of og_render) either way. At a voxel with
+ *     n <= OG_AMB_SLOTS ambiguous pairs every include/exclude subset of them gives its own
+ *     S, W, I and so its own contribution to each Gaussian at that voxel (zero for an
+ *     ambiguous Gaussian left out); dlo and dhi add, per voxel, the smallest and the largest
+ *     of those contributions (componentwise) to dparams in place of the FP64 decision's.
+ *     Voxels are independent, so the sum of per-voxel ranges contains every combination.
+ *   n_unenum (optional): voxels with dI != 0 and more than OG_AMB_SLOTS ambiguous pairs
+ *     (their ranges are not formed; dparams uses the FP64 decisions there).
  */
 int64_t og_render_grad(const double* params, int64_t N, const int32_t dims[3], const double h[3],
                        const double origin[3], const int32_t* crop, double sigma_t, double eps,
-                       int signal_mode, int a_act, int t_act, int prune, const double* dI,
-                       double* dparams, double* dgeo) {
+                       int signal_mode, int a_act, int t_act, double amb_tol, int prune,
+                       const double* dI, double* dparams, double* dgeo, double* dlo,
+                       double* dhi, int64_t* n_unenum) {
     int32_t c[6] = {0, dims[0], 0, dims[1], 0, dims[2]};
     if (crop) memcpy(c, crop, sizeof(c));
     const int64_t cx = c[1] - c[0], cy = c[3] - c[2], cz = c[5] - c[4];
     const int64_t nv = cx * cy * cz;
-    double* I = (double*)malloc(sizeof(double) * (size_t)(nv > 0 ? nv : 1));
-    double* W = (double*)malloc(sizeof(double) * (size_t)(nv > 0 ? nv : 1));
-    double* S = (double*)malloc(sizeof(double) * (size_t)(nv > 0 ? nv : 1));
-    int32_t* amb = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nv > 0 ? nv : 1));
+    const size_t nv1 = (size_t)(nv > 0 ? nv : 1);
+    const int box = (dlo != NULL || dhi != NULL) && amb_tol > 0.0;
+    const double tol_r = box ? amb_tol : 0.0;
+    double* I = (double*)malloc(sizeof(double) * nv1);
+    double* W = (double*)malloc(sizeof(double) * nv1);
+    double* S = (double*)malloc(sizeof(double) * nv1);
+    int32_t* amb = (int32_t*)malloc(sizeof(int32_t) * nv1);
+    double *Ss = NULL, *Ws = NULL, *avw = NULL, *aw = NULL, *arel = NULL;
+    int32_t* aid = NULL;
+    if (box) {
+        Ss = (double*)malloc(sizeof(double) * nv1);
+        Ws = (double*)malloc(sizeof(double) * nv1);
+        aid = (int32_t*)malloc(sizeof(int32_t) * nv1 * OG_AMB_SLOTS);
+        avw = (double*)malloc(sizeof(double) * nv1 * OG_AMB_SLOTS);
+        aw = (double*)malloc(sizeof(double) * nv1 * OG_AMB_SLOTS);
+        arel = (double*)malloc(sizeof(double) * nv1 * OG_AMB_SLOTS);
+        if (!Ss || !Ws || !aid || !avw || !aw || !arel) return -1;
+    }
     if (!I || !W || !S || !amb) return -1;
     int64_t n_invalid = og_render(params, N, dims, h, origin, crop, sigma_t, eps, signal_mode,
-                                  a_act, t_act, 0.0, prune, I, W, S, amb, NULL);
-    og_gauss* G = og_activate_all(params, N, dims, h, origin, sigma_t, 0.0, signal_mode, a_act,
+                                  a_act, t_act, tol_r, prune, I, W, S, amb, NULL, Ss, Ws, aid,
+                                  avw, aw, arel, NULL);
+    og_gauss* G = og_activate_all(params, N, dims, h, origin, sigma_t, tol_r, signal_mode, a_act,
                                   t_act, prune);
     const double s2 = sigma_t * sigma_t;
+    if (n_unenum) {
+        int64_t cnt = 0;
+        if (box)
+            for (int64_t k = 0; k < nv; ++k) cnt += (amb[k] > OG_AMB_SLOTS && dI[k] != 0.0) ? 1 : 0;
+        *n_unenum = cnt;
+    }
 
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t i = 0; i < N; ++i) {
@@ -293,7 +423,13 @@ int64_t og_render_grad(const double* params, int64_t N, const int32_t dims[3], c
         for (int k = 0; k < OG_NPARAM; ++k) dp[k] = 0.0;
         if (dgeo)
             for (int k = 0; k < 11; ++k) dgeo[i * 11 + k] = 0.0;
-        if (!g->valid) continue;
+        double lo_d[OG_NPARAM], hi_d[OG_NPARAM];
+        for (int k = 0; k < OG_NPARAM; ++k) lo_d[k] = hi_d[k] = 0.0;
+        if (!g->valid) {
+            if (dlo) memset(dlo + i * OG_NPARAM, 0, sizeof(double) * OG_NPARAM);
+            if (dhi) memset(dhi + i * OG_NPARAM, 0, sizeof(double) * OG_NPARAM);
+            continue;
+        }
         double dmu[3] = {0, 0, 0};
         double dC[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
         double dv = 0.0, dr = 0.0;
@@ -311,25 +447,89 @@ int64_t og_render_grad(const double* params, int64_t N, const int32_t dims[3], c
                     const double px = origin[0] + (x + 0.5) * h[0];
                     double d[3] = {px - g->mu[0], py - g->mu[1], pz - g->mu[2]};
                     double d2 = og_d2(g, d);
-                    if (!(d2 <= s2)) continue;
+                    const int in = d2 <= s2;
+                    const int is_amb = box && fabs(d2 - s2) <= amb_tol * og_d2_abs(g, d);
+                    if (!in && !is_amb) continue;
                     int64_t idx = ((int64_t)(z - c[4]) * cy + (y - c[2])) * cx + (x - c[0]);
                     double gI = dI[idx];
                     if (gI == 0.0) continue;
                     double gk = exp(-0.5 * d2);   /* Gaussian kernel */
                     double w = gk * g->r;         /* Eq. 4 */
-                    double Wp = W[idx];
-                    /* dI/dw_i: (v_i - I)/W for W >= eps (Eq. 5), v_i/eps below the floor. */
-                    double dIdw = (Wp > eps) ? (g->v - I[idx]) / Wp : g->v / eps;
-                    double dIdv = w / (Wp > eps ? Wp : eps); /* Eq. 6 */
-                    double coef = gI * dIdw;
-                    dv += gI * dIdv;
-                    dr += coef * gk;
-                    /* dw/dmu = w C d ; dw/dC_ab = -1/2 w d_a d_b */
+                    double Cd[3];
                     for (int a = 0; a < 3; ++a) {
-                        double Cd = 0.0;
-                        for (int b = 0; b < 3; ++b) Cd += g->C[a][b] * d[b];
-                        dmu[a] += coef * w * Cd;
-                        for (int b = 0; b < 3; ++b) dC[a][b] += coef * w * (-0.5) * d[a] * d[b];
+                        Cd[a] = 0.0;
+                        for (int b = 0; b < 3; ++b) Cd[a] += g->C[a][b] * d[b];
+                    }
+                    double coef = 0.0;
+                    if (in) {
+                        double Wp = W[idx];
+                        /* dI/dw_i: (v_i - I)/W for W >= eps (Eq. 5), v_i/eps below the floor. */
+                        double dIdw = (Wp > eps) ? (g->v - I[idx]) / Wp : g->v / eps;
+                        double dIdv = w / (Wp > eps ? Wp : eps); /* Eq. 6 */
+                        coef = gI * dIdw;
+                        dv += gI * dIdv;
+                        dr += coef * gk;
+                        /* dw/dmu = w C d ; dw/dC_ab = -1/2 w d_a d_b */
+                        for (int a = 0; a < 3; ++a) {
+                            dmu[a] += coef * w * Cd[a];
+                            for (int b = 0; b < 3; ++b) dC[a][b] += coef * w * (-0.5) * d[a] * d[b];
+                        }
+                    }
+                    const int n = box ? amb[idx] : 0;
+                    if (n == 0 || n > OG_AMB_SLOTS) continue;
+                    /* Voxel with ambiguous pairs: this Gaussian's contribution under every
+                     * include/exclude subset of them. It is coef_s JU + dvc_s JV with the
+                     * chained unit vectors below. */
+                    double uC[3][3], umu[3], zmu[3] = {0, 0, 0};
+                    double zC[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+                    for (int a = 0; a < 3; ++a) {
+                        umu[a] = w * Cd[a];
+                        for (int b = 0; b < 3; ++b) uC[a][b] = -0.5 * w * d[a] * d[b];
+                    }
+                    double JU[OG_NPARAM], JV[OG_NPARAM];
+                    og_chain(g, signal_mode, a_act, t_act, umu, uC, 0.0, gk, JU);
+                    og_chain(g, signal_mode, a_act, t_act, zmu, zC, 1.0, 0.0, JV);
+                    const int64_t sl = idx * OG_AMB_SLOTS;
+                    int j = -1;
+                    if (is_amb)
+                        for (int k = 0; k < n; ++k)
+                            if (aid[sl + k] == (int32_t)i) j = k;
+                    double vstar[OG_NPARAM];
+                    {
+                        double Wp = W[idx];
+                        double dvc = in ? gI * w / (Wp > eps ? Wp : eps) : 0.0;
+                        for (int k = 0; k < OG_NPARAM; ++k) vstar[k] = coef * JU[k] + dvc * JV[k];
+                    }
+                    double mn[OG_NPARAM], mx[OG_NPARAM];
+                    for (int k = 0; k < OG_NPARAM; ++k) {
+                        mn[k] = INFINITY;
+                        mx[k] = -INFINITY;
+                    }
+                    for (int sig = 0; sig < (1 << n); ++sig) {
+                        double val[OG_NPARAM];
+                        if (j >= 0 && !((sig >> j) & 1)) {
+                            for (int k = 0; k < OG_NPARAM; ++k) val[k] = 0.0;
+                        } else {
+                            double Wsig = Ws[idx], Ssig = Ss[idx];
+                            for (int k = 0; k < n; ++k)
+                                if ((sig >> k) & 1) {
+                                    Wsig += aw[sl + k];
+                                    Ssig += avw[sl + k];
+                                }
+                            double Wf = Wsig > eps ? Wsig : eps;
+                            double Isig = Ssig / Wf;
+                            double dIdw = (Wsig > eps) ? (g->v - Isig) / Wsig : g->v / eps;
+                            double cs = gI * dIdw, dvc = gI * w / Wf;
+                            for (int k = 0; k < OG_NPARAM; ++k) val[k] = cs * JU[k] + dvc * JV[k];
+                        }
+                        for (int k = 0; k < OG_NPARAM; ++k) {
+                            if (val[k] < mn[k]) mn[k] = val[k];
+                            if (val[k] > mx[k]) mx[k] = val[k];
+                        }
+                    }
+                    for (int k = 0; k < OG_NPARAM; ++k) {
+                        lo_d[k] += mn[k] - vstar[k];
+                        hi_d[k] += mx[k] - vstar[k];
                     }
                 }
             }
@@ -348,60 +548,23 @@ int64_t og_render_grad(const double* params, int64_t N, const int32_t dims[3], c
             o[9] = dv;
             o[10] = dr;
         }
-        /* Chain C = R D R^T, D = diag(s^-2), G = dL/dC (full symmetric matrix):
-         *   dL/dD_mm = (R^T G R)_mm, dL/dR = 2 G R D. */
-        double RtGR[3];
-        for (int m = 0; m < 3; ++m) {
-            double acc = 0.0;
-            for (int a = 0; a < 3; ++a)
-                for (int b = 0; b < 3; ++b) acc += g->R[a][m] * dC[a][b] * g->R[b][m];
-            RtGR[m] = acc;
-        }
-        for (int m = 0; m < 3; ++m) {
-            /* D_mm = exp(-2 log_s_m)  =>  dD_mm/dlog_s_m = -2 D_mm */
-            double Dmm = 1.0 / (g->s[m] * g->s[m]);
-            dp[3 + m] = RtGR[m] * (-2.0 * Dmm);
-        }
-        double dR[3][3];
-        for (int a = 0; a < 3; ++a)
-            for (int m = 0; m < 3; ++m) {
-                double acc = 0.0;
-                for (int b = 0; b < 3; ++b) acc += dC[a][b] * g->R[b][m];
-                dR[a][m] = 2.0 * acc / (g->s[m] * g->s[m]);
-            }
-        /* dR/dq for R(w, x, y, z) as in og_quat_to_R. */
-        double w = g->qn[0], x = g->qn[1], y = g->qn[2], z = g->qn[3];
-        double dqn[4];
-        dqn[0] = 2.0 * (-z * dR[0][1] + y * dR[0][2] + z * dR[1][0] - x * dR[1][2] - y * dR[2][0] +
-                        x * dR[2][1]);
-        dqn[1] = 2.0 * (y * dR[0][1] + z * dR[0][2] + y * dR[1][0] - 2.0 * x * dR[1][1] -
-                        w * dR[1][2] + z * dR[2][0] + w * dR[2][1] - 2.0 * x * dR[2][2]);
-        dqn[2] = 2.0 * (-2.0 * y * dR[0][0] + x * dR[0][1] + w * dR[0][2] + x * dR[1][0] +
-                        z * dR[1][2] - w * dR[2][0] + z * dR[2][1] - 2.0 * y * dR[2][2]);
-        dqn[3] = 2.0 * (-2.0 * z * dR[0][0] - w * dR[0][1] + x * dR[0][2] + w * dR[1][0] -
-                        2.0 * z * dR[1][1] + y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
-        /* q_n = q / |q|  =>  dq = (dq_n - q_n (q_n . dq_n)) / |q| */
-        double dot = 0.0;
-        for (int k = 0; k < 4; ++k) dot += g->qn[k] * dqn[k];
-        for (int k = 0; k < 4; ++k) dp[6 + k] = (dqn[k] - g->qn[k] * dot) / g->qnorm;
-        for (int a = 0; a < 3; ++a) dp[a] = dmu[a];
-        /* (v, r) -> (A, T) -> raw (a, t) */
-        double dA, dT;
-        if (signal_mode == 0) {
-            dA = dv;
-            dT = dr;
-        } else {
-            dA = dv * g->T;
-            dT = dv * g->A;
-        }
-        dp[10] = a_act ? dA * g->A * (1.0 - g->A) : dA;
-        dp[11] = t_act ? dT * g->T * (1.0 - g->T) : dT;
+        og_chain(g, signal_mode, a_act, t_act, dmu, dC, dv, dr, dp);
+        if (dlo)
+            for (int k = 0; k < OG_NPARAM; ++k) dlo[i * OG_NPARAM + k] = dp[k] + lo_d[k];
+        if (dhi)
+            for (int k = 0; k < OG_NPARAM; ++k) dhi[i * OG_NPARAM + k] = dp[k] + hi_d[k];
     }
     free(G);
     free(I);
     free(W);
     free(S);
     free(amb);
+    free(Ss);
+    free(Ws);
+    free(aid);
+    free(avw);
+    free(aw);
+    free(arel);
     return n_invalid;
 }
 

@@ -1,8 +1,9 @@
 """Forward render on the GPU (Eq. 3-4, Sec. 3.3) against the FP64 oracle.
 
-Acceptance: max relative error of I <= 1e-5 over voxels with W > 1e-6, excluding voxels
-where some pair's d^2 lies within 2e-5 of the form's absolute terms of the truncation
-boundary (there an FP32 evaluation may fall either side, so both results are valid)."""
+Acceptance: max relative error of I <= 1e-5 over voxels with W > 1e-6, and of W <= 1e-5.
+At a voxel where some pair lies in the ambiguity band around the truncation boundary (an FP32
+evaluation of d^2 may fall on either side there), the result must match the oracle's sums for
+some include/exclude decision on those pairs: nothing is skipped."""
 import numpy as np
 import pytest
 
@@ -35,32 +36,40 @@ def gpu_render(params_np, og, brick=(8, 8, 8), signal_mode=0, a_act=0, t_act=0, 
     return out
 
 
-# W (the normaliser) is held to 5e-5: an FP32 rotation of a 24-voxel offset along the long
-# axis of a 16:1 anisotropic Gaussian leaves about 1e-5 relative error in a single weight.
-TOL_W = 5e-5
+# W (the normaliser) is held to 1e-5, except at voxels whose pairs are ill-conditioned in FP32:
+# a single weight's relative error is half the error of its d^2, and an FP32 evaluation of the
+# quadratic form from FP32 coefficients errs by a few units u = 2^-24 of its absolute terms
+# A = sum_ab |C_ab d_a d_b| (far along the long axis of a 16:1 Gaussian A exceeds d^2 by two
+# orders of magnitude). There W is held to 2 u times its weighted conditioning
+# cond = sum_i w_i A_i / W (the largest error measured on the clustered cloud is 0.85 u cond).
+TOL_W = 1e-5
+U32 = 2.0 ** -24
 
 
-def check_forward(I, W, ref, tol=TOL, max_tie_frac=0.02):
-    mask = (ref["W"] > 1e-6) & (ref["amb"] == 0)
-    assert mask.sum() > 0
-    excluded = ((ref["W"] > 1e-6) & (ref["amb"] > 0)).sum()
-    assert excluded <= max_tie_frac * (ref["W"] > 1e-6).sum() + 2
-    Io, Wo = ref["I"][mask], ref["W"][mask]
-    relI = np.abs(I[mask] - Io) / np.maximum(np.abs(Io), 1e-30)
-    relW = np.abs(W[mask] - Wo) / Wo
-    assert relI.max() <= tol, (relI.max(), np.argmax(relI))
-    assert relW.max() <= TOL_W, relW.max()
-    # voxels nobody reaches render exactly zero
-    none = ref["W"] == 0
-    assert np.all(W[none] == 0) and np.all(I[none] == 0)
-    return relI.max()
+def tol_w(ref):
+    cond = ref["cond_w"] / np.maximum(ref["W"], 1e-300)
+    return np.maximum(TOL_W, 2.0 * U32 * cond)
+
+
+def oracle_ref(params, og, cfg=None, crop=None):
+    import oracle
+    return oracle.render(np.asarray(params, np.float64), og, cfg or oracle.Config(), crop=crop,
+                         want_amb=True)
+
+
+def check_forward(I, W, ref, tol=TOL):
+    import oracle
+    st = oracle.forward_subset_check(I, W, ref, tol=tol, tol_w=tol_w(ref))
+    print("forward check:", {k: (round(v, 9) if isinstance(v, float) else v)
+                             for k, v in st.items()})
+    return st["max_relI"]
 
 
 def test_forward_workload_vs_oracle():
     """32^3 grid, 4,096 Gaussians (the forward-only workload), full volume."""
     import oracle
     params, og = c1()
-    ref = oracle.render(params.astype(np.float64), og)
+    ref = oracle_ref(params, og)
     out = gpu_render(params, og, stats=True)
     check_forward(out["I"], out["W"], ref)
     # effective pairs counted by the kernel = pairs with d^2 <= 9, up to boundary ties
@@ -94,7 +103,7 @@ def test_forward_ragged_anisotropic_grid():
     d["mu"] = d["mu"] + np.array(og.origin, np.float32)
     d["mu"][:50] = d["mu"][:50] * 1.6 - 10.0
     params = cloud_params(d)
-    ref = oracle.render(params.astype(np.float64), og)
+    ref = oracle_ref(params, og)
     out = gpu_render(params, og)
     check_forward(out["I"], out["W"], ref)
 
@@ -110,7 +119,7 @@ def test_forward_signal_modes_and_activations(mode, a_act, t_act):
     if t_act:
         p[:, 11] = rng.normal(-0.5, 1.5, p.shape[0])
     cfg = oracle.Config(signal_mode=mode, a_act=a_act, t_act=t_act)
-    ref = oracle.render(p.astype(np.float64), og, cfg)
+    ref = oracle_ref(p, og, cfg)
     out = gpu_render(p, og, signal_mode=mode, a_act=a_act, t_act=t_act)
     check_forward(out["I"], out["W"], ref)
 
@@ -126,7 +135,7 @@ def test_forward_edge_cases():
                   [10.0, 9.0, 6.0, np.log(0.05), np.log(0.05), np.log(0.05), 1, 0, 0, 0, 0.3, 0.5],
                   [10.0, 9.0, 6.0, np.log(40.0), np.log(30.0), np.log(20.0), 0.3, 0.2, 0.1, 0.9,
                    0.6, 0.8]], np.float32)
-    ref = oracle.render(p.astype(np.float64), og)
+    ref = oracle_ref(p, og)
     out = gpu_render(p, og)
     check_forward(out["I"], out["W"], ref)
     assert np.all(out["W"] > 0)
@@ -143,8 +152,7 @@ def test_forward_fit_workload_crops():
     assert out["status"] == 0
     for (x0, y0, z0) in ((116, 116, 52), (0, 0, 0), (232, 100, 104)):
         crop = (x0, x0 + 24, y0, y0 + 24, z0, z0 + 24)
-        ref = oracle.render(w["params0"].astype(np.float64), og, oracle.Config(t_act=1),
-                            crop=crop)
+        ref = oracle_ref(w["params0"], og, oracle.Config(t_act=1), crop=crop)
         sl = (slice(z0, z0 + 24), slice(y0, y0 + 24), slice(x0, x0 + 24))
         check_forward(out["I"][sl], out["W"][sl], ref)
 
@@ -156,7 +164,8 @@ def test_forward_clustered_anisotropic():
     og = oracle.Grid(64, 64, 64)
     d = inputs.gmm_cloud(3, 20000, (64, 64, 64), n_blobs=4, blob_std=8.0)
     params = cloud_params(d)
-    ref = oracle.render(params.astype(np.float64), og)
+    ref = oracle_ref(params, og)
     out = gpu_render(params, og)
-    # Hundreds of pairs per voxel in the blob cores: more voxels hold a boundary tie.
-    check_forward(out["I"], out["W"], ref, max_tie_frac=0.10)
+    # Hundreds of pairs per voxel in the blob cores: about 4 % of the voxels hold a boundary
+    # tie, each validated against every decision on its ambiguous pairs.
+    check_forward(out["I"], out["W"], ref)
