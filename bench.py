@@ -19,6 +19,14 @@ and replayed (it has no host synchronisation; --no-graph times eager calls); L2 
 (256 MB write) between timed steps; barrier + synchronize on both sides; max over ranks. `--gpus N` under torchrun runs
 N independent replicas (one scan per GPU; the path does not shard).
 
+Also on the default line (one GPU; `--no-extras` skips them): the pair rate of the same fit
+timed from step 1,000 (`mid_fit`: the cloud spreads as the fit proceeds); two complete
+2,000-step fits of a 256 x 256 x 160 phantom with 1M Gaussians at z factors 2 and 4
+(`full_fit_256x256x160_1M`, seconds per scan and PSNR / SSIM against the clean phantom), whose
+mean time is `fit_s_per_scan`; and the serving stream of 32 requests through the serving
+runtime against one request at a time (`serving`: p50 / p99 latency, scans per hour, and the
+mean PSNR each arm's fits end at).
+
 `--impl reference` times the FP64 CPU oracle (the only reference: the paper ships no code)
 on a bounded sample of the same workload, in the same unit.
 """
@@ -45,6 +53,8 @@ N_GAUSS = 500_000
 SHAPE_TRI = (155, 240, 240)
 LR_TRI = (100, 100, 100)
 FIT_ITERS = 2000
+MID_STEP = 1000               # the mid-fit pair rate is timed from this fitting step
+MID_TIMED = 100
 L2_FLUSH_BYTES = 256 << 20
 SM_COUNT_NOMINAL = 152
 EX2_PER_CLK_SM = 16           # MUFU ex2 results per clock per SM
@@ -87,6 +97,10 @@ def parse_args():
     ap.add_argument("--serve-budget-gb", type=float, default=150.0,
                     help="serve: device arena of the server")
     ap.add_argument("--serve-requests", type=int, default=32, help="serve: stream length")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="fit workload: skip the extra measurements of the default line (the "
+                         "mid-fit pair rate, two complete 256 x 256 x 160 fits with 1M Gaussians "
+                         "and the serving stream)")
     return ap.parse_args()
 
 
@@ -299,7 +313,8 @@ def run_reference(args, world, rank):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * tot_t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(args),
+            "config": dict(config_dict(args), launch="FP64 oracle on the host cores",
+                           l2="not applicable (CPU)"),
             "cpu_baseline": {"value": value, "unit": "pair-evals/s", "cores": oracle.num_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "pair-evals/s", "h2d_bytes_per_step": 0,
@@ -430,6 +445,28 @@ def run_ours(args, world, rank, local):
     # and credit each step with the mean of the two counts.
     n_eff_end, n_eval_end, n_pairs_end = pair_stats()
     n_eff_step = 0.5 * (n_eff + n_eff_end)
+
+    # mid-fit pair rate: the cloud spreads as the fit proceeds, so the first steps of a fit
+    # are not representative; continue the fit (untimed) to step MID_STEP and time
+    # MID_TIMED more replays there, pairs counted before and after them
+    mid = None
+    if not args.no_extras and graph is not None:
+        for _ in range(max(0, MID_STEP - int(st.d_step))):
+            graph.replay()
+        torch.cuda.synchronize()
+        m_eff0, m_eval0, _ = pair_stats()
+        mid_ms = []
+        for _ in range(MID_TIMED):
+            flush.fill_(1.0)
+            graph.replay()
+            events[-1].synchronize()
+            mid_ms.append(events[0].elapsed_time(events[-1]))
+        m_eff1, m_eval1, _ = pair_stats()
+        m_eff = 0.5 * (m_eff0 + m_eff1)
+        mid = {"from_step": MID_STEP, "steps": MID_TIMED,
+               "ms_per_step": statistics.mean(mid_ms),
+               "value": m_eff * MID_TIMED / (sum(mid_ms) / 1000.0), "unit": "pair-evals/s",
+               "effective_pairs": m_eff, "evaluated_pairs": 0.5 * (m_eval0 + m_eval1)}
     t_dev = sum(step_ms) / 1000.0
     value, t_max, _ = replica_throughput(n_eff_step * args.steps, t_dev, world)
     ms_step = 1000.0 * t_max / args.steps
@@ -484,16 +521,34 @@ def run_ours(args, world, rank, local):
                "h2d_bytes_per_step": h_params.numel() * 4 + h_lr.numel() * 4,
                "d2h_bytes_per_step": 4, "ms_per_step": 1000.0 * t_e2e / len(e2e_ms)}
 
+    # extra measurements of the default line (one GPU): two complete fits of the
+    # 256 x 256 x 160 phantom with 1M Gaussians (z box x2 and x4, Rician noise), and the
+    # serving stream against one-request-at-a-time service
+    fullfits, serving = None, None
+    if world == 1 and not tri and not args.no_extras:
+        del graph
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        fullfits = {f"zbox_noisy_x{f}": full_fit_case("zbox_noisy", f, 1_000_000, rank, cfg, dev)
+                    for f in (2, 4)}
+        serving = serve_metrics(args, rank, dev)
     if rank != 0:
         return
     nz, ny, nx = SHAPE_TRI if tri else SHAPE
+    if fullfits:
+        fit_s = statistics.mean(v["fit_s_per_scan"] for v in fullfits.values())
+        fit_basis = ("measured: mean of two complete 2,000-step fits of a 256x256x160 phantom "
+                     "with 1M Gaussians (z box x2 and x4, Rician noise), CUDA-graph replays")
+    else:
+        fit_s = FIT_ITERS * ms_step / 1000.0
+        fit_basis = f"extrapolated: {FIT_ITERS} x ms_per_step of this workload"
     line = {"metric": "gaussian_voxel_pair_evals_per_s", "value": value,
             "unit": "pair-evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded ellipsoid tissue phantom standing in for MSD/FeTA)",
             "config": config_dict(args),
-            "fit_s_per_scan": FIT_ITERS * ms_step / 1000.0,
+            "fit_s_per_scan": fit_s, "fit_s_per_scan_basis": fit_basis,
             "voxels_per_s": world * nx * ny * nz * args.steps / t_max,
             "pairs": {"effective": n_eff_step, "effective_first": n_eff,
                       "effective_last": n_eff_end, "evaluated": 0.5 * (n_eval + n_eval_end),
@@ -502,6 +557,12 @@ def run_ours(args, world, rank, local):
                       "counted": "mean of the first and last timed step"},
             "phase_ms": per_phase, "wall_s": wall,
             "roofline": roofline, "clocks": clk, "e2e": e2e, "gpu_launches": launches}
+    if mid:
+        line["mid_fit"] = mid
+    if fullfits:
+        line["full_fit_256x256x160_1M"] = fullfits
+    if serving:
+        line["serving"] = serving
     if world == 1 and not args.no_cpu_baseline and not tri:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -611,6 +672,69 @@ def ssim3d_t(x, ref, data_range: float = 1.0, sigma: float = 1.5) -> float:
     return float((num / den).mean())
 
 
+def full_fit_case(kind: str, f: int, n_gauss: int, seed: int, cfg, dev, shape=(160, 256, 256),
+                  iters: int = FIT_ITERS, chunk: int = 50, every: int = 250):
+    """One complete zero-shot fit: 2,000 Adam steps replayed from a CUDA graph of `chunk` steps
+    (bins sized for 40 pairs per Gaussian), from the lattice init of a seeded phantom's LR
+    scan: z box slice profile at factor f with Rician noise (sigma 0.02) ("zbox_noisy"), or
+    isotropic trilinear downsampling by f without noise fitted through the trilinear LR model
+    ("trilinear_clean"). Returns the seconds of graph replays, the status, and PSNR / SSIM
+    against the clean HR phantom of the fitted render (every `every` steps and at the end) and
+    of the trilinear upsampling of the LR scan."""
+    import torch
+    from paper_2603_09621_gb300 import gs, workloads
+    rcfg = gs.Config(t_act=1)
+    if kind == "zbox_noisy":
+        w = workloads.phantom_fit(shape=shape, s=f, n_gauss=n_gauss, seed=seed)
+        st = gs.FitState(w["params0"], w["lr"], w["grid"], f, cfg, capacity=40 * n_gauss)
+    else:
+        w = workloads.phantom_fit_trilinear(shape=shape, lr_shape=tuple(d // f for d in shape),
+                                            n_gauss=n_gauss, seed=seed, noise_sigma=0.0)
+        st = gs.FitState(w["params0"], w["lr"], w["grid"], 1, cfg, capacity=40 * n_gauss,
+                         lr_model=gs.GS_LR_TRILINEAR)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        st.step()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        for _ in range(chunk):
+            st.step()
+    # restart from the initial cloud
+    st.params.copy_(w["params0"])
+    st.m.zero_()
+    st.v.zero_()
+    st.d_step.zero_()
+    torch.cuda.synchronize()
+    curve, fit_ms = [], 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for it in range(0, iters + 1, chunk):
+        if it % every == 0:
+            I = gs.render(st.params, w["grid"], rcfg)[0]
+            curve.append([it, round(psnr_t(I, w["hr"]), 3)])
+        if it < iters:
+            e0.record()
+            graph.replay()
+            e1.record()
+            e1.synchronize()
+            fit_ms += e0.elapsed_time(e1)
+    rc, bits = st.check()
+    I = gs.render(st.params, w["grid"], rcfg)[0]
+    up = gs.gs_resample_fwd(w["lr"], shape)
+    torch.cuda.synchronize()
+    res = {"fit_s_per_scan": fit_ms / 1000.0, "steps": int(st.d_step), "status": rc,
+           "n_gauss": int(w["params0"].shape[0]),
+           "final_loss": float(st.d_loss), "psnr": psnr_t(I, w["hr"]), "ssim": ssim3d_t(I, w["hr"]),
+           "psnr_every_250_steps": curve,
+           "psnr_trilinear_upsampling": psnr_t(up, w["hr"]),
+           "ssim_trilinear_upsampling": ssim3d_t(up, w["hr"])}
+    del st, graph, w, I, up
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_fullfit(args, world, rank, local):
     """Complete zero-shot fits (not the headline line) of a 256 x 256 x 160 phantom, 2,000 Adam
     steps replayed from a CUDA graph of 50 steps (bins sized for 40 pairs per Gaussian):
@@ -623,94 +747,45 @@ def run_fullfit(args, world, rank, local):
     import torch
     from paper_2603_09621_gb300 import build as gbuild
     gbuild.build()
-    from paper_2603_09621_gb300 import gs, workloads
+    from paper_2603_09621_gb300 import gs
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    shape, iters, chunk, every = (160, 256, 256), FIT_ITERS, 50, 250
+    shape = (160, 256, 256)
     cfg = gs.Config(t_act=1, deterministic=0 if args.fast else 1)
-    rcfg = gs.Config(t_act=1)
     out = {}
     cases = [(k, f, n) for n in (1_000_000, 250_000)
              for k, f in (("zbox_noisy", 2), ("zbox_noisy", 4), ("trilinear_clean", 2),
                           ("trilinear_clean", 4))]
     for kind, f, n_gauss in cases:
-        if kind == "zbox_noisy":
-            w = workloads.phantom_fit(shape=shape, s=f, n_gauss=n_gauss, seed=rank)
-            st = gs.FitState(w["params0"], w["lr"], w["grid"], f, cfg, capacity=40 * n_gauss)
-        else:
-            w = workloads.phantom_fit_trilinear(shape=shape, lr_shape=tuple(d // f for d in shape),
-                                                n_gauss=n_gauss, seed=rank, noise_sigma=0.0)
-            st = gs.FitState(w["params0"], w["lr"], w["grid"], 1, cfg, capacity=40 * n_gauss,
-                             lr_model=gs.GS_LR_TRILINEAR)
-        side = torch.cuda.Stream()
-        side.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(side):
-            st.step()
-        torch.cuda.current_stream().wait_stream(side)
-        torch.cuda.synchronize()
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
-            for _ in range(chunk):
-                st.step()
-        # restart from the initial cloud
-        st.params.copy_(w["params0"])
-        st.m.zero_()
-        st.v.zero_()
-        st.d_step.zero_()
-        torch.cuda.synchronize()
-        curve, fit_ms = [], 0.0
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        for it in range(0, iters + 1, chunk):
-            if it % every == 0:
-                I = gs.render(st.params, w["grid"], rcfg)[0]
-                curve.append([it, round(psnr_t(I, w["hr"]), 3)])
-            if it < iters:
-                e0.record()
-                graph.replay()
-                e1.record()
-                e1.synchronize()
-                fit_ms += e0.elapsed_time(e1)
-        rc, bits = st.check()
-        I = gs.render(st.params, w["grid"], rcfg)[0]
-        up = gs.gs_resample_fwd(w["lr"], shape)
-        torch.cuda.synchronize()
-        out[f"{kind}_x{f}_N{n_gauss}"] = {
-            "fit_s_per_scan": fit_ms / 1000.0, "steps": int(st.d_step), "status": rc,
-            "final_loss": float(st.d_loss), "psnr": psnr_t(I, w["hr"]), "ssim": ssim3d_t(I, w["hr"]),
-            "psnr_every_250_steps": curve,
-            "psnr_trilinear_upsampling": psnr_t(up, w["hr"]),
-            "ssim_trilinear_upsampling": ssim3d_t(up, w["hr"])}
-        del st, graph, w, I, up
-        torch.cuda.empty_cache()
+        out[f"{kind}_x{f}_N{n_gauss}"] = full_fit_case(kind, f, n_gauss, rank, cfg, dev, shape)
     if rank == 0:
         nz, ny, nx = shape
-        print(json.dumps({"workload": f"full zero-shot fits: {nx}x{ny}x{nz} phantom, {iters} "
+        print(json.dumps({"workload": f"full zero-shot fits: {nx}x{ny}x{nz} phantom, {FIT_ITERS} "
                                       f"steps, deterministic", "results": out}), flush=True)
 
 
-def run_serve(args, world, rank, local):
-    """Serving stream (not the headline line): Poisson arrivals at 2 per second of requests
-    that fit a new scan (75 %: 128^3 to 256 x 256 x 192 voxels, slice factor 2-4, 100k-1M
-    Gaussians, 500 steps) or re-render an earlier fit on a new isotropic grid (25 %), through
-    the serving runtime with `--serve-active` requests resident, against the same stream one
-    request at a time; and the same requests all arriving at once (closed batch)."""
+def serve_metrics(args, rank, dev):
+    """Serving stream: Poisson arrivals at 2 per second of requests that fit a new scan (75 %:
+    128^3 to 256 x 256 x 192 voxels, slice factor 2-4, 100k-1M Gaussians, 500 steps) or
+    re-render an earlier fit on a new isotropic grid (25 %), through the serving runtime with
+    `--serve-active` requests resident, against the same stream one request at a time; and the
+    same requests all arriving at once (closed batch). Each arm reports latency percentiles,
+    makespan, scans per hour and the mean PSNR of its fitted scans against their phantoms."""
     import numpy as np
     import torch
-    from paper_2603_09621_gb300 import build as gbuild
-    gbuild.build()
-    from paper_2603_09621_gb300 import inputs, serve, workloads
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
+    from paper_2603_09621_gb300 import gs, inputs, serve, workloads
     draws = inputs.serving_draws(seed=rank, n=args.serve_requests)
     t0 = time.perf_counter()
-    reqs = workloads.serving_workload(draws, device=dev)
+    reqs = workloads.serving_workload(draws, device=dev, keep_hr=True)
     torch.cuda.synchronize()
     prep_s = time.perf_counter() - t0
     torch.cuda.empty_cache()
     budget = int(args.serve_budget_gb * (1 << 30))
     chunk = 25
+    rcfg = gs.Config(t_act=1)
+    fitted = {}
 
-    def play(max_active, arrivals, subset=None):
+    def play(max_active, arrivals, subset=None, name=None):
         use = reqs if subset is None else subset
         with serve.Server(budget, max_active=max_active, chunk_steps=chunk) as sv:
             t_base = sv.stats()["now_s"] + 0.05
@@ -726,32 +801,66 @@ def run_serve(args, world, rank, local):
             sv.run(timeout_s=3600)
             res = [sv.result(i) for i in ids]
             st = sv.stats()
+            psnrs, same = [], True
+            if name is not None:
+                # per-scan quality of the fitted clouds, and whether each equals the first arm's
+                for k, (r, i) in enumerate(zip(use, ids)):
+                    if r["kind"] != "fit" or res[k]["state"] != "done":
+                        continue
+                    out = sv.output(i).clone()
+                    if k in fitted:
+                        same = same and bool(torch.equal(out.view(torch.int32),
+                                                         fitted[k].view(torch.int32)))
+                    else:
+                        fitted[k] = out
+                    I = gs.render(out, r["grid"], rcfg)[0]
+                    psnrs.append(psnr_t(I, r["hr"]))
         lat = np.array([x["done_s"] - x["arrival_s"] for x in res])
         span = max(x["done_s"] for x in res) - t_base
         kinds = [r["kind"] for r in use]
-        return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-                "mean_s": float(lat.mean()),
-                "p50_fit_s": float(np.percentile(lat[[k == "fit" for k in kinds]], 50)),
-                "makespan_s": span, "scans_per_h": len(res) * 3600.0 / span,
-                "done": sum(x["state"] == "done" for x in res),
-                "failed": sum(x["state"] != "done" for x in res),
-                "peak_arena_gb": st["peak_bytes"] / (1 << 30),
-                "chunks": st["chunks_launched"], "graphs": st["graphs_captured"],
-                "grows": st["grows"]}
+        d = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+             "mean_s": float(lat.mean()),
+             "p50_fit_s": float(np.percentile(lat[[k == "fit" for k in kinds]], 50)),
+             "makespan_s": span, "scans_per_h": len(res) * 3600.0 / span,
+             "done": sum(x["state"] == "done" for x in res),
+             "failed": sum(x["state"] != "done" for x in res),
+             "peak_arena_gb": st["peak_bytes"] / (1 << 30),
+             "chunks": st["chunks_launched"], "graphs": st["graphs_captured"],
+             "grows": st["grows"]}
+        if name is not None:
+            d["psnr_mean_fits"] = float(np.mean(psnrs)) if psnrs else None
+            d["fits_identical_to_first_arm"] = same
+        return d
 
     # warm-up: the smallest fit once (module loading, first graph instantiation)
     small = min((r for r in reqs if r["kind"] == "fit"), key=lambda r: r["n_gauss"])
     play(1, False, [dict(small, iters=2 * chunk)])
     k = args.serve_active
-    out = {"stream": {f"active_{k}": play(k, True), "active_1": play(1, True)},
-           "batch": {f"active_{k}": play(k, False), "active_1": play(1, False)}}
+    out = {"stream": {f"active_{k}": play(k, True, name="s"), "active_1": play(1, True, name="s1")},
+           "batch": {f"active_{k}": play(k, False, name="b"), "active_1": play(1, False, name="b1")}}
     n_fit = sum(r["kind"] == "fit" for r in reqs)
+    out["gain_scans_per_h_batch"] = (out["batch"][f"active_{k}"]["scans_per_h"] /
+                                     out["batch"]["active_1"]["scans_per_h"])
+    out["workload"] = (f"{len(reqs)} requests ({n_fit} fits of 500 steps, {len(reqs) - n_fit} "
+                       f"re-renders), Poisson 2/s, {args.serve_budget_gb:.0f} GB arena, chunks of "
+                       f"{chunk} steps; sequential = one request resident")
+    out["prep_s"] = prep_s
+    del reqs, fitted
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serve(args, world, rank, local):
+    """Serving stream (not the headline line): see serve_metrics."""
+    import torch
+    from paper_2603_09621_gb300 import build as gbuild
+    gbuild.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    out = serve_metrics(args, rank, dev)
     if rank == 0:
-        print(json.dumps({
-            "workload": f"serving stream: {len(reqs)} requests ({n_fit} fits of 500 steps, "
-                        f"{len(reqs) - n_fit} re-renders), Poisson 2/s, "
-                        f"{args.serve_budget_gb:.0f} GB arena, chunks of {chunk} steps",
-            "prep_s": prep_s, "results": out}), flush=True)
+        print(json.dumps({"workload": "serving stream: " + out["workload"], "results": out}),
+              flush=True)
 
 
 def main():

@@ -88,11 +88,11 @@ def phantom_fit_trilinear(shape=(155, 240, 240), lr_shape=(100, 100, 100), n_gau
     return dict(grid=grid, hr=hr, lr=lr, params0=params0, nl=nl)
 
 
-def serving_workload(draws: list, device="cuda") -> list:
+def serving_workload(draws: list, device="cuda", keep_hr: bool = False) -> list:
     """Device inputs of a serving request stream (``inputs.serving_draws``): each fit gets its
     own phantom scan (seeded by its draw), noisy LR target and lattice-initialised cloud; each
     render gets its output grid. Returns the draws with ``grid`` added, and ``params0``,
-    ``lr`` for fits."""
+    ``lr`` (and with ``keep_hr`` the clean HR phantom ``hr``) for fits."""
     out = []
     for d in draws:
         e = dict(d)
@@ -101,6 +101,8 @@ def serving_workload(draws: list, device="cuda") -> list:
                             device=device)
             e.update(grid=w["grid"], params0=w["params0"], lr=w["lr"],
                      n_gauss=int(w["params0"].shape[0]))
+            if keep_hr:
+                e["hr"] = w["hr"]
             del w
         else:
             nz, ny, nx = d["shape"]

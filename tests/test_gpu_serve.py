@@ -190,3 +190,68 @@ def test_held_outputs_block_until_released():
         sv.run(timeout_s=60)
         assert sv.result(b)["state"] == "done"
         assert _equal(sv.output(b), first)
+
+
+def _tie_free_scan(seed=1, margin=(0.04, 0.08)):
+    """Small fitting workload built by the oracle (phantom, LR scan, lattice init), with an LR
+    target shifted from the oracle's initial prediction by +-[0.04, 0.08]: three Adam steps
+    move the prediction by less than that, so no residual of the L1 loss crosses zero and the
+    sign of its gradient is the same in FP32 and FP64."""
+    import numpy as np
+    import oracle
+    from helpers import phantom_fit
+    w = phantom_fit(shape=(32, 48, 48), s=4, n_gauss=6000, seed=seed, n_ell=5, semi=(5.0, 16.0))
+    cfg_o = oracle.Config(t_act=1)
+    r = oracle.render(w["params0"].astype(np.float64), w["grid"], cfg_o)
+    pred = oracle.downsample(r["I"], w["s"])
+    rng = np.random.default_rng(11)
+    shift = rng.choice([-1.0, 1.0], pred.shape) * rng.uniform(margin[0], margin[1], pred.shape)
+    return w, (pred + shift).astype(np.float32), cfg_o
+
+
+def test_served_fit_matches_oracle_alone_and_in_mix():
+    """A fit served alone (a graph chunk of 2 steps and an eager tail) and the same fit served
+    among two other scans' fits give identical bits, and both agree with the FP64 oracle's
+    composed fitting step (render, z box profile, L1, adjoints, Adam) iterated 3 times: the
+    last step's loss to 1e-5, and the parameters to the fit step's tolerance wherever every
+    step's gradient is clearly nonzero (elsewhere Adam's move is bounded by its rate)."""
+    import numpy as np
+    import oracle
+    from helpers import to_dev
+    torch, gs, serve, _ = _mods()
+    K = 3
+    w, target, cfg_o = _tie_free_scan()
+    og, s = w["grid"], w["s"]
+    n = w["params0"].shape[0]
+    p, m, v = w["params0"].astype(np.float64), np.zeros((n, 12)), np.zeros((n, 12))
+    grads, loss = [], None
+    for t in range(1, K + 1):
+        ref = oracle.fit_step(p, target, og, s, cfg_o, m, v, t)
+        grads.append(ref["grad"])
+        p, m, v, loss = ref["params"], ref["m"], ref["v"], ref["loss"]
+    grid = gs.Grid(og.nx, og.ny, og.nz)
+    p0, lr = to_dev(w["params0"]), to_dev(target)
+    with serve.Server(512 * MB, max_active=1, chunk_steps=2) as sv:
+        rid = sv.submit_fit(p0, lr, grid, s, K)
+        sv.run(timeout_s=120)
+        r = sv.result(rid)
+        assert r["state"] == "done" and r["steps_done"] == K
+        alone, alone_loss = sv.output(rid).clone(), r["loss"]
+    with serve.Server(2048 * MB, max_active=3, chunk_steps=2) as sv:
+        for seed in (3, 4):
+            q0, qlr, qg, qs = _scan(seed)
+            sv.submit_fit(q0, qlr, qg, qs, 7, arrival_s=0.0)
+        mid = sv.submit_fit(p0, lr, grid, s, K, arrival_s=0.0)
+        sv.run(timeout_s=300)
+        assert sv.stats()["n_done"] == 3
+        mixed = sv.output(mid).clone()
+    assert _equal(alone, mixed)
+    assert alone_loss == pytest.approx(loss, rel=1e-5)
+    got = alone.cpu().numpy().astype(np.float64)
+    clear = np.ones_like(got, dtype=bool)
+    for g in grads:
+        clear &= np.abs(g) > 1e-3 * np.sqrt((g ** 2).mean(0))[None, :]
+    assert clear.mean() > 0.5
+    np.testing.assert_allclose(got[clear], p[clear], rtol=1e-6, atol=K * 2e-6)
+    lrs = oracle.AdamConfig().lr_vector()[None, :] * np.ones_like(got)
+    assert np.all(np.abs(got - p) <= 2 * K * lrs + 1e-5)
