@@ -294,6 +294,28 @@ typedef struct {
 
 gs_status gs_fit_step(gs_fit_state* st, gs_stream stream);
 
+/* gs_fit_step split in two around its gradient, for one volume fitted by several processes,
+ * each owning a z-slab of it (the paper fits one scan on one device; the loss of Sec. 3.3 is
+ * a mean over LR voxels and its gradient (Eq. 5-6) a sum over voxels, so the slabs' gradients
+ * add up to the whole volume's, and one sum-reduction of grad between the two calls gives
+ * every process the same update).
+ * gs_fit_grad: bin, render, LR forward model, L1, adjoints and the chain to the raw
+ *   parameters, as gs_fit_step, without Adam: on return grad holds dL/d(params) of this
+ *   state's volume (zero if the step's binning overflowed the bins' capacity; the status word
+ *   then carries GS_STATUS_CAPACITY and *bins.d_npairs exceeds bins.capacity). The L1
+ *   mean is taken over n_lr_total LR values when n_lr_total > 0 (the whole volume's count, so
+ *   that d_loss and grad are this slab's share of the whole volume's loss and gradient), over
+ *   this state's own LR values when it is 0; n_lr_total < 0 is invalid. The step counter is
+ *   not changed. Phase events as gs_fit_step ([5] follows the chain).
+ * gs_fit_apply: one bias-corrected Adam update of params, m, v from grad with st->adam, and
+ *   the step counter incremented, unless d_skip (device int32, or NULL) holds a nonzero value:
+ *   then nothing changes (pass the OR over all processes of "my binning overflowed" so that an
+ *   overflow anywhere makes the step a no-op everywhere, as in gs_fit_step).
+ * With one process, gs_fit_grad(st, 0) followed by gs_fit_apply(st, overflowed) gives
+ * gs_fit_step's result bit for bit. */
+gs_status gs_fit_grad(gs_fit_state* st, int64_t n_lr_total, gs_stream stream);
+gs_status gs_fit_apply(gs_fit_state* st, const int32_t* d_skip, gs_stream stream);
+
 /* Synchronous: waits for `stream`, then copies the device status word to *h_status and
  * returns GS_ERR_CAPACITY or GS_ERR_NONFINITE if the matching bit is set, else GS_OK. */
 gs_status gs_status_read(const int32_t* d_status, int32_t* h_status, gs_stream stream);

@@ -227,7 +227,14 @@ gs_status resample_adj_prep_impl(const float* dlr, int32_t lnz, int32_t lny, int
                                  const float* I, const float* W, int32_t nz, int32_t ny, int32_t nx,
                                  float eps, float2* aip, cudaStream_t st);
 gs_status launch_l1(const float* pred, const float* target, int64_t n, float* d_loss,
-                    float* dpred, float* partials, cudaStream_t stream);
+                    float* dpred, float* partials, cudaStream_t stream, int64_t n_norm = 0);
+// Fitting-step tails (gs_param.cu): chain without Adam; Adam with an optional device skip flag.
+gs_status launch_chain_grad(const float* params, float* grad, const float* part,
+                            const float* gacc, const gs_bins* bins, int64_t n,
+                            const gs_grid* grid, const gs_config* cfg, cudaStream_t st);
+gs_status launch_adam(float* params, const float* grad, float* m, float* v, int64_t n_gauss,
+                      const gs_adam* hp, int32_t* d_step, const int32_t* d_skip,
+                      cudaStream_t st);
 
 }  // namespace gs
 

@@ -209,8 +209,10 @@ __device__ __forceinline__ float adam_one(float& p, float gr, float& m, float& v
 
 __global__ void __launch_bounds__(256) k_adam(float* __restrict__ params, const float* __restrict__ grad,
                                               float* __restrict__ m, float* __restrict__ v, int64_t n,
-                                              AdamLr hp, const int32_t* __restrict__ d_step) {
+                                              AdamLr hp, const int32_t* __restrict__ d_step,
+                                              const int32_t* __restrict__ d_skip) {
     pdl_enter();
+    if (d_skip && *d_skip != 0) return;  // the step was declared a no-op (see gs_fit_apply)
     const AdamCoef c = adam_coef(hp, d_step);
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += int64_t(gridDim.x) * blockDim.x) {
@@ -224,8 +226,8 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ params, const 
 
 // Fitting step tail, one thread per Gaussian: sum the per-brick partials in Gaussian-major
 // order (deterministic mode) or take the atomically accumulated gradient, chain it to the
-// raw parameters (written to grad), and apply Adam to params, m, v.
-template <bool kDet>
+// raw parameters (written to grad), and (kAdam) apply Adam to params, m, v.
+template <bool kDet, bool kAdam>
 __global__ void __launch_bounds__(256, 4) k_chain_adam(
     float* __restrict__ params, float* __restrict__ grad, float* __restrict__ m,
     float* __restrict__ v, const float* __restrict__ part, const float* __restrict__ gacc,
@@ -261,6 +263,7 @@ __global__ void __launch_bounds__(256, 4) k_chain_adam(
     load12(params + g * 12, p);
     chain_one(p, gv, C, out);
     store12(grad + g * 12, out);
+    if (!kAdam) return;
     load12(m + g * 12, mm);
     load12(v + g * 12, vv);
     const AdamCoef c = adam_coef(hp, d_step);
@@ -272,9 +275,11 @@ __global__ void __launch_bounds__(256, 4) k_chain_adam(
 }
 
 // Counts a step, unless npairs is given and the step's binning overflowed the pair capacity
-// (then the fitting step was a no-op).
-__global__ void k_step_inc(int32_t* d_step, const int64_t* __restrict__ npairs, int64_t capacity) {
+// (then the fitting step was a no-op), or d_skip is given and nonzero.
+__global__ void k_step_inc(int32_t* d_step, const int64_t* __restrict__ npairs, int64_t capacity,
+                           const int32_t* __restrict__ d_skip) {
     pdl_enter();
+    if (d_skip && *d_skip != 0) return;
     if (npairs) {
         const int64_t P = *npairs;
         if (P < 0 || P > capacity) return;
@@ -374,14 +379,59 @@ gs_status launch_chain_adam(float* params, float* grad, float* m, float* v, cons
     const AdamLr a = make_adam_lr(hp);
     const unsigned gb = static_cast<unsigned>((n + 255) / 256);
     if (cfg->deterministic)
-        launch_k(k_chain_adam<true>, dim3(gb), dim3(256), 0, st, params, grad, m, v, part, gacc,
-            bins->gm_off, bins->d_npairs, bins->capacity, n, C, a, d_step);
+        launch_k(k_chain_adam<true, true>, dim3(gb), dim3(256), 0, st, params, grad, m, v, part,
+            gacc, bins->gm_off, bins->d_npairs, bins->capacity, n, C, a, d_step);
     else
-        launch_k(k_chain_adam<false>, dim3(gb), dim3(256), 0, st, params, grad, m, v, part, gacc,
-            bins->gm_off, bins->d_npairs, bins->capacity, n, C, a, d_step);
+        launch_k(k_chain_adam<false, true>, dim3(gb), dim3(256), 0, st, params, grad, m, v, part,
+            gacc, bins->gm_off, bins->d_npairs, bins->capacity, n, C, a, d_step);
     gs_status s = last_launch_status();
     if (s != GS_OK) return s;
-    launch_k(k_step_inc, dim3(1), dim3(1), 0, st, d_step, bins->d_npairs, bins->capacity);
+    launch_k(k_step_inc, dim3(1), dim3(1), 0, st, d_step, bins->d_npairs, bins->capacity,
+        static_cast<const int32_t*>(nullptr));
+    return last_launch_status();
+}
+
+// The same tail without Adam: the raw-parameter gradient of the step into grad (zero when
+// the step's binning overflowed).
+gs_status launch_chain_grad(const float* params, float* grad, const float* part,
+                            const float* gacc, const gs_bins* bins, int64_t n,
+                            const gs_grid* grid, const gs_config* cfg, cudaStream_t st) {
+    ChainGeo C;
+    for (int k = 0; k < 3; ++k) C.h[k] = grid->h[k];
+    C.signal_mode = cfg->signal_mode;
+    C.a_act = cfg->a_act;
+    C.t_act = cfg->t_act;
+    const AdamLr a = {};
+    const unsigned gb = static_cast<unsigned>((n + 255) / 256);
+    float* p = const_cast<float*>(params);  // read only without Adam
+    if (cfg->deterministic)
+        launch_k(k_chain_adam<true, false>, dim3(gb), dim3(256), 0, st, p, grad,
+            static_cast<float*>(nullptr), static_cast<float*>(nullptr), part, gacc, bins->gm_off,
+            bins->d_npairs, bins->capacity, n, C, a, static_cast<const int32_t*>(nullptr));
+    else
+        launch_k(k_chain_adam<false, false>, dim3(gb), dim3(256), 0, st, p, grad,
+            static_cast<float*>(nullptr), static_cast<float*>(nullptr), part, gacc, bins->gm_off,
+            bins->d_npairs, bins->capacity, n, C, a, static_cast<const int32_t*>(nullptr));
+    return last_launch_status();
+}
+
+// Adam over n values of params with grad, moments m, v and the step counter d_step; nothing
+// changes when d_skip is given and nonzero.
+gs_status launch_adam(float* params, const float* grad, float* m, float* v, int64_t n_gauss,
+                      const gs_adam* hp, int32_t* d_step, const int32_t* d_skip,
+                      cudaStream_t st) {
+    if (n_gauss > 0) {
+        if (!adam_ok(hp)) return GS_ERR_INVALID_ARG;
+        const AdamLr a = make_adam_lr(hp);
+        const int64_t n = n_gauss * 12;
+        const int64_t blocks64 = (n + 255) / 256;
+        const unsigned blocks = static_cast<unsigned>(blocks64 < 65536 ? blocks64 : 65536);
+        launch_k(k_adam, dim3(blocks), dim3(256), 0, st, params, grad, m, v, n, a, d_step, d_skip);
+        gs_status s = last_launch_status();
+        if (s != GS_OK) return s;
+    }
+    launch_k(k_step_inc, dim3(1), dim3(1), 0, st, d_step, static_cast<const int64_t*>(nullptr),
+        int64_t(0), d_skip);
     return last_launch_status();
 }
 }  // namespace gs
@@ -403,19 +453,8 @@ extern "C" gs_status gs_adam_step(float* params, const float* grad, float* m, fl
                                   gs_stream stream) {
     if (n_gauss < 0 || !hp || !d_step) return GS_ERR_INVALID_ARG;
     if (n_gauss > 0 && (!params || !grad || !m || !v)) return GS_ERR_INVALID_ARG;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (n_gauss > 0) {
-        if (!adam_ok(hp)) return GS_ERR_INVALID_ARG;
-        const AdamLr a = make_adam_lr(hp);
-        const int64_t n = n_gauss * 12;
-        const int64_t blocks64 = (n + 255) / 256;
-        const unsigned blocks = static_cast<unsigned>(blocks64 < 65536 ? blocks64 : 65536);
-        launch_k(k_adam, dim3(blocks), dim3(256), 0, st, params, grad, m, v, n, a, d_step);
-        gs_status s = last_launch_status();
-        if (s != GS_OK) return s;
-    }
-    launch_k(k_step_inc, dim3(1), dim3(1), 0, st, d_step, nullptr, 0);
-    return last_launch_status();
+    return launch_adam(params, grad, m, v, n_gauss, hp, d_step, nullptr,
+                       reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" gs_status gs_init_lattice_lr(const float* lr, int32_t lnz, int32_t lny, int32_t lnx,

@@ -149,8 +149,10 @@ static bool vec_ok(const void* a, const void* b, int64_t plane, int slices) {
 }
 
 gs_status launch_l1(const float* pred, const float* target, int64_t n, float* d_loss, float* dpred,
-                    float* partials, cudaStream_t st) {
-    const float inv_n = n > 0 ? 1.0f / float(n) : 0.0f;
+                    float* partials, cudaStream_t st, int64_t n_norm) {
+    // the mean's normaliser: n, or n_norm > 0 when these values are one part of a larger mean
+    const int64_t nn = n_norm > 0 ? n_norm : n;
+    const float inv_n = nn > 0 ? 1.0f / float(nn) : 0.0f;
     launch_k(k_l1_partial, dim3(kL1Blocks), dim3(256), 0, st, pred, target, n, inv_n, dpred,
         partials);
     gs_status s = last_launch_status();
@@ -252,7 +254,27 @@ extern "C" gs_status gs_l1_loss(const float* pred, const float* target, int64_t 
                      reinterpret_cast<cudaStream_t>(stream));
 }
 
-extern "C" gs_status gs_fit_step(gs_fit_state* st, gs_stream stream) {
+namespace {
+
+// One fitting iteration's common part: validation, workspace and phase events.
+struct FitRun {
+    gs_fit_state* st = nullptr;
+    Workspace w = {};
+    cudaStream_t cs = nullptr;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+
+    // Phase events: during stream capture they must be external event-record nodes, or they
+    // would only serve as capture-internal dependencies.
+    bool mark(int phase) const {
+        if (!st->n_phase_events) return true;
+        cudaEvent_t ev = static_cast<cudaEvent_t>(st->phase_events[phase]);
+        if (cap == cudaStreamCaptureStatusActive)
+            return cudaEventRecordWithFlags(ev, cs, cudaEventRecordExternal) == cudaSuccess;
+        return cudaEventRecord(ev, cs) == cudaSuccess;
+    }
+};
+
+gs_status fit_prepare(gs_fit_state* st, gs_stream stream, FitRun* run) {
     if (!st) return GS_ERR_INVALID_ARG;
     gs_status s = validate_grid_cfg(&st->grid, &st->cfg);
     if (s != GS_OK) return s;
@@ -272,31 +294,34 @@ extern "C" gs_status gs_fit_step(gs_fit_state* st, gs_stream stream) {
         return GS_ERR_INVALID_ARG;
     if (!bins_match(&st->bins, &st->grid, &st->cfg) || st->bins.n_gauss != st->n_gauss)
         return GS_ERR_INVALID_ARG;
-    Workspace w;
-    s = bind_workspace(st->ws, st->ws_bytes, st->n_gauss, st->bins.capacity, &st->grid, &st->cfg, &w);
+    s = bind_workspace(st->ws, st->ws_bytes, st->n_gauss, st->bins.capacity, &st->grid, &st->cfg,
+                       &run->w);
     if (s != GS_OK) return s;
     if (st->n_phase_events != 0 && (st->n_phase_events != GS_FIT_PHASES || !st->phase_events))
         return GS_ERR_INVALID_ARG;
-    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
-    // Phase events: during stream capture they must be external event-record nodes, or they
-    // would only serve as capture-internal dependencies.
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    if (st->n_phase_events && cudaStreamIsCapturing(cs, &cap) != cudaSuccess) return GS_ERR_CUDA;
-    auto mark = [&](int phase) -> bool {
-        if (!st->n_phase_events) return true;
-        cudaEvent_t ev = static_cast<cudaEvent_t>(st->phase_events[phase]);
-        if (cap == cudaStreamCaptureStatusActive)
-            return cudaEventRecordWithFlags(ev, cs, cudaEventRecordExternal) == cudaSuccess;
-        return cudaEventRecord(ev, cs) == cudaSuccess;
-    };
+    run->st = st;
+    run->cs = reinterpret_cast<cudaStream_t>(stream);
+    if (st->n_phase_events && cudaStreamIsCapturing(run->cs, &run->cap) != cudaSuccess)
+        return GS_ERR_CUDA;
+    return GS_OK;
+}
+
+// Bin, render, LR forward model, L1 (normalised by n_norm LR values when n_norm > 0, else by
+// the state's own count), its adjoint with the adjoint render's per-voxel factors, and the
+// adjoint render kernel; phase events 0-4.
+gs_status fit_front(const FitRun& run, int64_t n_norm) {
+    gs_fit_state* st = run.st;
+    const Workspace& w = run.w;
+    cudaStream_t cs = run.cs;
+    const bool trilinear = st->lr_model == GS_LR_TRILINEAR;
     const gs_grid& g = st->grid;
-    if (!mark(0)) return GS_ERR_CUDA;
-    s = bin_bricks_impl(st->params, &g, &st->cfg, &st->bins, w, cs);
+    if (!run.mark(0)) return GS_ERR_CUDA;
+    gs_status s = bin_bricks_impl(st->params, &g, &st->cfg, &st->bins, w, cs);
     if (s != GS_OK) return s;
-    if (!mark(1)) return GS_ERR_CUDA;
+    if (!run.mark(1)) return GS_ERR_CUDA;
     s = render_fwd_impl(&st->bins, &g, &st->cfg, st->I, st->W, nullptr, cs);
     if (s != GS_OK) return s;
-    if (!mark(2)) return GS_ERR_CUDA;
+    if (!run.mark(2)) return GS_ERR_CUDA;
     if (trilinear)
         s = resample_fwd_impl(st->I, g.nz, g.ny, g.nx, st->lr_pred, st->lr_nz, st->lr_ny, st->lr_nx, cs);
     else
@@ -305,7 +330,7 @@ extern "C" gs_status gs_fit_step(gs_fit_state* st, gs_stream stream) {
     const int64_t n_lr = trilinear ? int64_t(st->lr_nz) * st->lr_ny * st->lr_nx
                                    : int64_t(g.nz / st->s) * g.ny * g.nx;
     // L1 loss; its gradient overwrites lr_pred in place.
-    s = launch_l1(st->lr_pred, st->lr_target, n_lr, st->d_loss, st->lr_pred, w.l1_part, cs);
+    s = launch_l1(st->lr_pred, st->lr_target, n_lr, st->d_loss, st->lr_pred, w.l1_part, cs, n_norm);
     if (s != GS_OK) return s;
     if (trilinear) {
         s = resample_adj_prep_impl(st->lr_pred, st->lr_nz, st->lr_ny, st->lr_nx, st->I, st->W, g.nz,
@@ -329,16 +354,49 @@ extern "C" gs_status gs_fit_step(gs_fit_state* st, gs_stream stream) {
         s = last_launch_status();
         if (s != GS_OK) return s;
     }
-    if (!mark(3)) return GS_ERR_CUDA;
+    if (!run.mark(3)) return GS_ERR_CUDA;
     s = launch_adjoint_pairs(&st->bins, &g, &st->cfg, w, cs);
     if (s != GS_OK) return s;
-    if (!mark(4)) return GS_ERR_CUDA;
-    s = launch_chain_adam(st->params, st->grad, st->m, st->v, w.part, w.gacc, &st->bins, st->n_gauss,
-                          &g, &st->cfg, &st->adam, st->d_step, cs);
-    if (s != GS_OK) return s;
-    if (!mark(5)) return GS_ERR_CUDA;
-    if (!mark(6)) return GS_ERR_CUDA;
+    if (!run.mark(4)) return GS_ERR_CUDA;
     return GS_OK;
+}
+
+}  // namespace
+
+extern "C" gs_status gs_fit_step(gs_fit_state* st, gs_stream stream) {
+    FitRun run;
+    gs_status s = fit_prepare(st, stream, &run);
+    if (s != GS_OK) return s;
+    s = fit_front(run, 0);
+    if (s != GS_OK) return s;
+    s = launch_chain_adam(st->params, st->grad, st->m, st->v, run.w.part, run.w.gacc, &st->bins,
+                          st->n_gauss, &st->grid, &st->cfg, &st->adam, st->d_step, run.cs);
+    if (s != GS_OK) return s;
+    if (!run.mark(5)) return GS_ERR_CUDA;
+    if (!run.mark(6)) return GS_ERR_CUDA;
+    return GS_OK;
+}
+
+extern "C" gs_status gs_fit_grad(gs_fit_state* st, int64_t n_lr_total, gs_stream stream) {
+    if (n_lr_total < 0) return GS_ERR_INVALID_ARG;
+    FitRun run;
+    gs_status s = fit_prepare(st, stream, &run);
+    if (s != GS_OK) return s;
+    s = fit_front(run, n_lr_total);
+    if (s != GS_OK) return s;
+    s = launch_chain_grad(st->params, st->grad, run.w.part, run.w.gacc, &st->bins, st->n_gauss,
+                          &st->grid, &st->cfg, run.cs);
+    if (s != GS_OK) return s;
+    if (!run.mark(5)) return GS_ERR_CUDA;
+    if (!run.mark(6)) return GS_ERR_CUDA;
+    return GS_OK;
+}
+
+extern "C" gs_status gs_fit_apply(gs_fit_state* st, const int32_t* d_skip, gs_stream stream) {
+    if (!st || st->n_gauss <= 0 || !st->params || !st->grad || !st->m || !st->v || !st->d_step)
+        return GS_ERR_INVALID_ARG;
+    return launch_adam(st->params, st->grad, st->m, st->v, st->n_gauss, &st->adam, st->d_step,
+                       d_skip, reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" gs_status gs_status_read(const int32_t* d_status, int32_t* h_status, gs_stream stream) {

@@ -135,6 +135,8 @@ SIGNATURES = {
     "gs_resample_fwd": (ctypes.c_int, [_P, _I32, _I32, _I32, _P, _I32, _I32, _I32, _P]),
     "gs_resample_bwd": (ctypes.c_int, [_P, _I32, _I32, _I32, _P, _I32, _I32, _I32, _P]),
     "gs_fit_step": (ctypes.c_int, [_P, _P]),
+    "gs_fit_grad": (ctypes.c_int, [_P, _I64, _P]),
+    "gs_fit_apply": (ctypes.c_int, [_P, _P, _P]),
     "gs_status_read": (ctypes.c_int, [_P, _P, _P]),
     "gs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "gs_launch_count": (ctypes.c_ulonglong, []),
@@ -312,6 +314,10 @@ class Bins:
 
     def npairs(self) -> int:
         return int(self._view(self.c.d_npairs, 1, torch.int64).item())
+
+    def npairs_dev(self) -> torch.Tensor:
+        """Device int64 [1]: pairs needed by the last binning (no host synchronisation)."""
+        return self._view(self.c.d_npairs, 1, torch.int64)
 
     def status(self) -> int:
         return int(self._view(self.c.d_status, 1, torch.int32).item())
@@ -573,6 +579,34 @@ class FitState:
 
     def step(self, stream=None):
         _check(load().gs_fit_step(ctypes.byref(self.c), _stream(stream)), "gs_fit_step")
+
+    def grad_step(self, n_lr_total: int = 0, stream=None):
+        """gs_fit_grad: this state's gradient into self.grad, no Adam; the L1 mean is taken over
+        n_lr_total LR values when > 0 (a slab's share of a whole volume's loss)."""
+        _check(load().gs_fit_grad(ctypes.byref(self.c), int(n_lr_total), _stream(stream)),
+               "gs_fit_grad")
+
+    def apply(self, d_skip: torch.Tensor | None = None, stream=None):
+        """gs_fit_apply: Adam from self.grad, skipped when d_skip (device int32) is nonzero."""
+        _check(load().gs_fit_apply(ctypes.byref(self.c), _ptr(d_skip), _stream(stream)),
+               "gs_fit_apply")
+
+    def overflow_flag(self) -> torch.Tensor:
+        """Device int32 [1]: 1 when the last binning needed more pairs than the capacity."""
+        return (self.bins.npairs_dev() > self.capacity).to(torch.int32)
+
+    def grow(self, capacity: int | None = None):
+        """New bins and workspace for `capacity` pairs (default: 1.125 x the last binning's
+        count); parameters, moments and the step counter are kept."""
+        if capacity is None:
+            capacity = int(self.bins.npairs() * 1.125) + 4096
+        dev = self.params.device
+        n = self.params.shape[0]
+        self.capacity = capacity
+        self.bins = Bins(n, capacity, self.grid, self.cfg, dev)
+        self.ws = Workspace(n, capacity, self.grid, self.cfg, dev)
+        self.c.bins = self.bins.c
+        self.c.ws, self.c.ws_bytes = self.ws.buf.data_ptr(), self.ws.nbytes
 
     def check(self, stream=None):
         rc, bits = gs_status_read(self.bins, stream)
