@@ -504,10 +504,8 @@ def run_ours(args, world, rank, local):
     for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         flush.fill_(1.0)
         e0.record(stream)
-        st.params.copy_(h_params, non_blocking=True)
-        st.lr_target.copy_(h_lr, non_blocking=True)
-        st.step()
-        h_loss.copy_(st.d_loss, non_blocking=True)
+        # the C-ABI call with host buffers: copies in, the fitting step, the loss out
+        st.step_host(h_params, h_lr, h_loss)
         e1.record(stream)
         e1.synchronize()
         if i > 0:
@@ -837,10 +835,13 @@ def serve_metrics(args, rank, dev):
     play(1, False, [dict(small, iters=2 * chunk)])
     k = args.serve_active
     out = {"stream": {f"active_{k}": play(k, True, name="s"), "active_1": play(1, True, name="s1")},
-           "batch": {f"active_{k}": play(k, False, name="b"), "active_1": play(1, False, name="b1")}}
+           "batch": {f"active_{k}": play(k, False, name="b"), "active_1": play(1, False, name="b1"),
+                     f"active_{2 * k}": play(2 * k, False, name="b2")}}
     n_fit = sum(r["kind"] == "fit" for r in reqs)
     out["gain_scans_per_h_batch"] = (out["batch"][f"active_{k}"]["scans_per_h"] /
                                      out["batch"]["active_1"]["scans_per_h"])
+    out[f"gain_scans_per_h_batch_{2 * k}_resident"] = (
+        out["batch"][f"active_{2 * k}"]["scans_per_h"] / out["batch"]["active_1"]["scans_per_h"])
     out["workload"] = (f"{len(reqs)} requests ({n_fit} fits of 500 steps, {len(reqs) - n_fit} "
                        f"re-renders), Poisson 2/s, {args.serve_budget_gb:.0f} GB arena, chunks of "
                        f"{chunk} steps; sequential = one request resident")

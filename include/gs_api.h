@@ -313,6 +313,16 @@ gs_status gs_fit_step(gs_fit_state* st, gs_stream stream);
  *   overflow anywhere makes the step a no-op everywhere, as in gs_fit_step).
  * With one process, gs_fit_grad(st, 0) followed by gs_fit_apply(st, overflowed) gives
  * gs_fit_step's result bit for bit. */
+/* gs_fit_step with the step's inputs and its loss in host memory (the same step, for callers
+ * whose data lives on the host): copies h_params (host float [n_gauss, 12], or NULL to keep
+ * st->params) and h_lr_target (host float of the LR shape, or NULL to keep st->lr_target) to
+ * the state's device buffers, runs gs_fit_step, and copies the step's loss to *h_loss (host
+ * float, or NULL), all asynchronously on `stream` (one cudaMemcpyAsync per buffer; page-locked
+ * host memory makes the copies asynchronous). st->lr_target must be writable device memory
+ * when h_lr_target is given. The caller synchronises `stream` before reading *h_loss. */
+gs_status gs_fit_step_host(gs_fit_state* st, const float* h_params, const float* h_lr_target,
+                           float* h_loss, gs_stream stream);
+
 gs_status gs_fit_grad(gs_fit_state* st, int64_t n_lr_total, gs_stream stream);
 gs_status gs_fit_apply(gs_fit_state* st, const int32_t* d_skip, gs_stream stream);
 

@@ -377,6 +377,30 @@ extern "C" gs_status gs_fit_step(gs_fit_state* st, gs_stream stream) {
     return GS_OK;
 }
 
+extern "C" gs_status gs_fit_step_host(gs_fit_state* st, const float* h_params,
+                                      const float* h_lr_target, float* h_loss, gs_stream stream) {
+    if (!st || st->n_gauss <= 0 || !st->params || !st->lr_target || !st->d_loss)
+        return GS_ERR_INVALID_ARG;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t n_lr = st->lr_model == GS_LR_TRILINEAR
+                             ? int64_t(st->lr_nz) * st->lr_ny * st->lr_nx
+                             : (st->s > 0 ? int64_t(st->grid.nz / st->s) * st->grid.ny * st->grid.nx : 0);
+    if (n_lr <= 0) return GS_ERR_INVALID_ARG;
+    if (h_params && cudaMemcpyAsync(st->params, h_params, sizeof(float) * 12 * st->n_gauss,
+                                    cudaMemcpyHostToDevice, cs) != cudaSuccess)
+        return GS_ERR_CUDA;
+    if (h_lr_target && cudaMemcpyAsync(const_cast<float*>(st->lr_target), h_lr_target,
+                                       sizeof(float) * n_lr, cudaMemcpyHostToDevice,
+                                       cs) != cudaSuccess)
+        return GS_ERR_CUDA;
+    gs_status s = gs_fit_step(st, stream);
+    if (s != GS_OK) return s;
+    if (h_loss && cudaMemcpyAsync(h_loss, st->d_loss, sizeof(float), cudaMemcpyDeviceToHost,
+                                  cs) != cudaSuccess)
+        return GS_ERR_CUDA;
+    return GS_OK;
+}
+
 extern "C" gs_status gs_fit_grad(gs_fit_state* st, int64_t n_lr_total, gs_stream stream) {
     if (n_lr_total < 0) return GS_ERR_INVALID_ARG;
     FitRun run;

@@ -136,6 +136,7 @@ SIGNATURES = {
     "gs_resample_bwd": (ctypes.c_int, [_P, _I32, _I32, _I32, _P, _I32, _I32, _I32, _P]),
     "gs_fit_step": (ctypes.c_int, [_P, _P]),
     "gs_fit_grad": (ctypes.c_int, [_P, _I64, _P]),
+    "gs_fit_step_host": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "gs_fit_apply": (ctypes.c_int, [_P, _P, _P]),
     "gs_status_read": (ctypes.c_int, [_P, _P, _P]),
     "gs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -579,6 +580,21 @@ class FitState:
 
     def step(self, stream=None):
         _check(load().gs_fit_step(ctypes.byref(self.c), _stream(stream)), "gs_fit_step")
+
+    def step_host(self, h_params=None, h_lr_target=None, h_loss=None, stream=None):
+        """gs_fit_step_host: one step with its inputs (and loss) in host memory: h_params
+        [n_gauss, 12] and h_lr_target (LR shape) float32 CPU tensors (page-locked for
+        asynchronous copies) or None to keep the device copies; h_loss a float32 CPU scalar
+        tensor or None. Synchronise the stream before reading h_loss."""
+        for name, t in (("h_params", h_params), ("h_lr_target", h_lr_target), ("h_loss", h_loss)):
+            if t is not None and (t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous float32 host tensor")
+        if h_params is not None and h_params.numel() != self.params.numel():
+            raise ValueError("h_params has the wrong size")
+        if h_lr_target is not None and h_lr_target.numel() != self.lr_target.numel():
+            raise ValueError("h_lr_target has the wrong size")
+        _check(load().gs_fit_step_host(ctypes.byref(self.c), _ptr(h_params), _ptr(h_lr_target),
+                                       _ptr(h_loss), _stream(stream)), "gs_fit_step_host")
 
     def grad_step(self, n_lr_total: int = 0, stream=None):
         """gs_fit_grad: this state's gradient into self.grad, no Adam; the L1 mean is taken over

@@ -187,3 +187,26 @@ def test_fit_step_full_size_equals_composed_entry_points(lr_model):
     assert torch.equal(st.params.view(torch.int32), params.view(torch.int32))
     assert torch.equal(st.m.view(torch.int32), m.view(torch.int32))
     assert int(st.d_step) == int(d_step) == 1
+
+
+def test_fit_step_host_equals_device_step():
+    """gs_fit_step_host (inputs copied from page-locked host memory inside the call, loss copied
+    back) gives the device step's result bit for bit."""
+    import torch
+    gs = _gs()
+    w = small_fit()
+    og = w["grid"]
+    g = gs.Grid(og.nx, og.ny, og.nz)
+    a = gs.FitState(to_dev(w["params0"]), to_dev(w["lr"]), g, w["s"], gs.Config(t_act=1))
+    b = gs.FitState(torch.zeros_like(a.params), torch.zeros_like(a.lr_target), g, w["s"],
+                    gs.Config(t_act=1), capacity=a.capacity)
+    h_params = torch.as_tensor(w["params0"]).contiguous().pin_memory()
+    h_lr = torch.as_tensor(w["lr"]).contiguous().pin_memory()
+    h_loss = torch.full((), -1.0).pin_memory()
+    a.step()
+    b.step_host(h_params, h_lr, h_loss)
+    torch.cuda.synchronize()
+    assert torch.equal(a.params, b.params) and torch.equal(a.grad, b.grad)
+    assert float(h_loss) == float(a.d_loss)
+    with pytest.raises(ValueError):
+        b.step_host(h_params[:10].contiguous())
