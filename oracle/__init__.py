@@ -60,7 +60,7 @@ def lib():
         i64, f64, f32, i32 = ctypes.c_int64, ctypes.c_double, ctypes.c_float, ctypes.c_int
         _lib.og_render.restype = i64
         _lib.og_render.argtypes = [P, i64, P, P, P, P, f64, f64, i32, i32, i32, f64, i32,
-                                   P, P, P, P, P, P, P, P, P, P, P, P]
+                                   P, P, P, P, P, P, P, P, P, P, P, P, P]
         _lib.og_render_grad.restype = i64
         _lib.og_render_grad.argtypes = [P, i64, P, P, P, P, f64, f64, i32, i32, i32, f64, i32,
                                         P, P, P, P, P, P]
@@ -168,7 +168,8 @@ def render(params, grid: Grid, cfg: Config = Config(), crop=None, amb_tol=None, 
     Gaussian order) ``amb_id`` (the Gaussian, -1 for an unused slot), ``amb_vw`` (v w),
     ``amb_w`` (w = exp(-d^2/2) r whichever side of the boundary), ``amb_rel``
     ((d^2 - sigma_t^2) / sum_ab |C_ab d_a d_b|; <= 0 means the FP64 decision includes it);
-    and ``cond_w`` (sum over contributing pairs of w sum_ab |C_ab d_a d_b|).
+    ``cond_w`` (sum over contributing pairs of w sum_ab |C_ab d_a d_b|) and ``cond_i`` (the
+    same sum with each term also weighted by |v - I|, the sensitivity of I to that weight).
     """
     p = np.ascontiguousarray(params, dtype=np.float64).reshape(-1, 12)
     dims, h, o = _grid_arrays(grid)
@@ -187,14 +188,15 @@ def render(params, grid: Grid, cfg: Config = Config(), crop=None, amb_tol=None, 
                      amb_vw=np.zeros(shape + (AMB_SLOTS,), np.float64),
                      amb_w=np.zeros(shape + (AMB_SLOTS,), np.float64),
                      amb_rel=np.zeros(shape + (AMB_SLOTS,), np.float64),
-                     cond_w=np.zeros(shape, np.float64))
+                     cond_w=np.zeros(shape, np.float64), cond_i=np.zeros(shape, np.float64))
     ep = (lambda k: _ptr(extra[k]) if want_amb else None)
     n_bad = lib().og_render(_ptr(p), p.shape[0], _ptr(dims), _ptr(h), _ptr(o),
                             None if carr is None else _ptr(carr), cfg.trunc_sigma, cfg.eps,
                             cfg.signal_mode, cfg.a_act, cfg.t_act, float(amb_tol),
                             1 if prune else 0, _ptr(I), _ptr(W), _ptr(S), _ptr(amb),
                             _ptr(npair), ep("S_sure"), ep("W_sure"), ep("amb_id"),
-                            ep("amb_vw"), ep("amb_w"), ep("amb_rel"), ep("cond_w"))
+                            ep("amb_vw"), ep("amb_w"), ep("amb_rel"), ep("cond_w"),
+                            ep("cond_i"))
     if n_bad < 0:
         raise MemoryError("oracle render: allocation failed")
     out = dict(I=I, W=W, S=S, amb=amb, npair=npair, n_invalid=int(n_bad))
@@ -626,7 +628,8 @@ def forward_subset_check(I, W, ref, tol: float = 1e-5, tol_w=1e-5, w_min: float 
     A voxel passes if some subset s of its ambiguous pairs gives W_s = W_sure + sum_{k in s} w_k
     with |W - W_s| <= tol_w max(W_s, w_min) and, where W_s > w_min, I_s = S_s / max(W_s, eps)
     with |I - I_s| <= tol |I_s|. Voxels with no ambiguous pair must match the FP64 decision
-    (a voxel no Gaussian reaches renders exactly zero). ``tol_w`` may be an array (per voxel).
+    (a voxel no Gaussian reaches renders exactly zero). ``tol`` and ``tol_w`` may be arrays
+    (per voxel).
     Voxels with more than AMB_SLOTS ambiguous pairs cannot be enumerated; their share of the
     voxels with W > w_min must stay below ``max_unenum_frac``.
 
@@ -637,6 +640,7 @@ def forward_subset_check(I, W, ref, tol: float = 1e-5, tol_w=1e-5, w_min: float 
     W = np.asarray(W, np.float64)
     amb = ref["amb"]
     tw = np.broadcast_to(np.asarray(tol_w, np.float64), amb.shape)
+    ti = np.broadcast_to(np.asarray(tol, np.float64), amb.shape)
     live = ref["W"] > w_min
     stats = dict(n_live=int(live.sum()), n_plain=0, n_tie=0, n_unenum=0, flips=0,
                  tie_pairs=0, max_flip_rel=0.0, max_relI=0.0, max_relW=0.0)
@@ -650,7 +654,8 @@ def forward_subset_check(I, W, ref, tol: float = 1e-5, tol_w=1e-5, w_min: float 
         stats["max_relI"] = float(relI.max())
         stats["max_relW"] = float(relW.max())
         stats["max_relW_over_tol"] = float((relW / tw[m]).max())
-        bad = (relI > tol) | (relW > tw[m])
+        stats["max_relI_over_tol"] = float((relI / ti[m]).max())
+        bad = (relI > ti[m]) | (relW > tw[m])
         assert not bad.any(), ("plain voxels", int(bad.sum()), float(relI.max()),
                                float(relW.max()))
     none = (ref["W"] == 0) & (amb == 0)
@@ -666,10 +671,10 @@ def forward_subset_check(I, W, ref, tol: float = 1e-5, tol_w=1e-5, w_min: float 
         Ws = ref["W_sure"][sel][:, None] + w @ masks.T
         Ss = ref["S_sure"][sel][:, None] + vw @ masks.T
         Is = Ss / np.maximum(Ws, eps)
-        Wg, Ig, twv = W[sel][:, None], I[sel][:, None], tw[sel][:, None]
+        Wg, Ig, twv, tiv = W[sel][:, None], I[sel][:, None], tw[sel][:, None], ti[sel][:, None]
         errW = np.abs(Wg - Ws) / np.maximum(Ws, w_min)
         errI = np.abs(Ig - Is) / np.maximum(np.abs(Is), 1e-30)
-        okI = (Ws <= w_min) | (errI <= tol)
+        okI = (Ws <= w_min) | (errI <= tiv)
         ok = (errW <= twv) & okI
         good = ok.any(axis=1)
         assert good.all(), ("tie voxels", int((~good).sum()), n)

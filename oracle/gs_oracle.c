@@ -211,7 +211,9 @@ static double og_d2_abs(const og_gauss* g, const double d[3]) {
  *   amb_w = w_i with w_i = exp(-d^2/2) r_i whichever side of the boundary d^2 lies,
  *   amb_rel = (d^2 - sigma_t^2) / sum_ab |C_ab d_a d_b| (<= 0: the pair contributes to S, W);
  *   cond_w = sum_i w_i sum_ab |C_ab d_a d_b| over contributing pairs (the rounding scale of
- *   the voxel's quadratic forms, weighted as W).
+ *   the voxel's quadratic forms, weighted as W);
+ *   cond_i = sum_i w_i |v_i - I| sum_ab |C_ab d_a d_b| over contributing pairs (the same scale
+ *   weighted as the sensitivity of I to each weight, dI/dw_i = (v_i - I) / W).
  * Returns the number of invalid Gaussians.
  */
 int64_t og_render(const double* params, int64_t N, const int32_t dims[3], const double h[3],
@@ -219,7 +221,7 @@ int64_t og_render(const double* params, int64_t N, const int32_t dims[3], const 
                   int signal_mode, int a_act, int t_act, double amb_tol, int prune, double* I,
                   double* W, double* S, int32_t* amb, int32_t* npair, double* S_sure,
                   double* W_sure, int32_t* amb_id, double* amb_vw, double* amb_w,
-                  double* amb_rel, double* cond_w) {
+                  double* amb_rel, double* cond_w, double* cond_i) {
     int32_t c[6] = {0, dims[0], 0, dims[1], 0, dims[2]};
     if (crop) memcpy(c, crop, sizeof(c));
     const int64_t cx = c[1] - c[0], cy = c[3] - c[2], cz = c[5] - c[4];
@@ -292,6 +294,29 @@ int64_t og_render(const double* params, int64_t N, const int32_t dims[3], const 
             }
         }
         for (int64_t k = 0; k < cy * cx; ++k) I[zoff + k] = Sz[k] / (Wz[k] > eps ? Wz[k] : eps);
+        if (!cond_i) continue;
+        /* second pass over the slice, now that I is known */
+        for (int64_t k = 0; k < cy * cx; ++k) cond_i[zoff + k] = 0.0;
+        for (int64_t i = 0; i < N; ++i) {
+            const og_gauss* g = &G[i];
+            if (!g->valid || z < g->lo[2] || z > g->hi[2]) continue;
+            int ylo = g->lo[1] > c[2] ? g->lo[1] : c[2];
+            int yhi = g->hi[1] < c[3] - 1 ? g->hi[1] : c[3] - 1;
+            int xlo = g->lo[0] > c[0] ? g->lo[0] : c[0];
+            int xhi = g->hi[0] < c[1] - 1 ? g->hi[0] : c[1] - 1;
+            for (int y = ylo; y <= yhi; ++y) {
+                const double py = origin[1] + (y + 0.5) * h[1];
+                for (int x = xlo; x <= xhi; ++x) {
+                    const double px = origin[0] + (x + 0.5) * h[0];
+                    double d[3] = {px - g->mu[0], py - g->mu[1], pz - g->mu[2]};
+                    double d2 = og_d2(g, d);
+                    if (!(d2 <= s2)) continue;
+                    int64_t idx = (int64_t)(y - c[2]) * cx + (x - c[0]);
+                    double w = exp(-0.5 * d2) * g->r;
+                    cond_i[zoff + idx] += w * fabs(g->v - I[zoff + idx]) * og_d2_abs(g, d);
+                }
+            }
+        }
     }
     free(G);
     return n_invalid;
@@ -405,7 +430,7 @@ int64_t og_render_grad(const double* params, int64_t N, const int32_t dims[3], c
     if (!I || !W || !S || !amb) return -1;
     int64_t n_invalid = og_render(params, N, dims, h, origin, crop, sigma_t, eps, signal_mode,
                                   a_act, t_act, tol_r, prune, I, W, S, amb, NULL, Ss, Ws, aid,
-                                  avw, aw, arel, NULL);
+                                  avw, aw, arel, NULL, NULL);
     og_gauss* G = og_activate_all(params, N, dims, h, origin, sigma_t, tol_r, signal_mode, a_act,
                                   t_act, prune);
     const double s2 = sigma_t * sigma_t;

@@ -37,7 +37,7 @@ def _brute(p, grid, sigma_t=3.0, band=0.0):
 def test_ambiguity_outputs_against_brute_force(oracle_mod):
     """A widened band (1e-2 of the absolute terms) puts hundreds of pairs in it. Per voxel the
     count, the slots (Gaussian, v w, w, relative distance to the boundary, in Gaussian order),
-    the sure sums and the conditioning sum must equal numpy brute force over all pairs.
+    the sure sums and the conditioning sums must equal numpy brute force over all pairs.
     Catches a sure sum that keeps band pairs, a slot that stores w only inside the boundary, a
     wrong sign or scale of the relative distance, and slots out of order."""
     import oracle
@@ -59,6 +59,10 @@ def test_ambiguity_outputs_against_brute_force(oracle_mod):
                                atol=1e-300)
     np.testing.assert_allclose(r["cond_w"].ravel(), (w * dabs * inside).sum(1), rtol=1e-12,
                                atol=1e-300)
+    Ib = (v * w * inside).sum(1) / np.maximum((w * inside).sum(1), 1e-12)
+    np.testing.assert_allclose(r["cond_i"].ravel(),
+                               (w * dabs * np.abs(v - Ib[:, None]) * inside).sum(1),
+                               rtol=1e-9, atol=1e-14)
     ids = r["amb_id"].reshape(-1, oracle.AMB_SLOTS)
     for vox in np.nonzero(amb.any(1))[0]:
         want = np.nonzero(amb[vox])[0][:oracle.AMB_SLOTS]
