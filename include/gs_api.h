@@ -317,9 +317,13 @@ gs_status gs_fit_step(gs_fit_state* st, gs_stream stream);
  * whose data lives on the host): copies h_params (host float [n_gauss, 12], or NULL to keep
  * st->params) and h_lr_target (host float of the LR shape, or NULL to keep st->lr_target) to
  * the state's device buffers, runs gs_fit_step, and copies the step's loss to *h_loss (host
- * float, or NULL), all asynchronously on `stream` (one cudaMemcpyAsync per buffer; page-locked
- * host memory makes the copies asynchronous). st->lr_target must be writable device memory
- * when h_lr_target is given. The caller synchronises `stream` before reading *h_loss. */
+ * float, or NULL), asynchronously with respect to the host (one cudaMemcpyAsync per buffer;
+ * page-locked host memory makes the copies asynchronous). The LR target is copied on a side
+ * stream that the library creates once per device (with two events) at the first such call
+ * on it, overlapped with the step's binning and forward render; the step waits for it before
+ * its LR model, and the copy itself waits for the work issued on `stream` before the call.
+ * st->lr_target must be writable device memory when h_lr_target is given. The caller
+ * synchronises `stream` before reading *h_loss. */
 gs_status gs_fit_step_host(gs_fit_state* st, const float* h_params, const float* h_lr_target,
                            float* h_loss, gs_stream stream);
 

@@ -2,6 +2,8 @@
 // adjoint, the deterministic L1 loss, the fused fitting step and the small host utilities of
 // the C ABI.
 #include <cuda_runtime.h>
+
+#include <mutex>
 #include <stdint.h>
 
 #include <atomic>
@@ -262,6 +264,7 @@ struct FitRun {
     Workspace w = {};
     cudaStream_t cs = nullptr;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaEvent_t lr_ready = nullptr;  // if set: the LR target is ready when this event is
 
     // Phase events: during stream capture they must be external event-record nodes, or they
     // would only serve as capture-internal dependencies.
@@ -322,6 +325,7 @@ gs_status fit_front(const FitRun& run, int64_t n_norm) {
     s = render_fwd_impl(&st->bins, &g, &st->cfg, st->I, st->W, nullptr, cs);
     if (s != GS_OK) return s;
     if (!run.mark(2)) return GS_ERR_CUDA;
+    if (run.lr_ready && cudaStreamWaitEvent(cs, run.lr_ready, 0) != cudaSuccess) return GS_ERR_CUDA;
     if (trilinear)
         s = resample_fwd_impl(st->I, g.nz, g.ny, g.nx, st->lr_pred, st->lr_nz, st->lr_ny, st->lr_nx, cs);
     else
@@ -377,6 +381,34 @@ extern "C" gs_status gs_fit_step(gs_fit_state* st, gs_stream stream) {
     return GS_OK;
 }
 
+namespace {
+
+// Per-device side stream and events of gs_fit_step_host, created once with that device current.
+struct HostCopyRes {
+    cudaStream_t side = nullptr;
+    cudaEvent_t entry = nullptr, lr_done = nullptr;
+};
+constexpr int kMaxHostDevices = 64;
+std::mutex g_host_res_mutex;
+HostCopyRes g_host_res[kMaxHostDevices];
+
+gs_status host_copy_res(HostCopyRes** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxHostDevices) return GS_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_host_res_mutex);
+    HostCopyRes& r = g_host_res[dev];
+    if (!r.side) {
+        if (cudaStreamCreateWithFlags(&r.side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&r.entry, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&r.lr_done, cudaEventDisableTiming) != cudaSuccess)
+            return GS_ERR_CUDA;
+    }
+    *out = &r;
+    return GS_OK;
+}
+
+}  // namespace
+
 extern "C" gs_status gs_fit_step_host(gs_fit_state* st, const float* h_params,
                                       const float* h_lr_target, float* h_loss, gs_stream stream) {
     if (!st || st->n_gauss <= 0 || !st->params || !st->lr_target || !st->d_loss)
@@ -386,15 +418,33 @@ extern "C" gs_status gs_fit_step_host(gs_fit_state* st, const float* h_params,
                              ? int64_t(st->lr_nz) * st->lr_ny * st->lr_nx
                              : (st->s > 0 ? int64_t(st->grid.nz / st->s) * st->grid.ny * st->grid.nx : 0);
     if (n_lr <= 0) return GS_ERR_INVALID_ARG;
+    FitRun run;
+    gs_status s = fit_prepare(st, stream, &run);
+    if (s != GS_OK) return s;
+    if (h_lr_target) {
+        // the LR target goes over on a side stream while the step bins and renders; the step
+        // waits for it before the LR model. The side stream first waits for everything issued
+        // on `stream` so far, so an earlier step still reading lr_target is not overwritten.
+        HostCopyRes* r = nullptr;
+        s = host_copy_res(&r);
+        if (s != GS_OK) return s;
+        if (cudaEventRecord(r->entry, cs) != cudaSuccess ||
+            cudaStreamWaitEvent(r->side, r->entry, 0) != cudaSuccess ||
+            cudaMemcpyAsync(const_cast<float*>(st->lr_target), h_lr_target, sizeof(float) * n_lr,
+                            cudaMemcpyHostToDevice, r->side) != cudaSuccess ||
+            cudaEventRecord(r->lr_done, r->side) != cudaSuccess)
+            return GS_ERR_CUDA;
+        run.lr_ready = r->lr_done;
+    }
     if (h_params && cudaMemcpyAsync(st->params, h_params, sizeof(float) * 12 * st->n_gauss,
                                     cudaMemcpyHostToDevice, cs) != cudaSuccess)
         return GS_ERR_CUDA;
-    if (h_lr_target && cudaMemcpyAsync(const_cast<float*>(st->lr_target), h_lr_target,
-                                       sizeof(float) * n_lr, cudaMemcpyHostToDevice,
-                                       cs) != cudaSuccess)
-        return GS_ERR_CUDA;
-    gs_status s = gs_fit_step(st, stream);
+    s = fit_front(run, 0);
     if (s != GS_OK) return s;
+    s = launch_chain_adam(st->params, st->grad, st->m, st->v, run.w.part, run.w.gacc, &st->bins,
+                          st->n_gauss, &st->grid, &st->cfg, &st->adam, st->d_step, cs);
+    if (s != GS_OK) return s;
+    if (!run.mark(5) || !run.mark(6)) return GS_ERR_CUDA;
     if (h_loss && cudaMemcpyAsync(h_loss, st->d_loss, sizeof(float), cudaMemcpyDeviceToHost,
                                   cs) != cudaSuccess)
         return GS_ERR_CUDA;
