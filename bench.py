@@ -830,6 +830,40 @@ def serve_metrics(args, rank, dev):
             d["fits_identical_to_first_arm"] = same
         return d
 
+    def back_to_back():
+        """The same requests one after another without the serving runtime: each fit a plain
+        FitState stepped by replays of a CUDA graph of `chunk` steps (eager tail), each render
+        gs.render of its source's fitted cloud."""
+        out_p, psnrs, same = {}, [], True
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k, r in enumerate(reqs):
+            if r["kind"] == "fit":
+                st = gs.FitState(r["params0"], r["lr"], r["grid"], r["s"], rcfg,
+                                 capacity=12 * r["n_gauss"] + 4096)
+                n_chunks, tail = divmod(r["iters"], chunk)
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph):
+                    for _ in range(chunk):
+                        st.step()
+                for _ in range(n_chunks):
+                    graph.replay()
+                for _ in range(tail):
+                    st.step()
+                out_p[k] = st.params
+                del graph
+            else:
+                gs.render(out_p[r["source"]], r["grid"], rcfg)
+        torch.cuda.synchronize()
+        span = time.perf_counter() - t0
+        for k, p in out_p.items():
+            if k in fitted:
+                same = same and bool(torch.equal(p.view(torch.int32), fitted[k].view(torch.int32)))
+            I = gs.render(p, reqs[k]["grid"], rcfg)[0]
+            psnrs.append(psnr_t(I, reqs[k]["hr"]))
+        return {"makespan_s": span, "scans_per_h": len(reqs) * 3600.0 / span,
+                "psnr_mean_fits": float(np.mean(psnrs)), "fits_identical_to_first_arm": same}
+
     # warm-up: the smallest fit once (module loading, first graph instantiation)
     small = min((r for r in reqs if r["kind"] == "fit"), key=lambda r: r["n_gauss"])
     play(1, False, [dict(small, iters=2 * chunk)])
@@ -838,8 +872,11 @@ def serve_metrics(args, rank, dev):
            "batch": {f"active_{k}": play(k, False, name="b"), "active_1": play(1, False, name="b1"),
                      f"active_{2 * k}": play(2 * k, False, name="b2")}}
     n_fit = sum(r["kind"] == "fit" for r in reqs)
+    out["batch"]["back_to_back"] = back_to_back()
     out["gain_scans_per_h_batch"] = (out["batch"][f"active_{k}"]["scans_per_h"] /
                                      out["batch"]["active_1"]["scans_per_h"])
+    out["gain_scans_per_h_vs_back_to_back"] = (out["batch"][f"active_{k}"]["scans_per_h"] /
+                                               out["batch"]["back_to_back"]["scans_per_h"])
     out[f"gain_scans_per_h_batch_{2 * k}_resident"] = (
         out["batch"][f"active_{2 * k}"]["scans_per_h"] / out["batch"]["active_1"]["scans_per_h"])
     out["workload"] = (f"{len(reqs)} requests ({n_fit} fits of 500 steps, {len(reqs) - n_fit} "
