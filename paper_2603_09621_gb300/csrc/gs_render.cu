@@ -53,6 +53,31 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
+// Division by an invariant positive integer d (T. Granlund and P. L. Montgomery, "Division by
+// invariant integers using multiplication", PLDI 1994, the unsigned case): with
+// l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1, every 32-bit unsigned n has
+// n / d = (t + ((n - t) >> s1)) >> s2, t = mulhi(m, n), s1 = min(l, 1), s2 = max(l - 1, 0):
+// one high multiply, a subtraction and three shifts in place of a division sequence.
+struct FastDiv {
+    unsigned m;
+    int s1, s2;
+};
+
+inline FastDiv make_fastdiv(unsigned d) {
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    FastDiv f;
+    f.m = static_cast<unsigned>(((1ull << 32) * ((1ull << l) - d)) / d + 1ull);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l - 1 > 0 ? l - 1 : 0;
+    return f;
+}
+
+__device__ __forceinline__ unsigned fast_div(unsigned n, FastDiv f) {
+    const unsigned t = __umulhi(f.m, n);
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
 struct RenderGeo {
     int nx, ny, nz;
     int bsx, bsy, bsz;  // brick shape
@@ -63,7 +88,17 @@ struct RenderGeo {
     float Tcull;        // cull bound on q: T (1 + 1e-2) + 1e-3
     float sqrtTcull;    // sqrt(Tcull)
     float eps;
+    FastDiv dnbx, dnby;  // division by the brick counts along x and y
 };
+
+// Brick coordinates (along x, y, z) of brick index b (x fastest).
+__device__ __forceinline__ void brick_xyz(int b, const RenderGeo& G, int& bx, int& by, int& bz) {
+    const unsigned q = fast_div(static_cast<unsigned>(b), G.dnbx);
+    bx = b - static_cast<int>(q) * G.nbx;
+    const unsigned r = fast_div(q, G.dnby);
+    by = static_cast<int>(q - r * static_cast<unsigned>(G.nby));
+    bz = static_cast<int>(r);
+}
 
 struct Rec {
     float nmhx, nmlx;        // minus the mean's x head and tail
@@ -162,7 +197,8 @@ __global__ void __launch_bounds__(128, 10) k_render_fwd(const int32_t* __restric
     const int tid = threadIdx.x, lane = tid & 31;
     const int nthreads = blockDim.x;
     const int b = blockIdx.x;
-    const int bx = b % G.nbx, by = (b / G.nbx) % G.nby, bz = b / (G.nbx * G.nby);
+    int bx, by, bz;
+    brick_xyz(b, G, bx, by, bz);
     // half-warp per 4^3 footprint; a lane owns one x-row of 4 voxels
     const int foot = tid >> 4, l16 = lane & 15;
     const int n_foot = G.fx * G.fy * G.fz;
@@ -475,9 +511,10 @@ __global__ void __launch_bounds__(kBwdThreads, 7) k_render_bwd(
             sstage[q] = static_cast<unsigned char>(min(kb, kBwdStage));
             const int gid = gidv[h];
             sgid[q] = gid;
-            const int by = (b_t[h] / G.nbx) % G.nby, bz = b_t[h] / (G.nbx * G.nby);
+            int bxx, by, bz;
+            brick_xyz(b_t[h], G, bxx, by, bz);
             const unsigned long long m = brick_row_mask(load_rec_bwd(rec4 + int64_t(gid) * REC_F4), G,
-                                                        (b_t[h] % G.nbx) * G.bsx, by * G.bsy, bz * G.bsz);
+                                                        bxx * G.bsx, by * G.bsy, bz * G.bsz);
             smask[q] = m;
             bucket[h] = 64 - __popcll(static_cast<long long>(m));
             atomicAdd(&hist[bucket[h]], 1);
@@ -515,8 +552,9 @@ __global__ void __launch_bounds__(kBwdThreads, 7) k_render_bwd(
     const int bpairs = kPairs * G.bsy * G.bsz;
     for (int k = 0; k < n_stage; ++k) {
         const int b = sbrick[k];
-        const int x0 = (b % G.nbx) * BX, y0 = ((b / G.nbx) % G.nby) * G.bsy,
-                  z0 = (b / (G.nbx * G.nby)) * G.bsz;
+        int bxx, byy, bzz;
+        brick_xyz(b, G, bxx, byy, bzz);
+        const int x0 = bxx * BX, y0 = byy * G.bsy, z0 = bzz * G.bsz;
         float4* dst = &sfac[k * kStageStride];
         if (x0 + BX <= G.nx && y0 + G.bsy <= G.ny && z0 + G.bsz <= G.nz && (G.nx & 1) == 0) {
             // brick inside the grid, rows 16-byte aligned: float4 loads of voxels (2c, 2c+1)
@@ -565,7 +603,8 @@ __global__ void __launch_bounds__(kBwdThreads, 7) k_render_bwd(
         const int lt = sorder[rank];
         const int64_t i = base + lt;
         const int b = pair_brick[i];
-        const int bx = b % G.nbx, by = (b / G.nbx) % G.nby, bz = b / (G.nbx * G.nby);
+        int bx, by, bz;
+        brick_xyz(b, G, bx, by, bz);
         const int x0 = bx * BX, y0 = by * G.bsy, z0 = bz * G.bsz;
         const int stage = sstage[lt];
         const Rec R = load_rec_bwd(rec4 + int64_t(sgid[lt]) * REC_F4);
@@ -655,6 +694,8 @@ RenderGeo make_geo(const gs_grid* grid, const gs_config* cfg) {
     G.Tcull = G.T * (1.0f + 1e-2f) + 1e-3f;
     G.sqrtTcull = sqrtf(G.Tcull);
     G.eps = cfg->eps;
+    G.dnbx = make_fastdiv(static_cast<unsigned>(b.nbx));
+    G.dnby = make_fastdiv(static_cast<unsigned>(b.nby));
     return G;
 }
 
