@@ -185,6 +185,7 @@ struct GridF {
     float ih[3];  // 1 / h
     int b[3];
     int nb[3];
+    FastDiv db[3];  // division by the brick size along each axis
 };
 
 // Error-free sum (Knuth): s + e == a + b exactly, s = fl(a + b).
@@ -283,8 +284,8 @@ __global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ pa
         int b0[3], b1[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            b0[k] = lo[k] / G.b[k];
-            b1[k] = hi[k] / G.b[k];
+            b0[k] = static_cast<int>(fast_div(static_cast<unsigned>(lo[k]), G.db[k]));
+            b1[k] = static_cast<int>(fast_div(static_cast<unsigned>(hi[k]), G.db[k]));
             br[k] = b0[k];
             br[3 + k] = b1[k];
         }
@@ -730,6 +731,7 @@ gs_status bin_bricks_impl(const float* params, const gs_grid* grid, const gs_con
     }
     G.b[0] = b.bx; G.b[1] = b.by; G.b[2] = b.bz;
     G.nb[0] = b.nbx; G.nb[1] = b.nby; G.nb[2] = b.nbz;
+    for (int k = 0; k < 3; ++k) G.db[k] = make_fastdiv(static_cast<unsigned>(G.b[k]));
 
     if (cudaMemsetAsync(bins->d_status, 0, sizeof(int32_t), st) != cudaSuccess) return GS_ERR_CUDA;
     long long* total = ws.scan_tmp + ws.scan_tmp_len - 1;

@@ -148,6 +148,26 @@ inline bool carve_workspace(void* base, int64_t n_gauss, int64_t capacity, int32
     return true;
 }
 
+// Division by an invariant positive integer d (T. Granlund and P. L. Montgomery, "Division by
+// invariant integers using multiplication", PLDI 1994, the unsigned case): with
+// l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1, every 32-bit unsigned n has
+// n / d = (t + ((n - t) >> s1)) >> s2, t = mulhi(m, n), s1 = min(l, 1), s2 = max(l - 1, 0):
+// one high multiply, a subtraction and three shifts in place of a division sequence.
+struct FastDiv {
+    unsigned m;
+    int s1, s2;
+};
+
+inline FastDiv make_fastdiv(unsigned d) {
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    FastDiv f;
+    f.m = static_cast<unsigned>(((1ull << 32) * ((1ull << l) - d)) / d + 1ull);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l - 1 > 0 ? l - 1 : 0;
+    return f;
+}
+
 // ------------------------------------------------------------------ helpers
 struct BrickGeom {
     int nbx, nby, nbz;
@@ -287,6 +307,12 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 }
 
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+__device__ __forceinline__ unsigned fast_div(unsigned n, FastDiv f) {
+    const unsigned t = __umulhi(f.m, n);
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
 
 }  // namespace gs
 #endif

@@ -53,31 +53,6 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
-// Division by an invariant positive integer d (T. Granlund and P. L. Montgomery, "Division by
-// invariant integers using multiplication", PLDI 1994, the unsigned case): with
-// l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1, every 32-bit unsigned n has
-// n / d = (t + ((n - t) >> s1)) >> s2, t = mulhi(m, n), s1 = min(l, 1), s2 = max(l - 1, 0):
-// one high multiply, a subtraction and three shifts in place of a division sequence.
-struct FastDiv {
-    unsigned m;
-    int s1, s2;
-};
-
-inline FastDiv make_fastdiv(unsigned d) {
-    int l = 0;
-    while ((1ull << l) < d) ++l;
-    FastDiv f;
-    f.m = static_cast<unsigned>(((1ull << 32) * ((1ull << l) - d)) / d + 1ull);
-    f.s1 = l < 1 ? l : 1;
-    f.s2 = l - 1 > 0 ? l - 1 : 0;
-    return f;
-}
-
-__device__ __forceinline__ unsigned fast_div(unsigned n, FastDiv f) {
-    const unsigned t = __umulhi(f.m, n);
-    return (t + ((n - t) >> f.s1)) >> f.s2;
-}
-
 struct RenderGeo {
     int nx, ny, nz;
     int bsx, bsy, bsz;  // brick shape
