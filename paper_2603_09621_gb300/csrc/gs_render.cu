@@ -269,38 +269,41 @@ __global__ void __launch_bounds__(128, 10) k_render_fwd(const int32_t* __restric
 // yc = mu_y - (P2yz / 2 Pyy) dz and hw^2 = Tcull / Pyy - c3 dz^2,
 // c3 = (Pzz - P2yz^2 / 4 Pyy) / Pyy (the interval is padded; Tcull carries a 1 % margin).
 // A z-plane whose section of the truncated ellipsoid misses the brick's x range is skipped.
+// The mask is a conservative superset only (the rows themselves test q <= T), so the plane
+// offsets are taken as dz(z0) + rz and positions relative to the brick, inside the padding.
 __device__ __forceinline__ unsigned long long brick_row_mask(const Rec& R, const RenderGeo& G,
                                                              int x0, int y0, int z0) {
     unsigned long long mask = 0;
-    const float mu_y = -(R.nmh_yz.x + R.nml_yz.x);
-    const float mu_x = -(R.nmhx + R.nmlx);
     const float ipyy = __fdividef(1.0f, R.pyc1.x);
     const float k1 = -0.5f * (R.pc2.x * ipyy);
-    const float c3 = (R.pzz - 0.25f * R.pc2.x * (R.pc2.x * ipyy)) * ipyy;
+    const float nc3 = -(R.pzz - 0.25f * R.pc2.x * (R.pc2.x * ipyy)) * ipyy;
     const float h0 = G.Tcull * ipyy;
+    const float mu_y = -(R.nmh_yz.x + R.nml_yz.x);
+    const float mu_x = -(R.nmhx + R.nmlx);
     const float pad = 1e-3f + 1e-5f * fabsf(mu_y);
-    // x extent of the section through plane dz: centre mu_x + (c1 k1 + c2) dz, half-width
-    // hw_y sqrt(Pyy / a + c1^2) (hw_y the y half-width of the same section)
+    // the section's x extent through plane dz: centre mu_x + (c1 k1 + c2) dz, half-width
+    // hw_y sqrt(Pyy / a + c1^2) (hw_y the y half-width of the same section); tested as
+    // |centre - brick centre| <= half-width + brick half-width
     const float kx = fmaf(R.pyc1.y, k1, R.pc2.y);
     const float lam = sqrt_approx(fmaf(R.pyc1.x, __fdividef(1.0f, R.sa * R.sa), R.pyc1.y * R.pyc1.y));
-    const float padx = 1e-3f + 1e-5f * fabsf(mu_x);
-    const float xa = float(x0), xb = float(x0 + G.bsx - 1);
+    const float half_bx = 0.5f * float(G.bsx - 1);
+    const float xrel = mu_x - (float(x0) + half_bx);
+    const float padx = 1e-3f + 1e-5f * fabsf(mu_x) + half_bx;
+    const float yrel = mu_y - float(y0);
+    const float dz0 = (float(z0) + R.nmh_yz.y) + R.nml_yz.y;
+    const unsigned full = (1u << G.bsy) - 1u;
     for (int rz = 0; rz < G.bsz; ++rz) {
-        const float dz = (float(z0 + rz) + R.nmh_yz.y) + R.nml_yz.y;
-        const float hw2 = fmaf(-c3 * dz, dz, h0);
-        if (!(hw2 >= 0.0f)) continue;
-        const float sh = sqrt_approx(hw2);
-        const float hwx = fmaf(sh, lam, padx);
-        const float xc = fmaf(kx, dz, mu_x);
-        if (xc + hwx < xa || xc - hwx > xb) continue;
+        const float dz = dz0 + float(rz);
+        const float hw2 = fmaf(nc3 * dz, dz, h0);
+        const float sh = sqrt_approx(fmaxf(hw2, 0.0f));
+        const bool in_x = fabsf(fmaf(kx, dz, xrel)) <= fmaf(sh, lam, padx);
+        const float yc = fmaf(k1, dz, yrel);
         const float hw = sh + pad;
-        const float yc = fmaf(k1, dz, mu_y);
-        int ia = static_cast<int>(ceilf(fmaxf(yc - hw, float(y0) - 1.0f))) - y0;
-        int ib = static_cast<int>(floorf(fminf(yc + hw, float(y0 + G.bsy)))) - y0;
-        ia = max(ia, 0);
-        ib = min(ib, G.bsy - 1);
-        if (ia > ib) continue;
-        mask |= ((2ull << (ib - ia)) - 1ull) << (rz * G.bsy + ia);
+        // rows ceil(yc - hw) .. floor(yc + hw), clamped to the brick; empty when ia > ib
+        const int ia = min(max(__float2int_ru(yc - hw), 0), G.bsy);
+        const int ib = min(max(__float2int_rd(yc + hw), -1), G.bsy - 1);
+        const unsigned bits = (full << ia) & (full >> (G.bsy - 1 - ib));
+        if (hw2 >= 0.0f && in_x) mask |= static_cast<unsigned long long>(bits) << (rz * G.bsy);
     }
     return mask;
 }
