@@ -271,8 +271,12 @@ __global__ void __launch_bounds__(128, 10) k_render_fwd(const int32_t* __restric
 // A z-plane whose section of the truncated ellipsoid misses the brick's x range is skipped.
 // The mask is a conservative superset only (the rows themselves test q <= T), so the plane
 // offsets are taken as dz(z0) + rz and positions relative to the brick, inside the padding.
+// kBY, kBZ: the brick's y and z sizes at compile time (0: taken from G).
+template <int kBY, int kBZ>
 __device__ __forceinline__ unsigned long long brick_row_mask(const Rec& R, const RenderGeo& G,
                                                              int x0, int y0, int z0) {
+    const int bsy = kBY > 0 ? kBY : G.bsy;
+    const int bsz = kBZ > 0 ? kBZ : G.bsz;
     unsigned long long mask = 0;
     const float ipyy = __fdividef(1.0f, R.pyc1.x);
     const float k1 = -0.5f * (R.pc2.x * ipyy);
@@ -291,8 +295,9 @@ __device__ __forceinline__ unsigned long long brick_row_mask(const Rec& R, const
     const float padx = 1e-3f + 1e-5f * fabsf(mu_x) + half_bx;
     const float yrel = mu_y - float(y0);
     const float dz0 = (float(z0) + R.nmh_yz.y) + R.nml_yz.y;
-    const unsigned full = (1u << G.bsy) - 1u;
-    for (int rz = 0; rz < G.bsz; ++rz) {
+    const unsigned full = (1u << bsy) - 1u;
+#pragma unroll (kBZ > 0 ? kBZ : 1)
+    for (int rz = 0; rz < bsz; ++rz) {
         const float dz = dz0 + float(rz);
         const float hw2 = fmaf(nc3 * dz, dz, h0);
         const float sh = sqrt_approx(fmaxf(hw2, 0.0f));
@@ -300,10 +305,10 @@ __device__ __forceinline__ unsigned long long brick_row_mask(const Rec& R, const
         const float yc = fmaf(k1, dz, yrel);
         const float hw = sh + pad;
         // rows ceil(yc - hw) .. floor(yc + hw), clamped to the brick; empty when ia > ib
-        const int ia = min(max(__float2int_ru(yc - hw), 0), G.bsy);
-        const int ib = min(max(__float2int_rd(yc + hw), -1), G.bsy - 1);
-        const unsigned bits = (full << ia) & (full >> (G.bsy - 1 - ib));
-        if (hw2 >= 0.0f && in_x) mask |= static_cast<unsigned long long>(bits) << (rz * G.bsy);
+        const int ia = min(max(__float2int_ru(yc - hw), 0), bsy);
+        const int ib = min(max(__float2int_rd(yc + hw), -1), bsy - 1);
+        const unsigned bits = (full << ia) & (full >> (bsy - 1 - ib));
+        if (hw2 >= 0.0f && in_x) mask |= static_cast<unsigned long long>(bits) << (rz * bsy);
     }
     return mask;
 }
@@ -491,8 +496,11 @@ __global__ void __launch_bounds__(kBwdThreads, 7) k_render_bwd(
             sgid[q] = gid;
             int bxx, by, bz;
             brick_xyz(b_t[h], G, bxx, by, bz);
-            const unsigned long long m = brick_row_mask(load_rec_bwd(rec4 + int64_t(gid) * REC_F4), G,
-                                                        bxx * G.bsx, by * G.bsy, bz * G.bsz);
+            const Rec Rm = load_rec_bwd(rec4 + int64_t(gid) * REC_F4);
+            const int mx0 = bxx * G.bsx, my0 = by * G.bsy, mz0 = bz * G.bsz;
+            const unsigned long long m = (G.bsy == 8 && G.bsz == 8)
+                                             ? brick_row_mask<8, 8>(Rm, G, mx0, my0, mz0)
+                                             : brick_row_mask<0, 0>(Rm, G, mx0, my0, mz0);
             smask[q] = m;
             bucket[h] = 64 - __popcll(static_cast<long long>(m));
             atomicAdd(&hist[bucket[h]], 1);
