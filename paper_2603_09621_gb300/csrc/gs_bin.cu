@@ -10,8 +10,9 @@
 //   k_emit         Gaussian-major pair emission (brick key, owner), staged per block in shared
 //                  memory so the stores are coalesced.
 //   radix passes   stable LSD radix sort of the brick keys, 8 bits per pass: per-tile digit
-//                  histograms, a digit-major scan, and a stable scatter whose in-tile ranks
-//                  come from warp match masks. Stability keeps ascending Gaussian ids inside
+//                  counts (the first pass's added up by k_emit, each later pass's by the
+//                  scatter before it), a digit-major scan, and a stable scatter whose in-tile
+//                  ranks come from warp match masks. Stability keeps ascending Gaussian ids inside
 //                  each brick, so the lists are deterministic.
 //                  The last pass stores pair_brick (key), pair_gmj (Gaussian-major position)
 //                  and pair_gid (owner) directly.
@@ -200,10 +201,15 @@ __global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ pa
                                                     int t_act, float* __restrict__ rec,
                                                     int32_t* __restrict__ brange,
                                                     int32_t* __restrict__ gm_cnt,
-                                                    int32_t* __restrict__ status) {
+                                                    int32_t* __restrict__ status,
+                                                    int32_t* __restrict__ hist_zero,
+                                                    int64_t hist_zero_len) {
     pdl_enter();
     const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g == 0) gm_cnt[N] = 0;  // sentinel: gm_off has N + 1 entries
+    // the digit counts of the first two radix passes are accumulated by k_emit and the first
+    // scatter: start them at zero
+    for (int64_t i = g; i < hist_zero_len; i += int64_t(gridDim.x) * blockDim.x) hist_zero[i] = 0;
     if (g >= N) return;
     const float4* p4 = reinterpret_cast<const float4*>(params + g * 12);
     float4 a0 = p4[0], a1 = p4[1], a2 = p4[2];
@@ -403,19 +409,25 @@ __device__ __forceinline__ int64_t valid_pairs(const int64_t* npairs, int64_t ca
 // range [gm_off[g0], gm_off[g0 + 256]). When that range fits kEmitStage entries, each thread
 // writes its pairs into shared memory and the block then stores the range with consecutive
 // threads on consecutive addresses; otherwise threads write their pairs straight to global
-// memory. Both paths write the same values.
+// memory. Both paths write the same values. The block also adds its pairs to the first radix
+// pass's digit counts (digit-major, hist[d * n_tiles + tile] over tiles of kSortTile
+// Gaussian-major positions), so that pass needs no counting launch of its own: a staged
+// range meets at most kEmitTiles tiles, counted in shared memory first.
 constexpr int kEmitThreads = 256;
 constexpr int kEmitStage = 4096;
+constexpr int kEmitTiles = (kEmitStage + kSortTile - 2) / kSortTile + 1;
 
 __global__ void __launch_bounds__(kEmitThreads) k_emit(const int32_t* __restrict__ brange,
                                                        const int32_t* __restrict__ gm_off, int64_t N,
                                                        int nbx, int nby,
                                                        const int64_t* __restrict__ npairs,
                                                        int64_t capacity, int32_t* __restrict__ keys,
-                                                       int32_t* __restrict__ gm_gid) {
+                                                       int32_t* __restrict__ gm_gid,
+                                                       int32_t* __restrict__ hist, int n_tiles) {
     pdl_enter();
     __shared__ int32_t skey[kEmitStage];
     __shared__ int32_t sgid[kEmitStage];
+    __shared__ int32_t hcnt[kEmitTiles * kRadix];
     if (valid_pairs(npairs, capacity) == 0) return;
     const int64_t g0 = int64_t(blockIdx.x) * kEmitThreads;
     const int64_t g = g0 + threadIdx.x;
@@ -432,44 +444,33 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const int32_t* __restrict
             for (int bz = br[B_LOZ]; bz <= br[B_HIZ]; ++bz)
                 for (int by = br[B_LOY]; by <= br[B_HIY]; ++by)
                     for (int bx = br[B_LOX]; bx <= br[B_HIX]; ++bx) {
-                        kdst[j] = (bz * nby + by) * nbx + bx;
+                        const int key = (bz * nby + by) * nbx + bx;
+                        kdst[j] = key;
                         gdst[j] = static_cast<int32_t>(g);
+                        if (!staged)
+                            atomicAdd(&hist[int64_t(key & (kRadix - 1)) * n_tiles + (base + j) / kSortTile], 1);
                         ++j;
                     }
         }
     }
     if (!staged) return;  // uniform across the block
+    for (int i = threadIdx.x; i < kEmitTiles * kRadix; i += kEmitThreads) hcnt[i] = 0;
     __syncthreads();
+    const int t0 = base / kSortTile;
     for (int i = threadIdx.x; i < total; i += kEmitThreads) {
-        keys[base + i] = skey[i];
+        const int key = skey[i];
+        keys[base + i] = key;
         gm_gid[base + i] = sgid[i];
+        atomicAdd(&hcnt[((base + i) / kSortTile - t0) * kRadix + (key & (kRadix - 1))], 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kEmitTiles * kRadix; i += kEmitThreads) {
+        const int c = hcnt[i];
+        if (c != 0) atomicAdd(&hist[int64_t(i % kRadix) * n_tiles + t0 + i / kRadix], c);
     }
 }
 
 // ============================================================================ radix sort
-
-__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const int32_t* __restrict__ keys,
-                                                            const int64_t* __restrict__ npairs,
-                                                            int64_t capacity, int shift, int n_tiles,
-                                                            int32_t* __restrict__ hist) {
-    pdl_enter();
-    __shared__ int cnt[kRadix];
-    const int64_t P = valid_pairs(npairs, capacity);
-    const int64_t base = int64_t(blockIdx.x) * kSortTile;
-    if (base >= P) {  // a tile past the last pair (the grid is sized by the capacity)
-        for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[int64_t(d) * n_tiles + blockIdx.x] = 0;
-        return;
-    }
-    for (int i = threadIdx.x; i < kRadix; i += blockDim.x) cnt[i] = 0;
-    __syncthreads();
-    for (int i = threadIdx.x; i < kSortTile; i += blockDim.x) {
-        int64_t idx = base + i;
-        if (idx < P) atomicAdd(&cnt[(keys[idx] >> shift) & (kRadix - 1)], 1);
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
-        hist[int64_t(d) * n_tiles + blockIdx.x] = cnt[d];
-}
 
 // Stable scatter of one tile of kSortTile keys. Warp w owns the contiguous sub-tile
 // [w * 384, (w + 1) * 384) and visits it in 12 rounds of 32 consecutive keys (kept in
@@ -481,13 +482,16 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const int32_t* __re
 // then written out in that order: digit d's run goes to [hist_off[d][tile], ...), so
 // consecutive threads store consecutive addresses.
 // kLast: the last pass stores the bins' per-pair arrays directly: brick (the key),
-// Gaussian-major position (the value) and owner (gm_gid of the value).
+// Gaussian-major position (the value) and owner (gm_gid of the value). Every other pass adds
+// each key to the next pass's digit counts at its output position's tile (one atomic per
+// group of equal (tile, digit) in a warp), so no pass after the first needs a counting launch.
 template <bool kFirst, bool kLast>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in,
     int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out,
     const int32_t* __restrict__ hist_off, const int64_t* __restrict__ npairs, int64_t capacity,
-    int shift, int n_tiles, const int32_t* __restrict__ gm_gid, int32_t* __restrict__ pair_gid) {
+    int shift, int n_tiles, const int32_t* __restrict__ gm_gid, int32_t* __restrict__ pair_gid,
+    int32_t* __restrict__ hist_next) {
     pdl_enter();
     constexpr int kWarps = kSortThreads / 32;
     constexpr int kPerWarp = kSortTile / kWarps;
@@ -570,7 +574,15 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
         const int pos = gstart[dk] + (j - dstart[dk]);
         keys_out[pos] = key;
         vals_out[pos] = sval[j];
-        if (kLast) pair_gid[pos] = gm_gid[sval[j]];
+        if (kLast) {
+            pair_gid[pos] = gm_gid[sval[j]];
+        } else {
+            const int tag = ((pos / kSortTile) << kRadixBits) | ((key >> (shift + kRadixBits)) & (kRadix - 1));
+            const unsigned peers = __match_any_sync(__activemask(), tag);
+            if (lane == __ffs(peers) - 1)
+                atomicAdd(&hist_next[int64_t(tag & (kRadix - 1)) * n_tiles + (tag >> kRadixBits)],
+                          __popc(peers));
+        }
     }
 }
 
@@ -739,7 +751,7 @@ gs_status bin_bricks_impl(const float* params, const gs_grid* grid, const gs_con
         const unsigned gb = static_cast<unsigned>((N + 255) / 256);
         launch_k(k_preprocess, dim3(gb), dim3(256), 0, st, params, N, G, cfg->trunc_sigma,
             cfg->signal_mode, cfg->a_act, cfg->t_act, bins->rec, bins->brange, ws.gm_cnt,
-            bins->d_status);
+            bins->d_status, ws.hist, 2 * (int64_t(kRadix) * ws.n_tiles + 1));
         gs_status s = last_launch_status();
         if (s != GS_OK) return s;
         // gm_off = exclusive scan of counts (N + 1 entries; gm_cnt[N] = 0 sentinel); the scan's
@@ -759,7 +771,7 @@ gs_status bin_bricks_impl(const float* params, const gs_grid* grid, const gs_con
     if (N > 0) {
         launch_k(k_emit, dim3(static_cast<unsigned>((N + kEmitThreads - 1) / kEmitThreads)),
             dim3(kEmitThreads), 0, st, bins->brange, bins->gm_off, N, b.nbx, b.nby, bins->d_npairs,
-            cap, ws.keys0, ws.gm_gid);
+            cap, ws.keys0, ws.gm_gid, ws.hist, ws.n_tiles);
         s = last_launch_status();
         if (s != GS_OK) return s;
     }
@@ -778,24 +790,29 @@ gs_status bin_bricks_impl(const float* params, const gs_grid* grid, const gs_con
     int32_t* vout = ws.vals1;
     const int nt = ws.n_tiles;
     const int64_t hist_len = int64_t(kRadix) * nt;
+    // digit counts: pass 0's from k_emit, pass p + 1's from pass p's scatter, in two buffers
+    // that k_preprocess zeroed; a third pass reuses the first buffer, zeroed again here
+    int32_t* hbuf[2] = {ws.hist, ws.hist1};
     for (int pass = 0; pass < passes; ++pass) {
         const int shift = pass * kRadixBits;
-        launch_k(k_radix_hist, dim3(nt), dim3(kSortThreads), 0, st, kin, bins->d_npairs, cap, shift,
-            nt, ws.hist);
-        s = last_launch_status();
-        if (s != GS_OK) return s;
-        s = exclusive_scan_i32(ws.hist, ws.hist, hist_len, nullptr, ws.scan_tmp, ws.scan_tmp_len - 1, st);
+        int32_t* hcur = hbuf[pass & 1];
+        int32_t* hnext = hbuf[(pass + 1) & 1];
+        if (pass >= 1 && pass + 1 < passes &&
+            cudaMemsetAsync(hnext, 0, sizeof(int32_t) * hist_len, st) != cudaSuccess)
+            return GS_ERR_CUDA;
+        s = exclusive_scan_i32(hcur, hcur, hist_len, nullptr, ws.scan_tmp, ws.scan_tmp_len - 1, st);
         if (s != GS_OK) return s;
         // the last pass writes the bins' pair arrays (brick, Gaussian-major position, owner)
         const bool last = pass == passes - 1;
         int32_t* ko = last ? bins->pair_brick : kout;
         int32_t* vo = last ? bins->pair_gmj : vout;
         using ScatterFn = void (*)(const int32_t*, const int32_t*, int32_t*, int32_t*, const int32_t*,
-                                   const int64_t*, int64_t, int, int, const int32_t*, int32_t*);
+                                   const int64_t*, int64_t, int, int, const int32_t*, int32_t*,
+                                   int32_t*);
         ScatterFn kern = pass == 0 ? (last ? k_radix_scatter<true, true> : k_radix_scatter<true, false>)
                                    : (last ? k_radix_scatter<false, true> : k_radix_scatter<false, false>);
-        launch_k(kern, dim3(nt), dim3(kSortThreads), 0, st, kin, vin, ko, vo, ws.hist,
-            bins->d_npairs, cap, shift, nt, ws.gm_gid, bins->pair_gid);
+        launch_k(kern, dim3(nt), dim3(kSortThreads), 0, st, kin, vin, ko, vo, hcur,
+            bins->d_npairs, cap, shift, nt, ws.gm_gid, bins->pair_gid, hnext);
         s = last_launch_status();
         if (s != GS_OK) return s;
         int32_t* t = kin; kin = kout; kout = t;

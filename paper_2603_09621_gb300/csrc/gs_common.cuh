@@ -91,7 +91,8 @@ struct Workspace {
     int32_t* vals1;
     int32_t* gm_gid;
     int32_t* gm_cnt;
-    int32_t* hist;
+    int32_t* hist;           // digit counts / offsets of the radix passes: two buffers
+    int32_t* hist1;          // of hist_len + 1, contiguous (hist1 = hist + hist_len + 1)
     long long* scan_tmp;     // block sums of the multi-level scan
     float* part;             // [capacity, 12] per-pair partial gradients (deterministic mode)
     float* gacc;             // [n_gauss, 12] render-space gradient per Gaussian
@@ -137,7 +138,8 @@ inline bool carve_workspace(void* base, int64_t n_gauss, int64_t capacity, int32
     ws->vals1 = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * cap));
     ws->gm_gid = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * cap));
     ws->gm_cnt = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * (n + 1)));
-    ws->hist = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * (hist_len + 1)));
+    ws->hist = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * 2 * (hist_len + 1)));
+    ws->hist1 = ws->hist ? ws->hist + hist_len + 1 : nullptr;
     ws->scan_tmp = reinterpret_cast<long long*>(take(sizeof(long long) * ws->scan_tmp_len));
     ws->part = reinterpret_cast<float*>(
         take(deterministic ? sizeof(float) * GRAD_FLOATS * cap : 256));
