@@ -473,9 +473,10 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const int32_t* __restrict
 // ============================================================================ radix sort
 
 // Stable scatter of one tile of kSortTile keys. Warp w owns the contiguous sub-tile
-// [w * 384, (w + 1) * 384) and visits it in 12 rounds of 32 consecutive keys (kept in
-// registers; 3,072-key tiles measured faster than 4,096 at the fitting size, with 4 blocks
-// per SM and shorter tail waves). Pass 1 counts each warp's digits. A block-wide prefix then gives, per digit,
+// [w * 256, (w + 1) * 256) and visits it in 8 rounds of 32 consecutive keys (kept in
+// registers; with the digit counts accumulated by the launch before, 2,048-key tiles measured
+// faster than 1,024, 1,536, 2,560 and 3,072 at the fitting size). Pass 1 counts each warp's
+// digits. A block-wide prefix then gives, per digit,
 // the tile-local start of its run and each warp's start inside it. Pass 2 places every key in
 // shared memory at its warp's start + its rank among equal digits in lower lanes (warp match
 // masks), so the tile sits in shared memory sorted by digit, ties in tile order. The tile is

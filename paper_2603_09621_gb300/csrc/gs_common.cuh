@@ -70,8 +70,8 @@ enum BrangeField : int { B_LOX = 0, B_LOY, B_LOZ, B_HIX, B_HIY, B_HIZ, B_CNT, B_
 
 // ------------------------------------------------------------------ sort constants
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 12;
-constexpr int kSortTile = kSortThreads * kSortItems;  // 3072 keys per tile
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 2048 keys per tile
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 

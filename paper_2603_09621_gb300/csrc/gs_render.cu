@@ -40,7 +40,7 @@
 
 namespace gs {
 
-constexpr int kFwdChunk = 192;   // Gaussians staged per forward round
+constexpr int kFwdChunk = 224;   // Gaussians staged per forward round
 constexpr int kBwdThreads = 128;
 constexpr int kBwdPairs = 256;        // pairs per adjoint block, taken by warps 32 at a time
 constexpr int kBwdStage = 4;          // bricks of per-voxel factors staged per adjoint block
