@@ -224,16 +224,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": n}
 
 
-def traffic_for(kernel: str):
+def traffic_for(kernel: str, brick=(8, 8, 8)):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when the
-    kernel source changed since the counters were taken."""
+    kernel source changed since the counters were taken or the brick shape differs from the
+    captured one."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         t = json.load(f)
     ent = t.get(kernel)
-    if not ent:
+    if not ent or tuple(ent.get("brick", (8, 8, 8))) != tuple(brick):
         return None
     src = os.path.join(ROOT, "paper_2603_09621_gb300", "csrc", ent["source"])
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -485,7 +486,7 @@ def run_ours(args, world, rank, local):
     achieved = n_eff_step / t_k / 1e9
     roofline = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak_gpairs,
                 "unit": "Gpair/s", "frac": achieved / peak_gpairs,
-                "traffic": traffic_for(kern),
+                "traffic": traffic_for(kern, cfg.brick),
                 "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_CLK_SM} FP32 lanes/clk / "
                               f"{MIN_FP32_PER_PAIR[kern]} FP32 operations per effective pair "
                               f"x {f_mhz:.0f} MHz (SM max clock, {peak_src}); the SFU ceiling "

@@ -411,11 +411,12 @@ __device__ __forceinline__ int64_t valid_pairs(const int64_t* npairs, int64_t ca
 // threads on consecutive addresses; otherwise threads write their pairs straight to global
 // memory. Both paths write the same values. The block also adds its pairs to the first radix
 // pass's digit counts (digit-major, hist[d * n_tiles + tile] over tiles of kSortTile
-// Gaussian-major positions), so that pass needs no counting launch of its own: a staged
-// range meets at most kEmitTiles tiles, counted in shared memory first.
+// Gaussian-major positions), so that pass needs no counting launch of its own: counted in
+// shared memory when the range meets at most kEmitTiles tiles (then one global atomic per
+// nonzero count), else one global atomic per pair.
 constexpr int kEmitThreads = 256;
 constexpr int kEmitStage = 4096;
-constexpr int kEmitTiles = (kEmitStage + kSortTile - 2) / kSortTile + 1;
+constexpr int kEmitTiles = 4;
 
 __global__ void __launch_bounds__(kEmitThreads) k_emit(const int32_t* __restrict__ brange,
                                                        const int32_t* __restrict__ gm_off, int64_t N,
@@ -435,6 +436,10 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const int32_t* __restrict
     const int base = gm_off[g0];
     const int total = gm_off[gl] - base;
     const bool staged = total <= kEmitStage;
+    const int t0 = base / kSortTile;
+    const bool local = total == 0 || (base + total - 1) / kSortTile - t0 < kEmitTiles;  // uniform
+    for (int i = threadIdx.x; i < kEmitTiles * kRadix; i += kEmitThreads) hcnt[i] = 0;
+    __syncthreads();
     int32_t* kdst = staged ? skey : keys + base;
     int32_t* gdst = staged ? sgid : gm_gid + base;
     if (g < N) {
@@ -447,26 +452,32 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const int32_t* __restrict
                         const int key = (bz * nby + by) * nbx + bx;
                         kdst[j] = key;
                         gdst[j] = static_cast<int32_t>(g);
-                        if (!staged)
-                            atomicAdd(&hist[int64_t(key & (kRadix - 1)) * n_tiles + (base + j) / kSortTile], 1);
+                        if (!staged) {  // (staged ranges are counted as they are stored)
+                            const int t = (base + j) / kSortTile;
+                            if (local)
+                                atomicAdd(&hcnt[(t - t0) * kRadix + (key & (kRadix - 1))], 1);
+                            else
+                                atomicAdd(&hist[int64_t(key & (kRadix - 1)) * n_tiles + t], 1);
+                        }
                         ++j;
                     }
         }
     }
-    if (!staged) return;  // uniform across the block
-    for (int i = threadIdx.x; i < kEmitTiles * kRadix; i += kEmitThreads) hcnt[i] = 0;
     __syncthreads();
-    const int t0 = base / kSortTile;
-    for (int i = threadIdx.x; i < total; i += kEmitThreads) {
-        const int key = skey[i];
-        keys[base + i] = key;
-        gm_gid[base + i] = sgid[i];
-        atomicAdd(&hcnt[((base + i) / kSortTile - t0) * kRadix + (key & (kRadix - 1))], 1);
+    if (staged) {
+        for (int i = threadIdx.x; i < total; i += kEmitThreads) {
+            const int key = skey[i];
+            keys[base + i] = key;
+            gm_gid[base + i] = sgid[i];
+            atomicAdd(&hcnt[((base + i) / kSortTile - t0) * kRadix + (key & (kRadix - 1))], 1);
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kEmitTiles * kRadix; i += kEmitThreads) {
-        const int c = hcnt[i];
-        if (c != 0) atomicAdd(&hist[int64_t(i % kRadix) * n_tiles + t0 + i / kRadix], c);
+    if (local) {
+        for (int i = threadIdx.x; i < kEmitTiles * kRadix; i += kEmitThreads) {
+            const int c = hcnt[i];
+            if (c != 0) atomicAdd(&hist[int64_t(i % kRadix) * n_tiles + t0 + i / kRadix], c);
+        }
     }
 }
 
