@@ -486,7 +486,7 @@ def run_ours(args, world, rank, local):
     achieved = n_eff_step / t_k / 1e9
     roofline = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak_gpairs,
                 "unit": "Gpair/s", "frac": achieved / peak_gpairs,
-                "traffic": traffic_for(kern, cfg.brick),
+                "traffic": None if tri else traffic_for(kern, cfg.brick),
                 "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_CLK_SM} FP32 lanes/clk / "
                               f"{MIN_FP32_PER_PAIR[kern]} FP32 operations per effective pair "
                               f"x {f_mhz:.0f} MHz (SM max clock, {peak_src}); the SFU ceiling "
