@@ -40,7 +40,8 @@
 
 namespace gs {
 
-constexpr int kFwdChunk = 224;   // Gaussians staged per forward round
+constexpr int kFwdChunkPerFoot = 28;  // Gaussians staged per forward round and 4^3 footprint
+                                      // (in steps of a factor 2: 56, 112 or 224 records)
 constexpr int kBwdThreads = 128;
 constexpr int kBwdPairs = 256;        // pairs per adjoint block, taken by warps 32 at a time
 constexpr int kBwdStage = 4;          // bricks of per-voxel factors staged per adjoint block
@@ -161,14 +162,14 @@ __device__ __forceinline__ bool foot_hit(const float4* s, float cx, float cy, fl
 
 // ------------------------------------------------------------------------ forward
 
-template <bool kStats>
+template <bool kStats, int kChunk>
 __global__ void __launch_bounds__(128, 10) k_render_fwd(const int32_t* __restrict__ brick_off,
                                                     const int32_t* __restrict__ pair_gid,
                                                     const float4* __restrict__ rec4, RenderGeo G,
                                                     float* __restrict__ I, float* __restrict__ W,
                                                     unsigned long long* __restrict__ stats) {
     pdl_enter();
-    __shared__ float4 srec[kFwdChunk][REC_F4];
+    __shared__ float4 srec[kChunk][REC_F4];
     const int tid = threadIdx.x, lane = tid & 31;
     const int nthreads = blockDim.x;
     const int b = blockIdx.x;
@@ -191,8 +192,8 @@ __global__ void __launch_bounds__(128, 10) k_render_fwd(const int32_t* __restric
     for (int xi = 0; xi < 4; ++xi) SW[xi] = f2(0.f, 0.f);
     unsigned long long n_eff = 0, n_eval = 0;
     const int start = brick_off[b], end = brick_off[b + 1];
-    for (int c0 = start; c0 < end; c0 += kFwdChunk) {
-        const int cnt = min(kFwdChunk, end - c0);
+    for (int c0 = start; c0 < end; c0 += kChunk) {
+        const int cnt = min(kChunk, end - c0);
         if (c0 != start) __syncthreads();  // the previous chunk's records are no longer read
         for (int i = tid; i < cnt * REC_F4; i += nthreads) {
             const int k = i / REC_F4, part = i - k * REC_F4;
@@ -688,14 +689,21 @@ RenderGeo make_geo(const gs_grid* grid, const gs_config* cfg) {
 gs_status render_fwd_impl(const gs_bins* bins, const gs_grid* grid, const gs_config* cfg,
                           float* I, float* W, unsigned long long* stats, cudaStream_t st) {
     RenderGeo G = make_geo(grid, cfg);
-    const int threads = 32 * ((G.fx * G.fy * G.fz + 1) / 2);  // a half-warp per footprint
+    const int n_foot = G.fx * G.fy * G.fz;
+    const int threads = 32 * ((n_foot + 1) / 2);  // a half-warp per footprint
+    // records staged per round about in proportion to the footprints (the lists of smaller
+    // bricks are shorter), so that smaller bricks keep more blocks resident
     const float4* rec4 = reinterpret_cast<const float4*>(bins->rec);
-    if (stats)
-        launch_k(k_render_fwd<true>, dim3(bins->n_bricks), dim3(threads), 0, st, bins->brick_off,
-            bins->pair_gid, rec4, G, I, W, stats);
+    auto go = [&](auto kernel) {
+        launch_k(kernel, dim3(bins->n_bricks), dim3(threads), 0, st, bins->brick_off, bins->pair_gid,
+            rec4, G, I, W, stats);
+    };
+    if (n_foot >= 6)
+        stats ? go(k_render_fwd<true, 8 * kFwdChunkPerFoot>) : go(k_render_fwd<false, 8 * kFwdChunkPerFoot>);
+    else if (n_foot >= 3)
+        stats ? go(k_render_fwd<true, 4 * kFwdChunkPerFoot>) : go(k_render_fwd<false, 4 * kFwdChunkPerFoot>);
     else
-        launch_k(k_render_fwd<false>, dim3(bins->n_bricks), dim3(threads), 0, st, bins->brick_off,
-            bins->pair_gid, rec4, G, I, W, nullptr);
+        stats ? go(k_render_fwd<true, 2 * kFwdChunkPerFoot>) : go(k_render_fwd<false, 2 * kFwdChunkPerFoot>);
     return last_launch_status();
 }
 
