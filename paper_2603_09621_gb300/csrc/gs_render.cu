@@ -272,7 +272,8 @@ __global__ void __launch_bounds__(128, 10) k_render_fwd(const int32_t* __restric
 // A z-plane whose section of the truncated ellipsoid misses the brick's x range is skipped.
 // The mask is a conservative superset only (the rows themselves test q <= T), so the plane
 // offsets are taken as dz(z0) + rz and positions relative to the brick, inside the padding.
-// kBY, kBZ: the brick's y and z sizes at compile time (0: taken from G).
+// kBY, kBZ: the brick's y and z sizes at compile time (0: taken from G); the fitting
+// workload's 8^3 bricks and the paper's 8 x 8 x 4 ones have their own unrolled copies.
 template <int kBY, int kBZ>
 __device__ __forceinline__ unsigned long long brick_row_mask(const Rec& R, const RenderGeo& G,
                                                              int x0, int y0, int z0) {
@@ -501,7 +502,9 @@ __global__ void __launch_bounds__(kBwdThreads, 7) k_render_bwd(
             const int mx0 = bxx * G.bsx, my0 = by * G.bsy, mz0 = bz * G.bsz;
             const unsigned long long m = (G.bsy == 8 && G.bsz == 8)
                                              ? brick_row_mask<8, 8>(Rm, G, mx0, my0, mz0)
-                                             : brick_row_mask<0, 0>(Rm, G, mx0, my0, mz0);
+                                             : (G.bsy == 8 && G.bsz == 4)
+                                                   ? brick_row_mask<8, 4>(Rm, G, mx0, my0, mz0)
+                                                   : brick_row_mask<0, 0>(Rm, G, mx0, my0, mz0);
             smask[q] = m;
             bucket[h] = 64 - __popcll(static_cast<long long>(m));
             atomicAdd(&hist[bucket[h]], 1);
