@@ -102,9 +102,11 @@ def test_grad_modes_activations_bricks(mode, a_act, t_act, brick):
     check_grad(got, oracle_box(p, og, dI, cfg))
 
 
-def test_grad_fit_workload_crop():
+@pytest.mark.parametrize("brick", [(8, 8, 8), (8, 8, 4)])
+def test_grad_fit_workload_crop(brick):
     """Fitting workload (256 x 256 x 128, 500k Gaussians): dL/dI random on a 24^3 crop and
-    zero elsewhere; every Gaussian's gradient compared with the oracle's."""
+    zero elsewhere; every Gaussian's gradient compared with the oracle's, with the fitting
+    workload's bricks and the paper's."""
     import oracle
     w = phantom_fit()
     og = w["grid"]
@@ -115,7 +117,7 @@ def test_grad_fit_workload_crop():
     box = oracle_box(w["params0"], og, dIc, cfg, crop=crop)
     dI = np.zeros((og.nz, og.ny, og.nx), np.float32)
     dI[z0:z0 + 24, y0:y0 + 24, x0:x0 + 24] = dIc
-    got = gpu_grad(w["params0"], og, dI, t_act=1)
+    got = gpu_grad(w["params0"], og, dI, t_act=1, brick=brick)
     touched = (np.abs(box["lo"]).sum(1) + np.abs(box["hi"]).sum(1)) > 0
     assert touched.sum() > 1000
     assert np.all(got[~touched] == 0)

@@ -95,6 +95,16 @@ def test_forward_brick_shape_invariance(brick):
     assert np.array_equal(a["I"], b["I"]) and np.array_equal(a["W"], b["W"])
 
 
+def test_forward_fit_workload_brick_invariance():
+    """At the fitting workload's size (256 x 256 x 128, 500k Gaussians) the paper's 8 x 8 x 4
+    bricks (112 records staged per round, the 8-row, 4-plane row-mask copy) give the 8^3
+    bricks' volumes bit for bit."""
+    w = phantom_fit()
+    a = gpu_render(w["params0"], w["grid"], t_act=1)
+    b = gpu_render(w["params0"], w["grid"], brick=(8, 8, 4), t_act=1)
+    assert np.array_equal(a["I"], b["I"]) and np.array_equal(a["W"], b["W"])
+
+
 def test_forward_deterministic():
     params, og = c1()
     a = gpu_render(params, og)
