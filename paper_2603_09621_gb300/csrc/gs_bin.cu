@@ -390,7 +390,13 @@ __global__ void __launch_bounds__(256, 6) k_preprocess(const float* __restrict__
         ext[k] = 1.01f * trunc_sigma * sqrtf(sig) * G.ih[k] + 1.5f + 1e-3f;
     }
     r4[3] = make_float4(ext[0], rho4, ext[1], ext[2]);
-    r4[4] = make_float4(v * r, r, v, 0.0f);
+    // lower bound of q per squared voxel distance from the mean: (log2 e / 2) h_min^2 / s_max^2
+    // bounds the smallest eigenvalue of the voxel-space form (less 1e-3 for rounding), so
+    // a footprint whose voxel box lies farther than sqrt(Tcull / lam) from the mean is missed
+    const float smax = fmaxf(s[0], fmaxf(s[1], s[2]));
+    const float hmin = fminf(G.h[0], fminf(G.h[1], G.h[2]));
+    const float lam = kHalfLog2e * (1.0f - 1e-3f) * (hmin / smax) * (hmin / smax);
+    r4[4] = make_float4(v * r, r, v, lam);
 }
 
 // ============================================================================ capacity / emit

@@ -84,6 +84,7 @@ struct Rec {
     float2 pc2;              // (P2yz, c2): the dz coefficients of the row terms
     float2 pyc1;             // (Pyy, c1): their dy coefficients
     float pzz, sa, rho4, vr, r, v;
+    float lam;               // q per squared voxel distance from the mean, at the least (culling)
     float ex, ey, ez;        // footprint-centre box half-extents (culling)
 };
 
@@ -95,7 +96,7 @@ __device__ __forceinline__ Rec load_rec(const float4* s) {
     R.pyc1 = make_float2(c.x, c.y); R.pzz = c.z; R.sa = c.w;
     R.rho4 = d.y;
     R.ex = d.x; R.ey = d.z; R.ez = d.w;
-    R.vr = e.x; R.r = e.y; R.v = e.z;
+    R.vr = e.x; R.r = e.y; R.v = e.z; R.lam = e.w;
     return R;
 }
 
@@ -110,7 +111,7 @@ __device__ __forceinline__ Rec load_rec_bwd(const float4* s) {
     R.pyc1 = make_float2(c.x, c.y); R.pzz = c.z; R.sa = c.w;
     R.rho4 = 0.f;
     R.ex = R.ey = R.ez = 0.f;
-    R.vr = e.x; R.r = e.y; R.v = e.z;
+    R.vr = e.x; R.r = e.y; R.v = e.z; R.lam = 0.f;
     return R;
 }
 
@@ -147,9 +148,11 @@ __device__ __forceinline__ float q_of_k(const Rec& R, float tq0, int k, float S)
 }
 
 // Footprint cull: may the Gaussian reach a voxel centre within 3/2 of (cx, cy, cz) per axis?
-// Two conservative tests: the whitened triangle inequality, and the footprint centre's offset
-// from the mean against the truncated ellipsoid's box widened by the footprint's half-width.
-// (An approximate square root suffices: Tcull carries a 1 % margin over T.)
+// Three conservative tests: the whitened triangle inequality; the footprint centre's offset
+// from the mean against the truncated ellipsoid's box widened by the footprint's half-width;
+// and q's lower bound lam |p - mu|^2 at the footprint's voxel box's nearest point (exact for
+// isotropic Gaussians, it drops footprints that only a corner of the ellipsoid grazes between
+// voxel centres). (An approximate square root suffices: Tcull carries a 1 % margin over T.)
 __device__ __forceinline__ bool foot_hit(const float4* s, float cx, float cy, float cz,
                                          float sqrtTcull) {
     const Rec R = load_rec(s);
@@ -158,8 +161,11 @@ __device__ __forceinline__ bool foot_hit(const float4* s, float cx, float cy, fl
     const float ux = (cx + R.nmhx) + R.nmlx;
     const float tq = R.sa * (ux - dxs);
     const float qc = fmaf(tq, tq, S);
+    const float ax = fmaxf(fabsf(ux) - 1.5f, 0.0f), ay = fmaxf(fabsf(dy) - 1.5f, 0.0f);
+    const float az = fmaxf(fabsf(dz) - 1.5f, 0.0f);
+    const float dist2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
     return (sqrt_approx(fmaxf(qc, 0.0f)) - R.rho4 <= sqrtTcull) & (fabsf(ux) <= R.ex) &
-           (fabsf(dy) <= R.ey) & (fabsf(dz) <= R.ez);
+           (fabsf(dy) <= R.ey) & (fabsf(dz) <= R.ez) & (R.lam * dist2 <= sqrtTcull * sqrtTcull);
 }
 
 // ------------------------------------------------------------------------ forward
