@@ -12,11 +12,12 @@
 // x-row of four voxels. The block stages the brick's list in rounds of about 28 records per
 // footprint (224 for an 8^3 brick), so most lists take one round and smaller bricks, with
 // shorter lists, keep more blocks resident. A half-warp tests 16 staged Gaussians against
-// its footprint with one ballot and two conservative tests: the triangle inequality in
+// its footprint with one ballot and three conservative tests: the triangle inequality in
 // whitened space (|M (p - mu)| >= |M (c - mu)| - rho4, with rho4 the whitened radius of the
 // footprint around its centre c, so a footprint whose centre is farther than sqrt(T) + rho4
-// is missed) and the truncated ellipsoid's bounding box widened by 3/2 along each axis; a
-// margin absorbs FP32 rounding. It evaluates the hits in ascending Gaussian id, accumulating S and W in registers
+// is missed), the truncated ellipsoid's bounding box widened by 3/2 along each axis, and q's
+// lower bound from the smallest eigenvalue at the footprint's nearest point; a margin
+// absorbs FP32 rounding. It evaluates the hits in ascending Gaussian id, accumulating S and W in registers
 // (deterministic; one packed FFMA2 updates a voxel's (S, W) with (v r, r) g).
 // Adjoint: one thread per (brick, Gaussian) pair evaluates the brick rows the Gaussian
 // reaches (the row shadow, per z-row a quadratic in dy; z-planes whose section of the
