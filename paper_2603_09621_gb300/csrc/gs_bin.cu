@@ -3,7 +3,8 @@
 //
 // Pipeline of gs_bin_bricks (all asynchronous on one stream):
 //   k_preprocess   one thread per Gaussian: validity, FP32 brick range (fixed operation order,
-//                  bit-exact against the oracle's binning specification), render record.
+//                  bit-exact against the oracle's binning specification), render record; it
+//                  also clears the radix passes' two digit-count buffers.
 //   scan           exclusive scan of per-Gaussian pair counts -> gm_off; its last thread stores
 //                  the total as d_npairs and flags GS_STATUS_CAPACITY when it exceeds the
 //                  bins' capacity.
