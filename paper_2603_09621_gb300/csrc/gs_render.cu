@@ -601,14 +601,25 @@ __global__ void __launch_bounds__(kBwdThreads, 7) k_render_bwd(
         if (rank >= nvalid) continue;
         const int lt = sorder[rank];
         const int64_t i = base + lt;
+        const unsigned long long m = smask[lt];
+        if (m == 0ull) {
+            // a pair whose Gaussian reaches none of the brick's rows (the count-sorted list puts
+            // them in the last chunks): its partial is zero, with no record or brick to load
+            if (kDet) {
+                float4* dst = reinterpret_cast<float4*>(part + int64_t(pair_gmj[i]) * GRAD_FLOATS);
+                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                dst[0] = z4;
+                dst[1] = z4;
+                dst[2] = z4;
+            }
+            continue;
+        }
         const int b = pair_brick[i];
         int bx, by, bz;
         brick_xyz(b, G, bx, by, bz);
         const int x0 = bx * BX, y0 = by * G.bsy, z0 = bz * G.bsz;
         const int stage = sstage[lt];
         const Rec R = load_rec_bwd(rec4 + int64_t(sgid[lt]) * REC_F4);
-        const unsigned long long m = smask[lt];
-        const bool any = m != 0ull;
         AdjAcc A;
         A.h = A.hy = A.hz = A.p1 = A.p1y = A.p1z = A.pq = A.ag = f2(0.f, 0.f);
         A.yy = A.zz = A.yz = 0.f;
@@ -639,7 +650,7 @@ __global__ void __launch_bounds__(kBwdThreads, 7) k_render_bwd(
             dst[0] = make_float4(m1x, m1y, m1z, m2xx);
             dst[1] = make_float4(m2yy, m2zz, m2xy, m2xz);
             dst[2] = make_float4(m2yz, dv, dr, 0.f);
-        } else if (any) {
+        } else {
             float* dst = gacc + int64_t(sgid[lt]) * GRAD_FLOATS;
             const float vals[11] = {m1x, m1y, m1z, m2xx, m2yy, m2zz, m2xy, m2xz, m2yz, dv, dr};
 #pragma unroll
