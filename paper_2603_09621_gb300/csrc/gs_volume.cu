@@ -421,10 +421,15 @@ extern "C" gs_status gs_fit_step_host(gs_fit_state* st, const float* h_params,
     FitRun run;
     gs_status s = fit_prepare(st, stream, &run);
     if (s != GS_OK) return s;
+    // The parameters go first, alone on the link, since binning waits for them; the LR target
+    // follows on a side stream while the step bins and renders, and the step waits for it
+    // only before the LR model. The side stream starts after everything issued on `stream`
+    // so far (the parameter copy included), so an earlier step still reading lr_target is
+    // not overwritten.
+    if (h_params && cudaMemcpyAsync(st->params, h_params, sizeof(float) * 12 * st->n_gauss,
+                                    cudaMemcpyHostToDevice, cs) != cudaSuccess)
+        return GS_ERR_CUDA;
     if (h_lr_target) {
-        // the LR target goes over on a side stream while the step bins and renders; the step
-        // waits for it before the LR model. The side stream first waits for everything issued
-        // on `stream` so far, so an earlier step still reading lr_target is not overwritten.
         HostCopyRes* r = nullptr;
         s = host_copy_res(&r);
         if (s != GS_OK) return s;
@@ -436,9 +441,6 @@ extern "C" gs_status gs_fit_step_host(gs_fit_state* st, const float* h_params,
             return GS_ERR_CUDA;
         run.lr_ready = r->lr_done;
     }
-    if (h_params && cudaMemcpyAsync(st->params, h_params, sizeof(float) * 12 * st->n_gauss,
-                                    cudaMemcpyHostToDevice, cs) != cudaSuccess)
-        return GS_ERR_CUDA;
     s = fit_front(run, 0);
     if (s != GS_OK) return s;
     s = launch_chain_adam(st->params, st->grad, st->m, st->v, run.w.part, run.w.gacc, &st->bins,
