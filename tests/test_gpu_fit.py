@@ -189,6 +189,39 @@ def test_fit_step_full_size_equals_composed_entry_points(lr_model):
     assert int(st.d_step) == int(d_step) == 1
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_fit_steps_host_equal_device_steps(pinned):
+    """Three steps through gs_fit_step_host, from page-locked or ordinary host memory, each
+    uploading the step's parameters and LR target, equal three device steps that start from
+    the same uploads (the side-stream copy of the LR target must not overtake the step before
+    it), bit for bit, with every step's loss read back."""
+    import torch
+    gs = _gs()
+    w = small_fit()
+    og = w["grid"]
+    g = gs.Grid(og.nx, og.ny, og.nz)
+    a = gs.FitState(to_dev(w["params0"]), to_dev(w["lr"]), g, w["s"], gs.Config(t_act=1))
+    b = gs.FitState(torch.zeros_like(a.params), torch.zeros_like(a.lr_target), g, w["s"],
+                    gs.Config(t_act=1), capacity=a.capacity)
+    rng = np.random.default_rng(11)
+    for k in range(3):
+        # each step gets its own inputs: perturbed parameters and LR target
+        p = (w["params0"] + rng.normal(0.0, 1e-3, w["params0"].shape)).astype(np.float32)
+        lr = (w["lr"] + rng.normal(0.0, 1e-2, w["lr"].shape)).astype(np.float32)
+        h_params, h_lr = torch.as_tensor(p).contiguous(), torch.as_tensor(lr).contiguous()
+        h_loss = torch.full((), -1.0)
+        if pinned:
+            h_params, h_lr, h_loss = h_params.pin_memory(), h_lr.pin_memory(), h_loss.pin_memory()
+        a.params.copy_(to_dev(p))
+        a.lr_target.copy_(to_dev(lr))
+        a.step()
+        b.step_host(h_params, h_lr, h_loss)
+        torch.cuda.synchronize()
+        assert torch.equal(a.params, b.params) and torch.equal(a.grad, b.grad)
+        assert torch.equal(a.m, b.m) and torch.equal(a.v, b.v)
+        assert float(h_loss) == float(a.d_loss)
+
+
 def test_fit_step_host_equals_device_step():
     """gs_fit_step_host (inputs copied from page-locked host memory inside the call, loss copied
     back) gives the device step's result bit for bit."""
