@@ -204,9 +204,10 @@ __global__ void __launch_bounds__(128, 10) k_render_fwd(const int32_t* __restric
     for (int c0 = start; c0 < end; c0 += kChunk) {
         const int cnt = min(kChunk, end - c0);
         if (c0 != start) __syncthreads();  // the previous chunk's records are no longer read
-        for (int i = tid; i < cnt * REC_F4; i += nthreads) {
-            const int k = i / REC_F4, part = i - k * REC_F4;
-            srec[k][part] = rec4[int64_t(pair_gid[c0 + k]) * REC_F4 + part];
+        for (int k = tid; k < cnt; k += nthreads) {  // a thread stages one record
+            const float4* src = rec4 + int64_t(pair_gid[c0 + k]) * REC_F4;
+#pragma unroll
+            for (int part = 0; part < REC_F4; ++part) srec[k][part] = src[part];
         }
         __syncthreads();
         for (int k0 = 0; k0 < cnt; k0 += 16) {
