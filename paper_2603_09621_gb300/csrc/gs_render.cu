@@ -26,8 +26,9 @@
 // brick-major pairs (one to three bricks), computes their row masks and counting-sorts them
 // by number of rows in shared memory; its four warps then take 32-pair chunks of the sorted
 // list, longest first, from a shared counter, so the lanes of a warp run pairs of equal length
-// and a warp that drew short pairs moves on to the next chunk (72 registers without spills,
-// 7 blocks per SM). The per-voxel factors (alpha, alpha I'), alpha = dL/dI / max(W, eps), are
+// and a warp that drew short pairs moves on to the next chunk (64 registers without spills,
+// 8 blocks per SM, 7 for 16-voxel-wide bricks; the y and z cross moments are summed over both
+// FP32x2 elements per row to keep the accumulators that small). The per-voxel factors (alpha, alpha I'), alpha = dL/dI / max(W, eps), are
 // precomputed into one float2 volume; a block copies those of its first four bricks into
 // shared memory (zero outside the grid), so rows read them without range tests; a 16-byte pad
 // after every 128 bytes and a 32-byte offset between staged bricks spread the rows that the
@@ -345,10 +346,11 @@ __global__ void __launch_bounds__(256) k_bwd_prep(const float* __restrict__ Iv,
 // A brick row of bx voxels is taken as bx/2 voxel pairs (p, p + bx/2); element e of a float2
 // holds the sums over the voxels p + e bx/2 (offset u = uc_e + p from the mean along x).
 struct AdjAcc {
-    float2 h, hy, hz;     // sum h, sum h dy, sum h dz
-    float2 p1, p1y, p1z;  // sum h p, sum h p dy, sum h p dz
+    float2 h, p1;         // sum h, sum h p
     float2 pq;            // sum h p (p + 1) / 2  (so sum h p^2 = 2 pq - p1)
     float2 ag;            // sum alpha g
+    float hy, hz;         // sum h dy, sum h dz over both elements
+    float oy, oz;         // sum h o dy, sum h o dz, o = p + e bx/2 the slot's offset from uc_0
     float yy, zz, yz;     // sum h dy^2, sum h dz^2, sum h dy dz
 };
 
@@ -419,15 +421,15 @@ __device__ __forceinline__ void adjoint_rows(const Rec& R, unsigned long long m,
                 qs = add2(qs, m1);       // ends as sum h p (p + 1) / 2
             }
         }
-        const float2 dy2 = f2(dy, dy), dz2 = f2(dz, dz);
         A.h = add2(A.h, rs);
         A.p1 = add2(A.p1, m1);
         A.pq = add2(A.pq, qs);
-        A.hy = fma2(dy2, rs, A.hy);
-        A.hz = fma2(dz2, rs, A.hz);
-        A.p1y = fma2(dy2, m1, A.p1y);
-        A.p1z = fma2(dz2, m1, A.p1z);
         const float s0 = rs.x + rs.y;
+        const float s1 = fmaf(float(P), rs.y, m1.x + m1.y);  // sum h o over the row
+        A.hy = fmaf(s0, dy, A.hy);
+        A.hz = fmaf(s0, dz, A.hz);
+        A.oy = fmaf(s1, dy, A.oy);
+        A.oz = fmaf(s1, dz, A.oz);
         const float ty = dy * s0;
         A.yy = fmaf(ty, dy, A.yy);
         A.yz = fmaf(ty, dz, A.yz);
@@ -436,7 +438,7 @@ __device__ __forceinline__ void adjoint_rows(const Rec& R, unsigned long long m,
 }
 
 template <int BX, bool kDet>
-__global__ void __launch_bounds__(kBwdThreads, 7) k_render_bwd(
+__global__ void __launch_bounds__(kBwdThreads, (BX == 16 ? 7 : 8)) k_render_bwd(
     const int32_t* __restrict__ pair_gid, const int32_t* __restrict__ pair_gmj,
     const int32_t* __restrict__ pair_brick, const int64_t* __restrict__ npairs, int64_t capacity,
     const float4* __restrict__ rec4, RenderGeo G, const float2* __restrict__ aip,
@@ -622,8 +624,8 @@ __global__ void __launch_bounds__(kBwdThreads, 7) k_render_bwd(
         const int stage = sstage[lt];
         const Rec R = load_rec_bwd(rec4 + int64_t(sgid[lt]) * REC_F4);
         AdjAcc A;
-        A.h = A.hy = A.hz = A.p1 = A.p1y = A.p1z = A.pq = A.ag = f2(0.f, 0.f);
-        A.yy = A.zz = A.yz = 0.f;
+        A.h = A.p1 = A.pq = A.ag = f2(0.f, 0.f);
+        A.hy = A.hz = A.oy = A.oz = A.yy = A.zz = A.yz = 0.f;
         if (stage < kBwdStage)
             adjoint_rows<BX, true>(R, m, G, x0, y0, z0, &sfac[stage * kStageStride],
                                    aip, A);
@@ -636,9 +638,10 @@ __global__ void __launch_bounds__(kBwdThreads, 7) k_render_bwd(
         // sum h u^2 = uc^2 sum h + 2 uc sum h p + (2 pq - p1)
         float m2xx = fmaf(uc0, fmaf(uc0, A.h.x, 2.0f * A.p1.x), fmaf(2.0f, A.pq.x, -A.p1.x)) +
                      fmaf(uc1, fmaf(uc1, A.h.y, 2.0f * A.p1.y), fmaf(2.0f, A.pq.y, -A.p1.y));
-        float m2xy = fmaf(uc0, A.hy.x, A.p1y.x) + fmaf(uc1, A.hy.y, A.p1y.y);
-        float m2xz = fmaf(uc0, A.hz.x, A.p1z.x) + fmaf(uc1, A.hz.y, A.p1z.y);
-        float m1y = A.hy.x + A.hy.y, m1z = A.hz.x + A.hz.y;
+        // (the y, z cross moments take slot o at uc_0 + o)
+        float m2xy = fmaf(uc0, A.hy, A.oy);
+        float m2xz = fmaf(uc0, A.hz, A.oz);
+        float m1y = A.hy, m1z = A.hz;
         float m2yy = A.yy, m2zz = A.zz, m2yz = A.yz;
         const float dvp = A.ag.x + A.ag.y, dr = A.h.x + A.h.y;
         const float rr = R.r;
